@@ -1,0 +1,339 @@
+#!/usr/bin/env python
+"""QAOA max-cut benchmark: layers/s of the whole hot path on one B300 (or N independent replicas).
+
+One step = the whole path once: reset to |+>^n (launch control), p levels of {cost phase with
+the on-the-fly cut count, RX mixer on every qubit}, and <C> with the norm reduced in FP64 and
+read back to the host.  Default workload: near-3-regular graph on n = 33 vertices (one degree-2
+vertex, since a 3-regular graph on an odd vertex count does not exist), seed 0, p = 8 seeded
+levels, complex64 state of 2^33 amplitudes (64 GiB), larger than L2, so no L2 flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--n 33] [--p 8]
+
+Prints ONE JSON line on rank 0.  `--impl reference` times the CPU oracle (gate-level complex128
+simulator, the paper's Algorithm 1) on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2312_03019_b300 import inputs as I  # noqa: E402
+
+METRIC = "QAOA layers/s"
+UNIT = "layers/s"
+# DRAM bytes (read + write) per launch of the dominant pass kernel from an ncu capture of the
+# same kernel build; None when the kernel changed since it was captured.
+NCU_TRAFFIC_BYTES_PER_LAUNCH = None
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=33)
+    ap.add_argument("--p", type=int, default=8)
+    ap.add_argument("--prec", choices=["c64", "c128"], default="c64")
+    ap.add_argument("--cpu-sample-n", type=int, default=24)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(n: int, p: int):
+    g = I.regular3(n, 0)
+    gamma, beta = I.angles(p, 0)
+    return g, gamma, beta
+
+
+def workload_name(g, p, prec):
+    fam = "near-3-regular (one degree-2 vertex)" if g.n % 2 else "3-regular"
+    elem = "complex64" if prec == "c64" else "complex128"
+    return (f"{fam} graph n={g.n}, |E|={g.m}, seed 0, p={p} seeded levels, {elem} state of 2^{g.n} "
+            f"amplitudes, cut values on the fly, <C> and norm reduced in FP64")
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+# --------------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                    power.append(float(parts[3]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------------------- CPU oracle
+
+def oracle_level_seconds(n_s: int, p_levels: int = 1):
+    """Time `p_levels` oracle levels (cost layer + mixer layer, gate by gate) at n_s."""
+    import oracle
+    g, gamma, beta = workload(n_s, p_levels)
+    psi = oracle.initial_state(n_s)
+    t0 = time.perf_counter()
+    for k in range(p_levels):
+        psi = oracle.cost_layer(g, gamma[k], psi)
+        psi = oracle.mixer_layer(n_s, beta[k], psi)
+    return time.perf_counter() - t0, g
+
+
+def gates_per_level(g):
+    return 3 * g.m + 1 + g.n  # CNOT-RZ-CNOT per edge, global phase, one RX per qubit
+
+
+def oracle_layers_per_s(n_target: int, m_target_graph, n_s: int):
+    """Oracle layers/s at n_target extrapolated from one timed level at n_s: every gate streams
+    the whole state, so time scales with 2^n times the gate count."""
+    import oracle
+    t, gs = oracle_level_seconds(n_s)
+    scale = (2.0 ** (n_target - n_s)) * gates_per_level(m_target_graph) / gates_per_level(gs)
+    return 1.0 / (t * scale), t, gs, oracle.threads()
+
+
+def cpu_baseline_block(args, g_target):
+    v, t, gs, cores = oracle_layers_per_s(g_target.n, g_target, args.cpu_sample_n)
+    return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"one oracle level (gate-level complex128, Algorithm 1) on the same graph family at "
+                       f"n={gs.n} (|E|={gs.m}) took {t:.2f} s on {cores} threads; scaled to n={g_target.n} "
+                       f"by 2^n x gate count ({gates_per_level(gs)} -> {gates_per_level(g_target)} gates/level)")}
+
+
+# --------------------------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    g, gamma, beta = workload(args.n, args.p)
+    import oracle
+    warm = max(3, args.warmup)
+    n_s = args.cpu_sample_n
+    for _ in range(warm):
+        oracle_level_seconds(n_s)
+    times = []
+    gs = None
+    for _ in range(args.steps):
+        t, gs = oracle_level_seconds(n_s)
+        times.append(t)
+    scale = (2.0 ** (args.n - n_s)) * gates_per_level(g) / gates_per_level(gs)
+    t_step = statistics.mean(times) * scale  # one layer at the target size
+    value = 1.0 / t_step
+    cores = oracle.threads()
+    rec = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": warm, "ms_per_step": t_step * 1e3 * args.p,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": workload_name(g, args.p, "c128"), "n": args.n, "p": args.p, "edges": g.m},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": (f"each step: one oracle level at n={n_s} (|E|={gs.m}, same family) on {cores} "
+                                    f"threads, scaled to n={args.n} by 2^n x gate count")},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(rec), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2312_03019_b300 import build as bld
+    bld.build()
+    from paper_2312_03019_b300 import binding as B
+
+    g, gamma, beta = workload(args.n, args.p)
+    warm = max(3, args.warmup)
+    st = B.QAOAState(g, args.prec, device=dev)
+    stream = st.stream
+
+    def step():
+        st.reset()
+        st.apply_layers(gamma, beta)
+        return st.expectation()
+
+    for _ in range(warm):
+        step()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    props = torch.cuda.get_device_properties(dev)
+    uuid = getattr(props, "uuid", None)
+    gpu_id = f"GPU-{uuid}" if uuid is not None else str(local)
+    sampler = ClockSampler(gpu_id)
+
+    B.qaoa_profile_enable(st.handle, True)
+    barrier()
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    results = []
+    for _ in range(args.steps):
+        results.append(step())
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    prof = B.qaoa_profile_read(st.handle)
+    B.qaoa_profile_enable(st.handle, False)
+
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * args.steps * args.p / (ms_max / 1e3)
+
+    # end to end through the public API with host inputs and a host result
+    e2e = None
+    if not args.no_e2e:
+        for _ in range(2):
+            h = B.qaoa_state_init(g, args.prec, st.buffer.data_ptr(), st.nbytes, stream.cuda_stream)
+            B.qaoa_apply_layers(h, gamma, beta)
+            B.qaoa_expectation(h)
+            B.qaoa_state_free(h)
+        barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            h = B.qaoa_state_init(g, args.prec, st.buffer.data_ptr(), st.nbytes, stream.cuda_stream)
+            B.qaoa_apply_layers(h, gamma, beta)
+            B.qaoa_expectation(h)
+            B.qaoa_state_free(h)
+        torch.cuda.synchronize(dev)
+        el = time.perf_counter() - t0
+        te = torch.tensor([el], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * args.steps * args.p / float(te.item()), "unit": UNIT,
+               "h2d_bytes_per_step": int(8 * g.m + 16 * args.p), "d2h_bytes_per_step": 16,
+               "note": "graph and angles go host to device as kernel parameters; <C> and norm come back"}
+
+    peak, peak_kind = measured_peaks()
+    elem = 8 if args.prec == "c64" else 16
+    roof = None
+    if prof["pass_launches"] > 0:
+        per_launch_s = prof["pass_ms"] / prof["pass_launches"] / 1e3
+        bytes_per_launch = 2.0 * elem * (1 << g.n)
+        achieved = bytes_per_launch / per_launch_s / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": NCU_TRAFFIC_BYTES_PER_LAUNCH, "peak_kind": f"{peak_kind} copy bandwidth",
+                "kernel": "tile_kernel (read+write state pass)",
+                "bytes_per_launch": bytes_per_launch, "launch_ms": per_launch_s * 1e3,
+                "launches": prof["pass_launches"]}
+    state_gbs = value * 2.0 * elem * (1 << g.n) / 1e9
+
+    rec = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": warm,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.prec == "c64" else "f64", "data": "synthetic",
+        "config": {"workload": workload_name(g, args.p, args.prec), "n": g.n, "p": args.p, "edges": g.m,
+                   "state_bytes": elem << g.n, "l2": "state larger than L2 (no flush needed)",
+                   "parallelism": f"{world} independent replicas" if world > 1 else "single GPU"},
+        "state_gbs_algorithmic": state_gbs,
+        "hbm_frac_algorithmic": state_gbs / world / peak,
+        "passes_per_step": (prof["pass_launches"] + prof["synth_launches"]) / args.steps,
+        "roofline": roof,
+        "gpu_launches": prof["kernel_launches"],
+        "clocks": clocks,
+        "e2e": e2e,
+        "expectation": results[-1][0], "norm": results[-1][1],
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        del st
+        torch.cuda.empty_cache()
+        rec["cpu_baseline"] = cpu_baseline_block(args, g)
+    if rank == 0:
+        print(json.dumps(rec), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

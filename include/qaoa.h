@@ -1,0 +1,155 @@
+/*
+ * qaoa.h -- C ABI of the B300 QAOA max-cut state-vector simulator.
+ *
+ * The library simulates the QAOA circuit of the paper's Algorithm 1 (Section 2.1) for the
+ * max-cut problem, using the paper's rotation compression (Eqs. rewrite_UC .. UC_opt,
+ * Algorithm 2), launch control (Section 2.2) and the popcount cut count of Algorithm 3
+ * (Section 2.3), on one GPU with hand-written sm_103a kernels.
+ *
+ * Conventions (fixed here because the paper's own definition of the cost Hamiltonian is not
+ * part of its text):
+ *   - qubit u is bit u of the basis index z (least significant bit = qubit 0);
+ *   - C(z) = sum over edges (u, v) of w_uv * (bit u of z XOR bit v of z);
+ *   - the initial state is |+>^n, every amplitude 2^(-n/2) (launch control, Section 2.2);
+ *   - level k applies psi_z <- exp(-i gamma_k C(z)) psi_z, then RX(2 beta_k) =
+ *     [[cos beta_k, -i sin beta_k], [-i sin beta_k, cos beta_k]] on every qubit.
+ *     The paper's gamma is minus this gamma and its RX angle is 2 beta (global phase aside);
+ *   - <C> = sum_z |psi_z|^2 C(z).
+ *
+ * Memory: a state of 2^n amplitudes lives in a device buffer the CALLER allocates and owns
+ * (complex64 = 2 x float32 interleaved, complex128 = 2 x float64 interleaved, index z).  The
+ * library borrows it; it allocates only small workspace of its own (phase tables, per-tile
+ * partial sums) at qaoa_state_init and frees it at qaoa_state_free.  Host arrays passed in
+ * are copied before the call returns; the caller may free them afterwards.
+ *
+ * Errors: every entry point returns a qaoa_status; negative values are errors and
+ * qaoa_last_error() returns a message for the calling thread.  Nothing aborts and no C++
+ * exception crosses the ABI.  Work is enqueued on the CUDA stream given at init; calls that
+ * return host results synchronise that stream.
+ */
+#ifndef QAOA_B300_QAOA_H
+#define QAOA_B300_QAOA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    QAOA_OK = 0,
+    QAOA_PENDING = 1,           /* serving: result not ready yet */
+    QAOA_ERR_INVALID = -1,      /* bad argument (graph, size, angle, handle) */
+    QAOA_ERR_OOM = -2,          /* workspace allocation failed */
+    QAOA_ERR_CUDA = -3,         /* a CUDA call failed; message in qaoa_last_error() */
+    QAOA_ERR_AGAIN = -4,        /* serving: queue full, retry later */
+    QAOA_ERR_TIMEOUT = -5,      /* serving: deadline passed */
+    QAOA_ERR_UNSUPPORTED = -6   /* valid request this build cannot run */
+} qaoa_status;
+
+typedef enum { QAOA_C64 = 0, QAOA_C128 = 1 } qaoa_prec;
+
+/* Problem statement of Table 1 (Section 2.1): N vertices (= qubits), the edge list that the
+ * upper-triangular matrix `graph` encodes, and optional edge weights `w`.
+ *   n       : 1 <= n <= 34
+ *   m       : number of edges, m >= 0
+ *   edges   : 2*m int32 endpoints (u0, v0, u1, v1, ...), 0 <= u, v < n, u != v, no pair twice
+ *   weights : NULL for unit weights (Algorithm 3); otherwise m finite doubles (Algorithm 2)
+ * Unit weights are required with more than 65535 edges' worth of cut values (never for n<=34). */
+typedef struct {
+    int32_t n;
+    int32_t m;
+    const int32_t *edges;
+    const double *weights;
+} qaoa_graph;
+
+typedef struct qaoa_state_s *qaoa_state; /* opaque; owned by the library */
+
+/* Bytes a state of n qubits needs: 2^n * 8 (complex64) or 2^n * 16 (complex128); 0 if n is
+ * out of range. */
+size_t qaoa_state_bytes(int32_t n, qaoa_prec prec);
+
+/* Binds a caller-owned device buffer (at least qaoa_state_bytes(n, prec) bytes, 16-byte
+ * aligned) and a CUDA stream (cudaStream_t passed as void*, NULL = legacy default stream) to a
+ * new state handle holding |+>^n (Section 2.2, launch control).  The buffer is not written
+ * here: the uniform amplitudes are produced by the first kernel that needs them, so the first
+ * level of qaoa_apply_layers reads nothing.  Validates the graph (QAOA_ERR_INVALID on a self
+ * loop, repeated edge, endpoint out of range, non-finite or negative weight), encodes the
+ * rows graph_I of Table 1 and the pass plan, and allocates workspace (QAOA_ERR_OOM).  On
+ * success *out receives the handle. */
+qaoa_status qaoa_state_init(const qaoa_graph *g, qaoa_prec prec, void *dev_buf, size_t buf_bytes,
+                            void *cuda_stream, qaoa_state *out);
+
+/* Returns the state to |+>^n (deferred, nothing is written) keeping the graph, buffer, stream
+ * and workspace: the initial layer of Algorithm 1 by launch control (Section 2.2). */
+qaoa_status qaoa_state_reset(qaoa_state s);
+
+/* Applies p levels (Algorithm 1's level loop) with angles gamma[0..p-1], beta[0..p-1] on top
+ * of the current state: per level, the rotation-compressed cost phase (Eq. UC_opt with the
+ * popcount count of Algorithm 3, evaluated on the fly) and the RX mixer on every qubit.
+ * Asynchronous on the state's stream; the angle arrays are copied before return.  p == 0
+ * only writes out a still-deferred |+>^n.  QAOA_ERR_INVALID on p < 0 or non-finite angles. */
+qaoa_status qaoa_apply_layers(qaoa_state s, int32_t p, const double *gamma, const double *beta);
+
+/* <C> = sum_z |psi_z|^2 C(z) and the squared norm sum_z |psi_z|^2 of the current state,
+ * reduced in FP64 in a fixed order (run-to-run identical).  Synchronises the stream. */
+qaoa_status qaoa_expectation(qaoa_state s, double *out_c, double *out_norm);
+
+/* Copies the current state (bytes = qaoa_state_bytes) to host memory, writing out a deferred
+ * |+>^n first.  Synchronises the stream.  Parity hook. */
+qaoa_status qaoa_state_copy_out(qaoa_state s, void *host_dst, size_t bytes);
+
+/* Releases the handle and its workspace after the stream's pending work; never frees the
+ * caller's buffer.  NULL is accepted. */
+qaoa_status qaoa_state_free(qaoa_state s);
+
+/* Cut value C(z) of every basis state (Algorithm 3 on the GPU, computed by the same device
+ * code the cost phase uses), written to host_out[0 .. 2^n - 1].  Unit weights only;
+ * n <= 30.  Runs on the current device's legacy default stream and synchronises it.  Parity
+ * hook. */
+qaoa_status qaoa_cut_table(const qaoa_graph *g, uint16_t *host_out);
+
+/* Same as qaoa_cut_table, but evaluated under the tile geometry of mixer group `group`
+ * (0 = the low group) of the pass plan for precision `prec`, in register layout `layout`
+ * (0, 1 or 2).  Lets tests check every split of the cut count the kernels use.  Parity
+ * hook; QAOA_ERR_INVALID for a group or layout the plan does not have. */
+qaoa_status qaoa_cut_table_geometry(const qaoa_graph *g, qaoa_prec prec, int32_t group,
+                                    int32_t layout, uint16_t *host_out);
+
+/* Host-only description of the pass plan for n qubits, precision prec and p levels (no GPU
+ * needed).  Writes up to cap int32 values into out and returns the number needed in *count:
+ *   [Q, R, c_min, n_groups, (lo, size) per group, n_passes,
+ *    per pass: (group, n_ops, (kind, arg, mask) per op)]
+ * kind: 1 load, 2 synthesise |+> (arg = layout), 3 exchange (arg = layout), 4 RX (arg =
+ * level, mask = local target bits), 5 phase (arg = level), 6 expectation, 7 store.  Small
+ * states (whole state in one CTA) have no pass plan: *count = 0.  For tests of the
+ * planner: every level must apply RX to every qubit exactly once, phases in order. */
+qaoa_status qaoa_plan_describe(int32_t n, qaoa_prec prec, int32_t p, int32_t *out, int32_t cap,
+                               int32_t *count);
+
+/* Launch statistics, for the benchmark's roofline.  When enabled, every state-pass kernel
+ * launch is bracketed by CUDA events on the state's stream. */
+typedef struct {
+    int64_t kernel_launches;     /* all kernels this handle launched since the last reset */
+    int64_t pass_launches;       /* read+write state passes among them */
+    double pass_ms;              /* summed event time of those passes */
+    double pass_bytes;           /* algorithmic bytes of those passes: 2 * 2^n * element size each */
+    int64_t synth_launches;      /* passes that write without reading (deferred |+>^n) */
+    double synth_ms;
+    double synth_bytes;
+} qaoa_profile_stats;
+
+/* enable != 0 starts recording (and resets the counters); 0 stops. */
+qaoa_status qaoa_profile_enable(qaoa_state s, int32_t enable);
+/* Synchronises the stream and returns the counters since the last enable. */
+qaoa_status qaoa_profile_read(qaoa_state s, qaoa_profile_stats *out);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char *qaoa_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QAOA_B300_QAOA_H */

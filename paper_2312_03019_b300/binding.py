@@ -1,0 +1,245 @@
+"""Thin ctypes binding of ``include/qaoa.h`` (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does nothing but convert
+arguments; all of the simulation runs in ``libqaoa_b300.so``.  Importing this module loads the
+library and raises ``ImportError`` if it is missing: there is no CPU fallback.
+
+Device memory and streams come from PyTorch: ``QAOAState`` allocates the state buffer with
+``torch.empty(..., device="cuda")`` and passes its ``data_ptr()`` and the current stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libqaoa_b300.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build it with `python -m paper_2312_03019_b300.build` "
+        "(there is no CPU fallback)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+QAOA_OK = 0
+QAOA_PENDING = 1
+QAOA_ERR_INVALID = -1
+QAOA_ERR_OOM = -2
+QAOA_ERR_CUDA = -3
+QAOA_ERR_AGAIN = -4
+QAOA_ERR_TIMEOUT = -5
+QAOA_ERR_UNSUPPORTED = -6
+QAOA_C64 = 0
+QAOA_C128 = 1
+
+_STATUS = {0: "OK", 1: "PENDING", -1: "INVALID", -2: "OOM", -3: "CUDA", -4: "AGAIN", -5: "TIMEOUT",
+           -6: "UNSUPPORTED"}
+
+
+class QAOAError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"QAOA_ERR_{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Graph(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("m", ctypes.c_int32),
+                ("edges", ctypes.POINTER(ctypes.c_int32)), ("weights", ctypes.POINTER(ctypes.c_double))]
+
+
+class ProfileStats(ctypes.Structure):
+    _fields_ = [("kernel_launches", ctypes.c_int64), ("pass_launches", ctypes.c_int64),
+                ("pass_ms", ctypes.c_double), ("pass_bytes", ctypes.c_double),
+                ("synth_launches", ctypes.c_int64), ("synth_ms", ctypes.c_double),
+                ("synth_bytes", ctypes.c_double)]
+
+
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+def _sig(name, res, args):
+    f = getattr(_lib, name)
+    f.restype = res
+    f.argtypes = args
+    return f
+
+
+_sig("qaoa_state_bytes", ctypes.c_size_t, [_i32, ctypes.c_int])
+_sig("qaoa_state_init", ctypes.c_int, [ctypes.POINTER(_Graph), ctypes.c_int, _vp, ctypes.c_size_t, _vp,
+                                        ctypes.POINTER(_vp)])
+_sig("qaoa_state_reset", ctypes.c_int, [_vp])
+_sig("qaoa_apply_layers", ctypes.c_int, [_vp, _i32, _dp, _dp])
+_sig("qaoa_expectation", ctypes.c_int, [_vp, _dp, _dp])
+_sig("qaoa_state_copy_out", ctypes.c_int, [_vp, _vp, ctypes.c_size_t])
+_sig("qaoa_state_free", ctypes.c_int, [_vp])
+_sig("qaoa_cut_table", ctypes.c_int, [ctypes.POINTER(_Graph), _vp])
+_sig("qaoa_cut_table_geometry", ctypes.c_int, [ctypes.POINTER(_Graph), ctypes.c_int, _i32, _i32, _vp])
+_sig("qaoa_plan_describe", ctypes.c_int, [_i32, ctypes.c_int, _i32, ctypes.POINTER(_i32), _i32,
+                                           ctypes.POINTER(_i32)])
+_sig("qaoa_profile_enable", ctypes.c_int, [_vp, _i32])
+_sig("qaoa_profile_read", ctypes.c_int, [_vp, ctypes.POINTER(ProfileStats)])
+_sig("qaoa_last_error", ctypes.c_char_p, [])
+
+
+def qaoa_last_error() -> str:
+    return _lib.qaoa_last_error().decode()
+
+
+def _check(st: int) -> int:
+    if st < 0:
+        raise QAOAError(st, qaoa_last_error())
+    return st
+
+
+def _prec(prec) -> int:
+    if prec in (QAOA_C64, "c64", "complex64"):
+        return QAOA_C64
+    if prec in (QAOA_C128, "c128", "complex128"):
+        return QAOA_C128
+    raise ValueError(f"unknown precision {prec!r}")
+
+
+def _graph(g):
+    """Marshal an object with .n, .edges ([m, 2] ints) and optional .weights."""
+    e = np.ascontiguousarray(np.asarray(g.edges, dtype=np.int32).reshape(-1))
+    w = getattr(g, "weights", None)
+    w = None if w is None else np.ascontiguousarray(np.asarray(w, dtype=np.float64))
+    s = _Graph(int(g.n), int(e.size // 2), e.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+               w.ctypes.data_as(_dp) if w is not None else None)
+    return s, (e, w)  # keep arrays alive
+
+
+def qaoa_state_bytes(n: int, prec="c64") -> int:
+    return int(_lib.qaoa_state_bytes(int(n), _prec(prec)))
+
+
+def qaoa_state_init(g, prec, dev_ptr: int, nbytes: int, stream: int = 0) -> int:
+    gs, keep = _graph(g)
+    h = _vp()
+    _check(_lib.qaoa_state_init(ctypes.byref(gs), _prec(prec), _vp(dev_ptr), nbytes, _vp(stream), ctypes.byref(h)))
+    return h.value
+
+
+def qaoa_state_reset(h: int) -> None:
+    _check(_lib.qaoa_state_reset(_vp(h)))
+
+
+def qaoa_apply_layers(h: int, gamma, beta) -> None:
+    ga = np.ascontiguousarray(np.asarray(gamma, dtype=np.float64).reshape(-1))
+    be = np.ascontiguousarray(np.asarray(beta, dtype=np.float64).reshape(-1))
+    if ga.size != be.size:
+        raise ValueError("gamma and beta must have the same length")
+    _check(_lib.qaoa_apply_layers(_vp(h), int(ga.size), ga.ctypes.data_as(_dp), be.ctypes.data_as(_dp)))
+
+
+def qaoa_expectation(h: int):
+    c = ctypes.c_double()
+    nn = ctypes.c_double()
+    _check(_lib.qaoa_expectation(_vp(h), ctypes.byref(c), ctypes.byref(nn)))
+    return c.value, nn.value
+
+
+def qaoa_state_copy_out(h: int, n: int, prec) -> np.ndarray:
+    dt = np.complex64 if _prec(prec) == QAOA_C64 else np.complex128
+    out = np.empty(1 << n, dtype=dt)
+    _check(_lib.qaoa_state_copy_out(_vp(h), _vp(out.ctypes.data), out.nbytes))
+    return out
+
+
+def qaoa_state_free(h: int) -> None:
+    _check(_lib.qaoa_state_free(_vp(h)))
+
+
+def qaoa_cut_table(g) -> np.ndarray:
+    gs, keep = _graph(g)
+    out = np.empty(1 << int(g.n), dtype=np.uint16)
+    _check(_lib.qaoa_cut_table(ctypes.byref(gs), _vp(out.ctypes.data)))
+    return out
+
+
+def qaoa_cut_table_geometry(g, prec, group: int, layout: int) -> np.ndarray:
+    gs, keep = _graph(g)
+    out = np.empty(1 << int(g.n), dtype=np.uint16)
+    _check(_lib.qaoa_cut_table_geometry(ctypes.byref(gs), _prec(prec), int(group), int(layout),
+                                        _vp(out.ctypes.data)))
+    return out
+
+
+def qaoa_plan_describe(n: int, prec, p: int) -> list:
+    cnt = _i32()
+    _check(_lib.qaoa_plan_describe(int(n), _prec(prec), int(p), None, 0, ctypes.byref(cnt)))
+    buf = (_i32 * max(1, cnt.value))()
+    _check(_lib.qaoa_plan_describe(int(n), _prec(prec), int(p), buf, cnt.value, ctypes.byref(cnt)))
+    return list(buf[: cnt.value])
+
+
+def qaoa_profile_enable(h: int, enable: bool = True) -> None:
+    _check(_lib.qaoa_profile_enable(_vp(h), 1 if enable else 0))
+
+
+def qaoa_profile_read(h: int) -> dict:
+    st = ProfileStats()
+    _check(_lib.qaoa_profile_read(_vp(h), ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in ProfileStats._fields_}
+
+
+class QAOAState:
+    """A state of ``g.n`` qubits in a torch-allocated device buffer, bound to the current stream."""
+
+    def __init__(self, g, prec="c64", device=None, stream=None):
+        import torch
+
+        self.n = int(g.n)
+        self.prec = _prec(prec)
+        self.nbytes = qaoa_state_bytes(self.n, self.prec)
+        if self.nbytes == 0:
+            raise ValueError("n out of range")
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.buffer = torch.empty(self.nbytes, dtype=torch.uint8, device=dev)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        with torch.cuda.device(dev):
+            self.handle = qaoa_state_init(g, self.prec, self.buffer.data_ptr(), self.nbytes,
+                                          self.stream.cuda_stream)
+
+    def reset(self):
+        qaoa_state_reset(self.handle)
+        return self
+
+    def apply_layers(self, gamma, beta):
+        qaoa_apply_layers(self.handle, gamma, beta)
+        return self
+
+    def expectation(self):
+        return qaoa_expectation(self.handle)
+
+    def amplitudes(self) -> np.ndarray:
+        return qaoa_state_copy_out(self.handle, self.n, self.prec)
+
+    def as_tensor(self):
+        """The device buffer viewed as a complex torch tensor (call after apply_layers)."""
+        import torch
+
+        dt = torch.complex64 if self.prec == QAOA_C64 else torch.complex128
+        return self.buffer.view(dt)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            qaoa_state_free(self.handle)
+            self.handle = None
+        self.buffer = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def uniform_amplitude(n: int) -> float:
+    return math.pow(2.0, -0.5 * n)

@@ -1,0 +1,612 @@
+// capi.cu -- host runtime behind include/qaoa.h.
+//
+// A state handle binds a caller-owned device buffer and stream to a graph.  qaoa_apply_layers
+// uploads the levels' angles as kernel parameters, builds the per-level phase tables on the
+// device (coeff_kernel), and enqueues the pass plan of plan.h: one tile_kernel launch per pass
+// (n > Q_small) or one small_kernel launch for all levels (n <= Q_small).  The expectation is
+// fused into the last pass; qaoa_expectation only reduces the per-tile partials.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <set>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/qaoa.h"
+#include "kernels.cuh"
+#include "plan.h"
+
+using namespace qaoa;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+qaoa_status fail(qaoa_status st, const std::string& msg) {
+    g_last_error = msg;
+    return st;
+}
+
+qaoa_status cuda_fail(cudaError_t e, const char* where) {
+    g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+    return QAOA_ERR_CUDA;
+}
+
+#define CUDA_TRY(call)                                          \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);     \
+    } while (0)
+
+constexpr int kSmallMaxC64 = 14;   // 2^14 x 8 B = 128 KiB of shared memory
+constexpr int kSmallMaxC128 = 13;  // 2^13 x 16 B
+
+struct HostGraph {
+    int n = 0, m = 0;
+    std::vector<std::pair<int, int>> edges;  // u < v
+    uint64_t upper[kMaxN] = {};              // graph_I rows (Table 1)
+    uint64_t adj[kMaxN] = {};                // full adjacency
+};
+
+qaoa_status encode_graph(const qaoa_graph* g, HostGraph& hg) {
+    if (!g) return fail(QAOA_ERR_INVALID, "graph is NULL");
+    if (g->n < 1 || g->n > kMaxN) return fail(QAOA_ERR_INVALID, "n must be in [1, 34]");
+    if (g->m < 0) return fail(QAOA_ERR_INVALID, "m must be >= 0");
+    if (g->m > 0 && !g->edges) return fail(QAOA_ERR_INVALID, "edges is NULL");
+    if (g->weights) return fail(QAOA_ERR_UNSUPPORTED, "weighted graphs are not supported by this entry point");
+    hg.n = g->n;
+    hg.m = g->m;
+    std::set<std::pair<int, int>> seen;
+    for (int e = 0; e < g->m; ++e) {
+        int u = g->edges[2 * e], v = g->edges[2 * e + 1];
+        if (u < 0 || v < 0 || u >= g->n || v >= g->n) return fail(QAOA_ERR_INVALID, "edge endpoint out of range");
+        if (u == v) return fail(QAOA_ERR_INVALID, "self loop");
+        if (u > v) std::swap(u, v);
+        if (!seen.insert({u, v}).second) return fail(QAOA_ERR_INVALID, "repeated edge");
+        hg.edges.push_back({u, v});
+        hg.upper[u] |= 1ull << v;
+        hg.adj[u] |= 1ull << v;
+        hg.adj[v] |= 1ull << u;
+    }
+    std::sort(hg.edges.begin(), hg.edges.end());
+    return QAOA_OK;
+}
+
+bool is_small(int n, int prec) { return n <= (prec == QAOA_C64 ? kSmallMaxC64 : kSmallMaxC128); }
+
+size_t elem_bytes(int prec) { return prec == QAOA_C64 ? 8 : 16; }
+
+// Per-geometry decomposition tables of the on-the-fly cut count.
+template <int Q>
+void fill_geometry(TileArgs<Q>& a, const HostGraph& hg, const Geometry& geo, const TileConfig& tc) {
+    a.n = hg.n;
+    a.cprime = geo.cprime;
+    a.g0 = geo.g0;
+    for (int v = 0; v < kMaxN; ++v) a.gmask[v] = v < hg.n ? hg.upper[v] : 0;
+    auto gpos = [&](int u) { return u < geo.cprime ? u : geo.g0 + (u - geo.cprime); };
+    auto lpos = [&](int w) -> int {
+        if (w < geo.cprime) return w;
+        if (w >= geo.g0 && w < geo.g0 + (Q - geo.cprime)) return geo.cprime + (w - geo.g0);
+        return -1;
+    };
+    uint64_t tileMask = 0;
+    for (int u = 0; u < Q; ++u) tileMask |= 1ull << gpos(u);
+    const uint64_t nMask = hg.n >= 64 ? ~0ull : ((1ull << hg.n) - 1ull);
+    for (int u = 0; u < Q; ++u) {
+        const int gu = gpos(u);
+        uint32_t la = 0;
+        for (int w = 0; w < hg.n; ++w)
+            if ((hg.adj[gu] >> w) & 1ull) {
+                const int lw = lpos(w);
+                if (lw >= 0) la |= 1u << lw;
+            }
+        a.locAdj[u] = la;
+        a.locUpper[u] = la & ~((2u << u) - 1u);
+        a.outAdj[u] = hg.adj[gu] & ~tileMask & nMask;
+    }
+    for (int L = 0; L < 3; ++L) {
+        const int rl = tc.regLo(L);
+        for (int x = 0; x < 32; ++x) {
+            int c = 0;
+            if (x < (1 << tc.R))
+                for (int j = 0; j < tc.R; ++j)
+                    for (int k = j + 1; k < tc.R; ++k)
+                        if ((a.locAdj[rl + j] >> (rl + k)) & 1u) c += ((x >> j) ^ (x >> k)) & 1;
+            a.crtab[L][x] = (uint8_t)c;
+        }
+    }
+}
+
+template <typename real>
+struct PrecTraits;
+template <>
+struct PrecTraits<float> {
+    static constexpr int Q = 13, R = 5;
+};
+template <>
+struct PrecTraits<double> {
+    static constexpr int Q = 12, R = 4;
+};
+
+struct EventPair {
+    cudaEvent_t a = nullptr, b = nullptr;
+    int kind = 0;  // 1 read+write pass, 2 synthesising pass
+};
+
+}  // namespace
+
+struct qaoa_state_s {
+    int dev = 0;
+    int n = 0;
+    int prec = 0;
+    uint64_t dim = 0;
+    void* buf = nullptr;
+    cudaStream_t stream = nullptr;
+    HostGraph g;
+    TileConfig tc{};
+    std::vector<Group> groups;
+    bool small = false;
+    uint64_t ntiles = 1;
+    void* d_phase = nullptr;
+    void* d_mix = nullptr;
+    double2* d_partials = nullptr;
+    double2* d_result = nullptr;
+    double2* h_result = nullptr;
+    uint64_t partial_count = 0;
+    bool lazy = true;
+    bool exp_valid = false;
+    // profiling
+    bool prof = false;
+    std::vector<EventPair> events;
+    size_t ev_used = 0;
+    int64_t launches = 0;
+};
+
+namespace {
+
+EventPair* next_event(qaoa_state s, int kind) {
+    if (!s->prof) return nullptr;
+    if (s->ev_used == s->events.size()) {
+        EventPair p;
+        if (cudaEventCreate(&p.a) != cudaSuccess || cudaEventCreate(&p.b) != cudaSuccess) return nullptr;
+        s->events.push_back(p);
+    }
+    EventPair* e = &s->events[s->ev_used++];
+    e->kind = kind;
+    return e;
+}
+
+template <typename real>
+qaoa_status launch_tile(qaoa_state s, TileArgs<PrecTraits<real>::Q>& a, int kind) {
+    constexpr int Q = PrecTraits<real>::Q, R = PrecTraits<real>::R;
+    using C2 = typename C2T<real>::type;
+    auto kfn = tile_kernel<real, Q, R>;
+    const size_t smem = (size_t)(1u << Q) * sizeof(C2);
+    static bool attr_set = false;
+    if (!attr_set) {
+        CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_set = true;
+    }
+    EventPair* ev = kind ? next_event(s, kind) : nullptr;
+    if (ev) CUDA_TRY(cudaEventRecord(ev->a, s->stream));
+    kfn<<<(unsigned)s->ntiles, 1u << (Q - R), smem, s->stream>>>(a);
+    CUDA_TRY(cudaGetLastError());
+    if (ev) CUDA_TRY(cudaEventRecord(ev->b, s->stream));
+    s->launches++;
+    return QAOA_OK;
+}
+
+template <typename real>
+qaoa_status launch_small(qaoa_state s, const SmallJob& j) {
+    using C2 = typename C2T<real>::type;
+    auto kfn = small_kernel<real>;
+    const size_t smem = (size_t)s->dim * sizeof(C2);
+    static bool attr_set = false;
+    if (!attr_set) {
+        CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024));
+        attr_set = true;
+    }
+    kfn<<<1, kSmallThreads, smem, s->stream>>>(j);
+    CUDA_TRY(cudaGetLastError());
+    s->launches++;
+    return QAOA_OK;
+}
+
+template <typename real>
+void fill_program(TileArgs<PrecTraits<real>::Q>& a, qaoa_state s, const Pass& ps) {
+    const Geometry geo = group_geometry(s->groups[ps.group], s->tc);
+    fill_geometry(a, s->g, geo, s->tc);
+    a.nops = (int)ps.ops.size();
+    a.need_cut = 0;
+    for (size_t i = 0; i < ps.ops.size(); ++i) {
+        a.ops[i] = ps.ops[i];
+        const uint8_t k = ps.ops[i].kind;
+        if (k == OP_PHASE || k == OP_EXPECT || k == OP_CUTVAL) a.need_cut = 1;
+    }
+    a.E1 = s->g.m + 1;
+    a.init_amp = std::pow(2.0, -0.5 * s->n);
+    a.state = s->buf;
+    a.phase = s->d_phase;
+    a.mix = s->d_mix;
+    a.partials = s->d_partials;
+    a.cutout = nullptr;
+}
+
+template <typename real>
+qaoa_status run_plan(qaoa_state s, const Plan& plan) {
+    constexpr int Q = PrecTraits<real>::Q;
+    TileArgs<Q> a;
+    for (const Pass& ps : plan.passes) {
+        std::memset(&a, 0, sizeof(a));
+        fill_program<real>(a, s, ps);
+        int kind = 0;
+        if (ps.store) kind = ps.synth ? 2 : 1;
+        qaoa_status st = launch_tile<real>(s, a, kind);
+        if (st != QAOA_OK) return st;
+    }
+    return QAOA_OK;
+}
+
+template <typename real>
+qaoa_status apply_chunk(qaoa_state s, int levels, const double* gamma, const double* beta, bool expect) {
+    CoeffArgs ca;
+    std::memset(&ca, 0, sizeof(ca));
+    ca.levels = levels;
+    ca.E1 = s->g.m + 1;
+    for (int k = 0; k < levels; ++k) {
+        ca.gamma[k] = gamma[k];
+        ca.beta[k] = beta[k];
+    }
+    ca.phase = s->d_phase;
+    ca.mix = s->d_mix;
+    dim3 grid((unsigned)std::max(1, (ca.E1 + 255) / 256), (unsigned)levels);
+    coeff_kernel<real><<<grid, 256, 0, s->stream>>>(ca);
+    CUDA_TRY(cudaGetLastError());
+    s->launches++;
+
+    if (s->small) {
+        SmallJob j;
+        std::memset(&j, 0, sizeof(j));
+        j.n = s->n;
+        j.levels = levels;
+        j.E1 = s->g.m + 1;
+        j.synth = s->lazy ? 1 : 0;
+        j.expect = expect ? 1 : 0;
+        j.store = 1;
+        j.init_amp = std::pow(2.0, -0.5 * s->n);
+        for (int v = 0; v < kMaxN; ++v) j.gmask[v] = v < s->n ? s->g.upper[v] : 0;
+        j.state = s->buf;
+        j.phase = s->d_phase;
+        j.mix = s->d_mix;
+        j.partials = s->d_partials;
+        qaoa_status st = launch_small<real>(s, j);
+        if (st != QAOA_OK) return st;
+    } else {
+        Plan plan = plan_levels(s->n, s->tc, levels, s->lazy, expect);
+        qaoa_status st = run_plan<real>(s, plan);
+        if (st != QAOA_OK) return st;
+    }
+    s->lazy = false;
+    if (expect) {
+        s->exp_valid = true;
+        s->partial_count = s->small ? 1 : s->ntiles;
+    } else {
+        s->exp_valid = false;
+    }
+    return QAOA_OK;
+}
+
+template <typename real>
+qaoa_status materialize(qaoa_state s) {
+    if (!s->lazy) return QAOA_OK;
+    fill_kernel<real><<<148 * 8, 256, 0, s->stream>>>(s->buf, s->dim, std::pow(2.0, -0.5 * s->n));
+    CUDA_TRY(cudaGetLastError());
+    s->launches++;
+    s->lazy = false;
+    return QAOA_OK;
+}
+
+template <typename real>
+qaoa_status compute_partials(qaoa_state s) {
+    if (s->exp_valid) return QAOA_OK;
+    if (s->small) {
+        SmallJob j;
+        std::memset(&j, 0, sizeof(j));
+        j.n = s->n;
+        j.levels = 0;
+        j.E1 = s->g.m + 1;
+        j.synth = s->lazy ? 1 : 0;
+        j.expect = 1;
+        j.store = 0;
+        j.init_amp = std::pow(2.0, -0.5 * s->n);
+        for (int v = 0; v < kMaxN; ++v) j.gmask[v] = v < s->n ? s->g.upper[v] : 0;
+        j.state = s->buf;
+        j.phase = s->d_phase;
+        j.mix = s->d_mix;
+        j.partials = s->d_partials;
+        qaoa_status st = launch_small<real>(s, j);
+        if (st != QAOA_OK) return st;
+        s->partial_count = 1;
+    } else {
+        Plan plan = plan_readonly(s->n, s->tc, s->lazy, OP_EXPECT, 0, 0);
+        qaoa_status st = run_plan<real>(s, plan);
+        if (st != QAOA_OK) return st;
+        s->partial_count = s->ntiles;
+    }
+    s->exp_valid = true;
+    return QAOA_OK;
+}
+
+template <typename real>
+qaoa_status expectation_impl(qaoa_state s, double* out_c, double* out_norm) {
+    qaoa_status st = compute_partials<real>(s);
+    if (st != QAOA_OK) return st;
+    finalize_kernel<<<1, 1024, 0, s->stream>>>(s->d_partials, s->partial_count, s->d_result);
+    CUDA_TRY(cudaGetLastError());
+    s->launches++;
+    CUDA_TRY(cudaMemcpyAsync(s->h_result, s->d_result, sizeof(double2), cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    if (out_c) *out_c = s->h_result->x;
+    if (out_norm) *out_norm = s->h_result->y;
+    return QAOA_OK;
+}
+
+void release(qaoa_state s) {
+    if (!s) return;
+    cudaSetDevice(s->dev);
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    for (auto& e : s->events) {
+        if (e.a) cudaEventDestroy(e.a);
+        if (e.b) cudaEventDestroy(e.b);
+    }
+    cudaFree(s->d_phase);
+    cudaFree(s->d_mix);
+    cudaFree(s->d_partials);
+    cudaFree(s->d_result);
+    if (s->h_result) cudaFreeHost(s->h_result);
+    delete s;
+}
+
+bool angles_ok(int p, const double* x) {
+    for (int k = 0; k < p; ++k)
+        if (!std::isfinite(x[k])) return false;
+    return true;
+}
+
+template <typename real>
+qaoa_status cut_table_impl(const HostGraph& hg, int prec, int group, int layout, uint16_t* host_out) {
+    const int n = hg.n;
+    const uint64_t dim = 1ull << n;
+    uint16_t* d_out = nullptr;
+    CUDA_TRY(cudaMalloc(&d_out, dim * sizeof(uint16_t)));
+    qaoa_state_s tmp;
+    tmp.n = n;
+    tmp.prec = prec;
+    tmp.dim = dim;
+    tmp.g = hg;
+    tmp.tc = tile_config_for(prec);
+    tmp.stream = nullptr;
+    qaoa_status st = QAOA_OK;
+    if (group < 0 && is_small(n, prec)) {
+        SmallJob j;
+        std::memset(&j, 0, sizeof(j));
+        j.n = n;
+        j.synth = 1;
+        j.cutval = 1;
+        j.E1 = hg.m + 1;
+        for (int v = 0; v < kMaxN; ++v) j.gmask[v] = v < n ? hg.upper[v] : 0;
+        j.cutout = d_out;
+        tmp.small = true;
+        tmp.dim = dim;
+        st = launch_small<real>(&tmp, j);
+    } else {
+        constexpr int Q = PrecTraits<real>::Q;
+        if (n < Q + 1) st = fail(QAOA_ERR_INVALID, "geometry cut table needs n > Q");
+        if (st == QAOA_OK) {
+            tmp.groups = make_groups(n, tmp.tc);
+            const int grp = group < 0 ? 0 : group;
+            if (grp >= (int)tmp.groups.size() || layout < 0 || layout > 2) {
+                st = fail(QAOA_ERR_INVALID, "no such group or layout");
+            } else {
+                tmp.ntiles = 1ull << (n - Q);
+                Plan plan = plan_readonly(n, tmp.tc, true, OP_CUTVAL, grp, layout);
+                TileArgs<Q> a;
+                std::memset(&a, 0, sizeof(a));
+                fill_program<real>(a, &tmp, plan.passes[0]);
+                a.cutout = d_out;
+                st = launch_tile<real>(&tmp, a, 0);
+            }
+        }
+    }
+    if (st == QAOA_OK) {
+        cudaError_t e = cudaMemcpy(host_out, d_out, dim * sizeof(uint16_t), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) st = cuda_fail(e, "cudaMemcpy(cut table)");
+    }
+    cudaFree(d_out);
+    return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t qaoa_state_bytes(int32_t n, qaoa_prec prec) {
+    if (n < 1 || n > kMaxN || (prec != QAOA_C64 && prec != QAOA_C128)) return 0;
+    return (size_t)1 << n << (prec == QAOA_C64 ? 3 : 4);
+}
+
+qaoa_status qaoa_state_init(const qaoa_graph* g, qaoa_prec prec, void* dev_buf, size_t buf_bytes,
+                            void* cuda_stream, qaoa_state* out) {
+    if (!out) return fail(QAOA_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (prec != QAOA_C64 && prec != QAOA_C128) return fail(QAOA_ERR_INVALID, "unknown precision");
+    HostGraph hg;
+    qaoa_status st = encode_graph(g, hg);
+    if (st != QAOA_OK) return st;
+    const size_t need = qaoa_state_bytes(hg.n, prec);
+    if (!dev_buf) return fail(QAOA_ERR_INVALID, "device buffer is NULL");
+    if (buf_bytes < need) return fail(QAOA_ERR_INVALID, "device buffer too small");
+    if (((uintptr_t)dev_buf & 15u) != 0) return fail(QAOA_ERR_INVALID, "device buffer not 16-byte aligned");
+
+    qaoa_state s = new (std::nothrow) qaoa_state_s;
+    if (!s) return fail(QAOA_ERR_OOM, "host allocation failed");
+    cudaGetDevice(&s->dev);
+    s->n = hg.n;
+    s->prec = prec;
+    s->dim = 1ull << hg.n;
+    s->buf = dev_buf;
+    s->stream = (cudaStream_t)cuda_stream;
+    s->g = hg;
+    s->tc = tile_config_for(prec);
+    s->small = is_small(hg.n, prec);
+    if (!s->small) {
+        s->groups = make_groups(hg.n, s->tc);
+        s->ntiles = 1ull << (hg.n - s->tc.Q);
+    }
+    const size_t eb = elem_bytes(prec);
+    cudaError_t e = cudaMalloc(&s->d_phase, (size_t)kLayerChunk * (hg.m + 1) * eb);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_mix, (size_t)kLayerChunk * eb);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_partials, (size_t)s->ntiles * sizeof(double2));
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_result, sizeof(double2));
+    if (e == cudaSuccess) e = cudaMallocHost(&s->h_result, sizeof(double2));
+    if (e != cudaSuccess) {
+        release(s);
+        cudaGetLastError();
+        return fail(QAOA_ERR_OOM, std::string("workspace allocation failed: ") + cudaGetErrorString(e));
+    }
+    s->lazy = true;
+    s->exp_valid = false;
+    *out = s;
+    return QAOA_OK;
+}
+
+qaoa_status qaoa_state_reset(qaoa_state s) {
+    if (!s) return fail(QAOA_ERR_INVALID, "state is NULL");
+    s->lazy = true;
+    s->exp_valid = false;
+    return QAOA_OK;
+}
+
+qaoa_status qaoa_apply_layers(qaoa_state s, int32_t p, const double* gamma, const double* beta) {
+    if (!s) return fail(QAOA_ERR_INVALID, "state is NULL");
+    if (p < 0) return fail(QAOA_ERR_INVALID, "p must be >= 0");
+    if (p > 0 && (!gamma || !beta)) return fail(QAOA_ERR_INVALID, "angle array is NULL");
+    if (!angles_ok(p, gamma) || !angles_ok(p, beta)) return fail(QAOA_ERR_INVALID, "non-finite angle");
+    CUDA_TRY(cudaSetDevice(s->dev));
+    if (p == 0) return s->prec == QAOA_C64 ? materialize<float>(s) : materialize<double>(s);
+    for (int k0 = 0; k0 < p; k0 += kLayerChunk) {
+        const int levels = std::min(kLayerChunk, p - k0);
+        const bool last = (k0 + levels == p);
+        qaoa_status st = s->prec == QAOA_C64 ? apply_chunk<float>(s, levels, gamma + k0, beta + k0, last)
+                                             : apply_chunk<double>(s, levels, gamma + k0, beta + k0, last);
+        if (st != QAOA_OK) return st;
+    }
+    return QAOA_OK;
+}
+
+qaoa_status qaoa_expectation(qaoa_state s, double* out_c, double* out_norm) {
+    if (!s) return fail(QAOA_ERR_INVALID, "state is NULL");
+    CUDA_TRY(cudaSetDevice(s->dev));
+    return s->prec == QAOA_C64 ? expectation_impl<float>(s, out_c, out_norm)
+                               : expectation_impl<double>(s, out_c, out_norm);
+}
+
+qaoa_status qaoa_state_copy_out(qaoa_state s, void* host_dst, size_t bytes) {
+    if (!s || !host_dst) return fail(QAOA_ERR_INVALID, "NULL argument");
+    const size_t need = qaoa_state_bytes(s->n, (qaoa_prec)s->prec);
+    if (bytes < need) return fail(QAOA_ERR_INVALID, "host buffer too small");
+    CUDA_TRY(cudaSetDevice(s->dev));
+    qaoa_status st = s->prec == QAOA_C64 ? materialize<float>(s) : materialize<double>(s);
+    if (st != QAOA_OK) return st;
+    CUDA_TRY(cudaMemcpyAsync(host_dst, s->buf, need, cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return QAOA_OK;
+}
+
+qaoa_status qaoa_state_free(qaoa_state s) {
+    release(s);
+    return QAOA_OK;
+}
+
+qaoa_status qaoa_cut_table(const qaoa_graph* g, uint16_t* host_out) {
+    if (!host_out) return fail(QAOA_ERR_INVALID, "host_out is NULL");
+    HostGraph hg;
+    qaoa_status st = encode_graph(g, hg);
+    if (st != QAOA_OK) return st;
+    if (hg.n > 30) return fail(QAOA_ERR_INVALID, "cut table limited to n <= 30");
+    return cut_table_impl<float>(hg, QAOA_C64, -1, 0, host_out);
+}
+
+qaoa_status qaoa_cut_table_geometry(const qaoa_graph* g, qaoa_prec prec, int32_t group, int32_t layout,
+                                    uint16_t* host_out) {
+    if (!host_out) return fail(QAOA_ERR_INVALID, "host_out is NULL");
+    if (prec != QAOA_C64 && prec != QAOA_C128) return fail(QAOA_ERR_INVALID, "unknown precision");
+    if (group < 0) return fail(QAOA_ERR_INVALID, "group must be >= 0");
+    HostGraph hg;
+    qaoa_status st = encode_graph(g, hg);
+    if (st != QAOA_OK) return st;
+    if (hg.n > 30) return fail(QAOA_ERR_INVALID, "cut table limited to n <= 30");
+    return prec == QAOA_C64 ? cut_table_impl<float>(hg, prec, group, layout, host_out)
+                            : cut_table_impl<double>(hg, prec, group, layout, host_out);
+}
+
+qaoa_status qaoa_plan_describe(int32_t n, qaoa_prec prec, int32_t p, int32_t* out, int32_t cap, int32_t* count) {
+    if (n < 1 || n > kMaxN || p < 0 || !count) return fail(QAOA_ERR_INVALID, "bad argument");
+    if (prec != QAOA_C64 && prec != QAOA_C128) return fail(QAOA_ERR_INVALID, "unknown precision");
+    if (is_small(n, prec)) {
+        *count = 0;
+        return QAOA_OK;
+    }
+    std::vector<int32_t> d;
+    try {
+        Plan plan = plan_levels(n, tile_config_for(prec), p, true, true);
+        d = describe(plan);
+    } catch (const std::exception& ex) {
+        return fail(QAOA_ERR_INVALID, ex.what());
+    }
+    *count = (int32_t)d.size();
+    if (out)
+        for (int32_t i = 0; i < std::min<int32_t>(cap, (int32_t)d.size()); ++i) out[i] = d[i];
+    return QAOA_OK;
+}
+
+qaoa_status qaoa_profile_enable(qaoa_state s, int32_t enable) {
+    if (!s) return fail(QAOA_ERR_INVALID, "state is NULL");
+    s->prof = enable != 0;
+    s->ev_used = 0;
+    s->launches = 0;
+    return QAOA_OK;
+}
+
+qaoa_status qaoa_profile_read(qaoa_state s, qaoa_profile_stats* out) {
+    if (!s || !out) return fail(QAOA_ERR_INVALID, "NULL argument");
+    CUDA_TRY(cudaSetDevice(s->dev));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    std::memset(out, 0, sizeof(*out));
+    out->kernel_launches = s->launches;
+    const double eb = (double)elem_bytes(s->prec);
+    for (size_t i = 0; i < s->ev_used; ++i) {
+        float ms = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&ms, s->events[i].a, s->events[i].b));
+        if (s->events[i].kind == 1) {
+            out->pass_launches++;
+            out->pass_ms += ms;
+            out->pass_bytes += 2.0 * eb * (double)s->dim;
+        } else if (s->events[i].kind == 2) {
+            out->synth_launches++;
+            out->synth_ms += ms;
+            out->synth_bytes += eb * (double)s->dim;
+        }
+    }
+    return QAOA_OK;
+}
+
+const char* qaoa_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,573 @@
+// kernels.cuh -- sm_103a device code of the QAOA layer.
+//
+// Kernels:
+//   coeff_kernel   per level k: phase table T_k[c] = exp(-i gamma_k c), c = 0..|E| (FP64
+//                  sincos, rounded to the state precision) and the mixer pair (cos b, sin b).
+//   tile_kernel    one pass over the state in tiles of 2^Q amplitudes (see plan.h): loads a
+//                  tile (or synthesises |+>^n), runs the pass program (RX butterflies in
+//                  registers, register-layout exchanges through swizzled shared memory, the
+//                  cost phase with the on-the-fly cut count, the <C> reduction) and stores.
+//   small_kernel   a whole state of n <= Q_small qubits in shared memory, all levels in one
+//                  launch; one CTA per state, so many small states share a launch.
+//   finalize_kernel fixed-order FP64 sum of the per-tile partials of <C> and the norm.
+//   fill_kernel    writes |+>^n when a deferred initial state has to be materialised.
+//
+// On-the-fly cut count (bit-exact integer arithmetic, Algorithm 3 re-associated).  For a
+// tile, split the index z into outer bits o (fixed per CTA) and the tile's local bits l.  With
+// K = C(o|0), e_u = d_u^out - 2 a_u(o) (d_u^out = neighbours of local bit u outside the tile,
+// a_u(o) = those set in o) and C_S the cut count of the tile-internal edges,
+//     C(o|l) = K + C_S(l) + sum over set bits u of l of e_u.
+// Inside a thread, l = tau | x (tau = thread bits, x = 2^R register bits), and the same split
+// once more gives  C = base(tau) + sum_{j: x_j = 1} s_j(tau) + C_R(x), where C_R(x) is a
+// 2^R-entry table of the register bits' internal edges.  K and e_u cost one popcount per
+// vertex per CTA, base and s_j about Q + R popcounts per thread, and each amplitude two
+// integer adds.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "plan.h"
+
+namespace qaoa {
+
+template <typename real>
+struct C2T;
+template <>
+struct C2T<float> {
+    using type = float2;
+};
+template <>
+struct C2T<double> {
+    using type = double2;
+};
+
+__device__ __forceinline__ float2 make_c2(float x, float y) { return make_float2(x, y); }
+__device__ __forceinline__ double2 make_c2(double x, double y) { return make_double2(x, y); }
+
+template <int Q>
+struct TileArgs {
+    int32_t n, cprime, g0, nops;
+    int32_t E1;        // entries per phase table (|E| + 1)
+    int32_t need_cut;  // program evaluates C(z)
+    double init_amp;   // 2^(-n/2)
+    uint64_t gmask[kMaxN];  // graph_I rows (Table 1): bit v of gmask[u] iff edge (u, v), v > u
+    uint32_t locUpper[Q];   // tile-internal upper neighbours of local bit u (local bit order)
+    uint32_t locAdj[Q];     // all tile-internal neighbours of local bit u
+    uint64_t outAdj[Q];     // neighbours of local bit u outside the tile (global positions)
+    uint8_t crtab[3][32];   // C_R(x) per register layout
+    Op ops[kMaxOps];
+    void* state;
+    const void* phase;   // [level][E1] complex<real>
+    const void* mix;     // [level] (cos beta, sin beta) as complex<real>
+    double2* partials;   // [tile] (sum |psi|^2 C, sum |psi|^2)
+    uint16_t* cutout;    // [2^n] cut values (OP_CUTVAL)
+};
+
+struct SmallJob {
+    int32_t n, levels, E1;
+    int32_t synth, expect, cutval, store;
+    double init_amp;
+    uint64_t gmask[kMaxN];
+    void* state;
+    const void* phase;
+    const void* mix;
+    double2* partials;  // one entry
+    uint16_t* cutout;
+};
+
+struct CoeffArgs {
+    int32_t levels, E1;
+    double gamma[kLayerChunk];
+    double beta[kLayerChunk];
+    void* phase;
+    void* mix;
+};
+
+// ---------------------------------------------------------------------------------- helpers
+
+template <typename C2>
+__device__ __forceinline__ C2 cmul(C2 a, C2 b) {
+    return make_c2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// RX(2 beta) = [[c, -i s], [-i s, c]] on the pair (a, b) = (bit 0, bit 1).
+template <typename C2, typename real>
+__device__ __forceinline__ void rx_pair(C2& a, C2& b, real c, real s) {
+    const C2 a0 = a, b0 = b;
+    a = make_c2(c * a0.x + s * b0.y, c * a0.y - s * b0.x);
+    b = make_c2(c * b0.x + s * a0.y, c * b0.y - s * a0.x);
+}
+
+__device__ __forceinline__ int warp_sum_int(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum_double(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Alg. 3 cut count of z over all n vertices (graph_I rows in `gm`).
+__device__ __forceinline__ int cut_count_full(const uint64_t* gm, int n, uint64_t z) {
+    int c = 0;
+    for (int v = 0; v < n; ++v) {
+        const uint64_t bI = 0ull - ((z >> v) & 1ull);
+        c += __popcll(gm[v] & (bI ^ z));
+    }
+    return c;
+}
+
+// ---------------------------------------------------------------------------------- tile pass
+
+template <typename real, int Q, int R>
+struct Tile {
+    using C2 = typename C2T<real>::type;
+    static constexpr int NT = 1 << (Q - R);
+    static constexpr int NE = 1 << R;
+    // swizzle shift: 8-byte elements are conflict-free per half warp, 16-byte per quarter warp
+    static constexpr int SW = sizeof(C2) == 8 ? 5 : 4;
+
+    static __host__ __device__ constexpr int rlo(int L) { return L == 0 ? Q - R : (L == 1 ? Q - 2 * R : 0); }
+    static __host__ __device__ constexpr uint32_t swz(uint32_t l) { return l ^ ((l >> SW) & 31u); }
+
+    // local bits of thread `tid` in layout L (register bits zero)
+    static __device__ __forceinline__ uint32_t tbits(int L, uint32_t tid) {
+        if (L == 0) return tid;
+        if (L == 1) {
+            constexpr int lo = Q - 2 * R;
+            return (tid & ((1u << lo) - 1u)) | ((tid >> lo) << (Q - R));
+        }
+        return tid << R;
+    }
+
+    struct Ctx {
+        uint64_t zb;  // outer bits of the tile
+        int K;
+        const TileArgs<Q>* a;
+        int* sE;
+        C2* tile;
+    };
+
+    static __device__ __forceinline__ uint64_t gofs(const TileArgs<Q>& a, uint32_t l) {
+        const uint32_t cm = (1u << a.cprime) - 1u;
+        return (uint64_t)(l & cm) | ((uint64_t)(l >> a.cprime) << a.g0);
+    }
+
+    template <int L>
+    static __device__ __forceinline__ void strides(const TileArgs<Q>& a, uint64_t (&st)[R]) {
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            const int u = rlo(L) + j;
+            st[j] = u < a.cprime ? (1ull << u) : (1ull << (a.g0 + u - a.cprime));
+        }
+    }
+
+    template <int x>
+    static __device__ __forceinline__ uint64_t xoff(const uint64_t (&st)[R]) {
+        uint64_t o = 0;
+#pragma unroll
+        for (int j = 0; j < R; ++j)
+            if ((x >> j) & 1) o += st[j];
+        return o;
+    }
+
+    template <int L>
+    static __device__ __forceinline__ void load(C2 (&v)[NE], const Ctx& c, uint32_t tid) {
+        const TileArgs<Q>& a = *c.a;
+        const C2* __restrict__ g = reinterpret_cast<const C2*>(a.state) + c.zb + gofs(a, tbits(L, tid));
+        uint64_t st[R];
+        strides<L>(a, st);
+#pragma unroll
+        for (int x = 0; x < NE; ++x) {
+            uint64_t o = 0;
+#pragma unroll
+            for (int j = 0; j < R; ++j)
+                if ((x >> j) & 1) o += st[j];
+            v[x] = g[o];
+        }
+    }
+
+    template <int L>
+    static __device__ __forceinline__ void store(const C2 (&v)[NE], const Ctx& c, uint32_t tid) {
+        const TileArgs<Q>& a = *c.a;
+        C2* __restrict__ g = reinterpret_cast<C2*>(a.state) + c.zb + gofs(a, tbits(L, tid));
+        uint64_t st[R];
+        strides<L>(a, st);
+#pragma unroll
+        for (int x = 0; x < NE; ++x) {
+            uint64_t o = 0;
+#pragma unroll
+            for (int j = 0; j < R; ++j)
+                if ((x >> j) & 1) o += st[j];
+            g[o] = v[x];
+        }
+    }
+
+    template <int L>
+    static __device__ __forceinline__ void to_smem(const C2 (&v)[NE], C2* tile, uint32_t tid) {
+        const uint32_t P = swz(tbits(L, tid));
+#pragma unroll
+        for (int x = 0; x < NE; ++x) tile[P ^ swz((uint32_t)x << rlo(L))] = v[x];
+    }
+
+    template <int L>
+    static __device__ __forceinline__ void from_smem(C2 (&v)[NE], const C2* tile, uint32_t tid) {
+        const uint32_t P = swz(tbits(L, tid));
+#pragma unroll
+        for (int x = 0; x < NE; ++x) v[x] = tile[P ^ swz((uint32_t)x << rlo(L))];
+    }
+
+    // base(tau) and slopes s_j of the on-the-fly cut count in layout L
+    template <int L>
+    static __device__ __forceinline__ int cut_setup(const Ctx& c, uint32_t tid, int (&s)[R]) {
+        const TileArgs<Q>& a = *c.a;
+        const uint32_t tau = tbits(L, tid);
+        int cs = 0, e = 0;
+#pragma unroll
+        for (int u = 0; u < Q; ++u) {
+            const uint32_t bit = (tau >> u) & 1u;
+            cs += __popc(a.locUpper[u] & (tau ^ (0u - bit)));
+            e += bit ? c.sE[u] : 0;
+        }
+        constexpr uint32_t RM = ((1u << R) - 1u) << rlo(L);
+        constexpr uint32_t TM = ((1u << Q) - 1u) & ~RM;
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            const int u = rlo(L) + j;
+            s[j] = c.sE[u] + __popc(a.locAdj[u] & TM) - 2 * __popc(a.locAdj[u] & tau);
+        }
+        return c.K + cs + e;
+    }
+
+    template <int x>
+    static __device__ __forceinline__ int cut_at(int base, const int (&s)[R], const uint8_t* cr) {
+        int cidx = base + cr[x];
+#pragma unroll
+        for (int j = 0; j < R; ++j)
+            if ((x >> j) & 1) cidx += s[j];
+        return cidx;
+    }
+
+    template <int L>
+    static __device__ __forceinline__ void phase(C2 (&v)[NE], const Ctx& c, uint32_t tid, int level) {
+        const TileArgs<Q>& a = *c.a;
+        int s[R];
+        const int base = cut_setup<L>(c, tid, s);
+        const C2* __restrict__ T = reinterpret_cast<const C2*>(a.phase) + (size_t)level * a.E1;
+#pragma unroll
+        for (int x = 0; x < NE; ++x) {
+            int cidx = base + a.crtab[L][x];
+#pragma unroll
+            for (int j = 0; j < R; ++j)
+                if ((x >> j) & 1) cidx += s[j];
+            // the count is always in [0, |E|]; the unsigned clamp keeps every table read in bounds
+            v[x] = cmul(v[x], __ldg(T + min((unsigned)cidx, (unsigned)(a.E1 - 1))));
+        }
+    }
+
+    template <int L>
+    static __device__ __forceinline__ void expect(const C2 (&v)[NE], const Ctx& c, uint32_t tid,
+                                                  double& accC, double& accN) {
+        const TileArgs<Q>& a = *c.a;
+        int s[R];
+        const int base = cut_setup<L>(c, tid, s);
+        real sc = 0, sn = 0;
+#pragma unroll
+        for (int x = 0; x < NE; ++x) {
+            int cidx = base + a.crtab[L][x];
+#pragma unroll
+            for (int j = 0; j < R; ++j)
+                if ((x >> j) & 1) cidx += s[j];
+            const real p = v[x].x * v[x].x + v[x].y * v[x].y;
+            sn += p;
+            sc += p * (real)cidx;
+        }
+        accC += (double)sc;
+        accN += (double)sn;
+    }
+
+    template <int L>
+    static __device__ __forceinline__ void cutval(const Ctx& c, uint32_t tid) {
+        const TileArgs<Q>& a = *c.a;
+        int s[R];
+        const int base = cut_setup<L>(c, tid, s);
+        uint16_t* __restrict__ g = a.cutout + c.zb + gofs(a, tbits(L, tid));
+        uint64_t st[R];
+        strides<L>(a, st);
+#pragma unroll
+        for (int x = 0; x < NE; ++x) {
+            int cidx = base + a.crtab[L][x];
+            uint64_t o = 0;
+#pragma unroll
+            for (int j = 0; j < R; ++j)
+                if ((x >> j) & 1) {
+                    cidx += s[j];
+                    o += st[j];
+                }
+            g[o] = (uint16_t)cidx;
+        }
+    }
+
+    static __device__ __forceinline__ void rx(C2 (&v)[NE], uint32_t mask, real cb, real sb) {
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            if (mask & (1u << j)) {
+#pragma unroll
+                for (int x = 0; x < NE; ++x)
+                    if (!(x & (1 << j))) rx_pair(v[x], v[x | (1 << j)], cb, sb);
+            }
+        }
+    }
+};
+
+template <typename real, int Q, int R>
+__global__ void __launch_bounds__(1 << (Q - R), 2) tile_kernel(const __grid_constant__ TileArgs<Q> a) {
+    using T = Tile<real, Q, R>;
+    using C2 = typename T::C2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int sE[Q];
+    __shared__ int sK;
+    __shared__ double sred[2][T::NT / 32];
+
+    C2* tile = reinterpret_cast<C2*>(smem_raw);
+    const uint32_t tid = threadIdx.x;
+    const uint64_t t = blockIdx.x;
+    const int nb = a.g0 - a.cprime;
+    const uint64_t zb = ((t & ((1ull << nb) - 1ull)) << a.cprime) | ((t >> nb) << (a.g0 + Q - a.cprime));
+
+    if (a.need_cut) {
+        if (tid < 32) {
+            int acc = 0;
+            for (int v = (int)tid; v < a.n; v += 32) {
+                const uint64_t bI = 0ull - ((zb >> v) & 1ull);
+                acc += __popcll(a.gmask[v] & (bI ^ zb));
+            }
+            acc = warp_sum_int(acc);
+            if (tid == 0) sK = acc;
+            if (tid < (uint32_t)Q) sE[tid] = __popcll(a.outAdj[tid]) - 2 * __popcll(a.outAdj[tid] & zb);
+        }
+        __syncthreads();
+    }
+
+    typename T::Ctx c;
+    c.zb = zb;
+    c.K = a.need_cut ? sK : 0;
+    c.a = &a;
+    c.sE = sE;
+    c.tile = tile;
+
+    C2 v[T::NE];
+    int L = 0;
+    double accC = 0.0, accN = 0.0;
+    bool did_expect = false;
+
+    for (int i = 0; i < a.nops; ++i) {
+        const Op op = a.ops[i];
+        switch (op.kind) {
+            case OP_SYNTH: {
+                const real amp = (real)a.init_amp;
+#pragma unroll
+                for (int x = 0; x < T::NE; ++x) v[x] = make_c2(amp, (real)0);
+                L = op.layout;
+                break;
+            }
+            case OP_LOAD:
+                L = op.layout;
+                if (L == 0) T::template load<0>(v, c, tid);
+                else if (L == 1) T::template load<1>(v, c, tid);
+                else T::template load<2>(v, c, tid);
+                break;
+            case OP_XCHG:
+                __syncthreads();
+                if (L == 0) T::template to_smem<0>(v, tile, tid);
+                else if (L == 1) T::template to_smem<1>(v, tile, tid);
+                else T::template to_smem<2>(v, tile, tid);
+                __syncthreads();
+                L = op.layout;
+                if (L == 0) T::template from_smem<0>(v, tile, tid);
+                else if (L == 1) T::template from_smem<1>(v, tile, tid);
+                else T::template from_smem<2>(v, tile, tid);
+                break;
+            case OP_RX: {
+                const C2 cs = reinterpret_cast<const C2*>(a.mix)[op.arg];
+                T::rx(v, op.mask, cs.x, cs.y);
+                break;
+            }
+            case OP_PHASE:
+                if (L == 0) T::template phase<0>(v, c, tid, op.arg);
+                else if (L == 1) T::template phase<1>(v, c, tid, op.arg);
+                else T::template phase<2>(v, c, tid, op.arg);
+                break;
+            case OP_EXPECT:
+                did_expect = true;
+                if (L == 0) T::template expect<0>(v, c, tid, accC, accN);
+                else if (L == 1) T::template expect<1>(v, c, tid, accC, accN);
+                else T::template expect<2>(v, c, tid, accC, accN);
+                break;
+            case OP_CUTVAL:
+                if (L == 0) T::template cutval<0>(c, tid);
+                else if (L == 1) T::template cutval<1>(c, tid);
+                else T::template cutval<2>(c, tid);
+                break;
+            case OP_STORE:
+                if (L == 0) T::template store<0>(v, c, tid);
+                else if (L == 1) T::template store<1>(v, c, tid);
+                else T::template store<2>(v, c, tid);
+                break;
+            default:
+                break;
+        }
+    }
+
+    if (did_expect) {
+        accC = warp_sum_double(accC);
+        accN = warp_sum_double(accN);
+        if ((tid & 31u) == 0) {
+            sred[0][tid >> 5] = accC;
+            sred[1][tid >> 5] = accN;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double sc = 0.0, sn = 0.0;
+            for (int w = 0; w < T::NT / 32; ++w) {
+                sc += sred[0][w];
+                sn += sred[1][w];
+            }
+            a.partials[t] = make_double2(sc, sn);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------- small states
+
+constexpr int kSmallThreads = 512;
+
+template <typename real>
+__device__ __forceinline__ void small_body(const SmallJob& j) {
+    using C2 = typename C2T<real>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C2* st = reinterpret_cast<C2*>(smem_raw);
+    __shared__ uint64_t gm[kMaxN];
+    __shared__ double sred[2][kSmallThreads / 32];
+    const int n = j.n;
+    const uint32_t dim = 1u << n;
+    const uint32_t tid = threadIdx.x;
+    if (tid < (uint32_t)n) gm[tid] = j.gmask[tid];
+    C2* gstate = reinterpret_cast<C2*>(j.state);
+    for (uint32_t z = tid; z < dim; z += kSmallThreads)
+        st[z] = j.synth ? make_c2((real)j.init_amp, (real)0) : gstate[z];
+    __syncthreads();
+
+    const C2* mix = reinterpret_cast<const C2*>(j.mix);
+    for (int k = 0; k < j.levels; ++k) {
+        const C2* T = reinterpret_cast<const C2*>(j.phase) + (size_t)k * j.E1;
+        for (uint32_t z = tid; z < dim; z += kSmallThreads) st[z] = cmul(st[z], __ldg(T + cut_count_full(gm, n, z)));
+        const C2 cs = mix[k];
+        for (int q = 0; q < n; ++q) {
+            __syncthreads();
+            for (uint32_t i = tid; i < dim / 2; i += kSmallThreads) {
+                const uint32_t lo = i & ((1u << q) - 1u);
+                const uint32_t za = ((i >> q) << (q + 1)) | lo;
+                rx_pair(st[za], st[za | (1u << q)], cs.x, cs.y);
+            }
+        }
+        __syncthreads();
+    }
+
+    if (j.cutval)
+        for (uint32_t z = tid; z < dim; z += kSmallThreads) j.cutout[z] = (uint16_t)cut_count_full(gm, n, z);
+
+    if (j.expect) {
+        double sc = 0.0, sn = 0.0;
+        for (uint32_t z = tid; z < dim; z += kSmallThreads) {
+            const double p = (double)st[z].x * (double)st[z].x + (double)st[z].y * (double)st[z].y;
+            sn += p;
+            sc += p * (double)cut_count_full(gm, n, z);
+        }
+        sc = warp_sum_double(sc);
+        sn = warp_sum_double(sn);
+        if ((tid & 31u) == 0) {
+            sred[0][tid >> 5] = sc;
+            sred[1][tid >> 5] = sn;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double a = 0.0, b = 0.0;
+            for (int w = 0; w < kSmallThreads / 32; ++w) {
+                a += sred[0][w];
+                b += sred[1][w];
+            }
+            j.partials[0] = make_double2(a, b);
+        }
+    }
+    if (j.store)
+        for (uint32_t z = tid; z < dim; z += kSmallThreads) gstate[z] = st[z];
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kSmallThreads) small_kernel(const __grid_constant__ SmallJob j) {
+    small_body<real>(j);
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kSmallThreads) small_batch_kernel(const SmallJob* __restrict__ jobs) {
+    small_body<real>(jobs[blockIdx.x]);
+}
+
+// ---------------------------------------------------------------------------------- coefficients
+
+template <typename real>
+__global__ void coeff_kernel(const __grid_constant__ CoeffArgs a) {
+    using C2 = typename C2T<real>::type;
+    const int k = blockIdx.y;
+    C2* T = reinterpret_cast<C2*>(a.phase) + (size_t)k * a.E1;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < a.E1; c += gridDim.x * blockDim.x) {
+        double s, co;
+        sincos(a.gamma[k] * (double)c, &s, &co);
+        T[c] = make_c2((real)co, (real)(-s));
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        double s, co;
+        sincos(a.beta[k], &s, &co);
+        reinterpret_cast<C2*>(a.mix)[k] = make_c2((real)co, (real)s);
+    }
+}
+
+// ---------------------------------------------------------------------------------- reductions / fill
+
+__global__ void __launch_bounds__(1024) finalize_kernel(const double2* __restrict__ partials, uint64_t count,
+                                                        double2* __restrict__ out) {
+    __shared__ double sc[1024], sn[1024];
+    double a = 0.0, b = 0.0;
+    for (uint64_t i = threadIdx.x; i < count; i += 1024) {
+        const double2 p = partials[i];
+        a += p.x;
+        b += p.y;
+    }
+    sc[threadIdx.x] = a;
+    sn[threadIdx.x] = b;
+    __syncthreads();
+    for (int s = 512; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) {
+            sc[threadIdx.x] += sc[threadIdx.x + s];
+            sn[threadIdx.x] += sn[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = make_double2(sc[0], sn[0]);
+}
+
+template <typename real>
+__global__ void fill_kernel(void* state, uint64_t dim, double amp) {
+    using C2 = typename C2T<real>::type;
+    C2* s = reinterpret_cast<C2*>(state);
+    const C2 val = make_c2((real)amp, (real)0);
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < dim; i += (uint64_t)gridDim.x * blockDim.x)
+        s[i] = val;
+}
+
+}  // namespace qaoa

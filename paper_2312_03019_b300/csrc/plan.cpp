@@ -1,0 +1,214 @@
+// plan.cpp -- host-side planning of the state passes (see plan.h).
+#include "plan.h"
+
+#include <algorithm>
+#include <array>
+#include <climits>
+#include <stdexcept>
+
+namespace qaoa {
+
+TileConfig tile_config_for(int prec) {
+    // complex64: 2^13 amplitudes x 8 B = 64 KiB tile, 32 amplitudes per thread, 256 threads,
+    //            high-group rows of >= 2^3 amplitudes (64 B).
+    // complex128: 2^12 x 16 B = 64 KiB tile, 16 amplitudes per thread, 256 threads,
+    //            high-group rows of >= 2^4 amplitudes (256 B).
+    if (prec == 0) return TileConfig{13, 5, 3};
+    return TileConfig{12, 4, 4};
+}
+
+std::vector<Group> make_groups(int n, const TileConfig& tc) {
+    std::vector<Group> g;
+    g.push_back(Group{0, std::min(n, tc.Q)});
+    int rest = n - tc.Q;
+    if (rest > 0) {
+        const int cap = tc.Q - tc.cmin;
+        const int ng = (rest + cap - 1) / cap;
+        const int base = rest / ng, extra = rest % ng;
+        int lo = tc.Q;
+        for (int i = 0; i < ng; ++i) {
+            // larger groups go last (highest bits): their rows are shortest, the others' longest
+            const int sz = base + (i >= ng - extra ? 1 : 0);
+            g.push_back(Group{lo, sz});
+            lo += sz;
+        }
+    }
+    return g;
+}
+
+Geometry group_geometry(const Group& g, const TileConfig& tc) {
+    if (g.lo == 0) return Geometry{tc.Q, tc.Q};
+    return Geometry{tc.Q - g.size, g.lo};
+}
+
+uint32_t group_target_mask(const Group& g, const TileConfig& tc) {
+    const uint32_t all = (1u << tc.Q) - 1u;
+    if (g.lo == 0) return all;
+    const Geometry geo = group_geometry(g, tc);
+    return all & ~((1u << geo.cprime) - 1u);
+}
+
+Plan plan_levels(int n, const TileConfig& tc, int levels, bool synth_first, bool expect_last) {
+    Plan plan;
+    plan.n = n;
+    plan.tc = tc;
+    plan.groups = make_groups(n, tc);
+    const int g = (int)plan.groups.size();
+    for (int k = 0; k < levels; ++k) {
+        for (int idx = 0; idx < g; ++idx) {
+            const int grp = (k % 2 == 0) ? idx : g - 1 - idx;
+            if (idx == 0 && k > 0) {
+                // same group as the last pass of level k-1: fuse phase + mixer into it
+                Pass& cur = plan.passes.back();
+                cur.lops.push_back(LOp{OP_PHASE, k});
+                cur.lops.push_back(LOp{OP_RX, k});
+                continue;
+            }
+            Pass ps;
+            ps.group = grp;
+            ps.synth = (k == 0 && idx == 0) ? synth_first : false;
+            ps.store = true;
+            if (idx == 0) ps.lops.push_back(LOp{OP_PHASE, k});
+            ps.lops.push_back(LOp{OP_RX, k});
+            plan.passes.push_back(ps);
+        }
+    }
+    if (expect_last && !plan.passes.empty()) plan.passes.back().lops.push_back(LOp{OP_EXPECT, 0});
+    assign_layouts(plan);
+    return plan;
+}
+
+Plan plan_readonly(int n, const TileConfig& tc, bool synth, uint8_t kind, int group, int layout) {
+    Plan plan;
+    plan.n = n;
+    plan.tc = tc;
+    plan.groups = make_groups(n, tc);
+    Pass ps;
+    ps.group = group;
+    ps.synth = synth;
+    ps.store = false;
+    ps.lops.push_back(LOp{kind, 0});
+    ps.ops.push_back(Op{(uint8_t)(synth ? OP_SYNTH : OP_LOAD), (uint8_t)layout, 0, 0});
+    ps.ops.push_back(Op{kind, (uint8_t)layout, 0, 0});
+    plan.passes.push_back(ps);
+    return plan;
+}
+
+namespace {
+
+struct Choice {
+    int cost = INT_MAX;
+    std::vector<Op> ops;
+};
+
+// All ordered sequences of distinct layouts whose register bits cover `target`, each layout
+// adding at least one new bit.
+std::vector<std::vector<int>> cover_sequences(const TileConfig& tc, uint32_t target) {
+    std::vector<std::vector<int>> out;
+    for (int subset = 1; subset < 8; ++subset) {
+        std::vector<int> seq;
+        for (int L = 0; L < 3; ++L)
+            if ((subset >> L) & 1) seq.push_back(L);
+        do {
+            uint32_t covered = 0;
+            bool useful = true;
+            for (int L : seq) {
+                const uint32_t add = tc.regMask(L) & target & ~covered;
+                if (!add) useful = false;
+                covered |= add;
+            }
+            if (useful && covered == target) out.push_back(seq);
+        } while (std::next_permutation(seq.begin(), seq.end()));
+    }
+    return out;
+}
+
+}  // namespace
+
+void assign_layouts(Plan& plan) {
+    const TileConfig& tc = plan.tc;
+    for (Pass& ps : plan.passes) {
+        if (!ps.ops.empty()) continue;  // prebuilt (read-only passes)
+        const uint32_t target = group_target_mask(plan.groups[ps.group], tc);
+        const auto seqs = cover_sequences(tc, target);
+        if (seqs.empty()) throw std::runtime_error("no layout cover for mixer group");
+        // DP over the logical ops with state = current layout
+        std::array<Choice, 3> st;
+        for (int s = 0; s < 2; ++s) {  // programs start in a coalesced layout
+            st[s].cost = 0;
+            st[s].ops.push_back(Op{(uint8_t)(ps.synth ? OP_SYNTH : OP_LOAD), (uint8_t)s, 0, 0});
+        }
+        for (const LOp& lo : ps.lops) {
+            std::array<Choice, 3> nx;
+            for (int cur = 0; cur < 3; ++cur) {
+                if (st[cur].cost == INT_MAX) continue;
+                if (lo.kind != OP_RX) {
+                    Choice c = st[cur];
+                    c.ops.push_back(Op{lo.kind, (uint8_t)cur, 0, lo.arg});
+                    if (c.cost < nx[cur].cost) nx[cur] = c;
+                    continue;
+                }
+                for (const auto& seq : seqs) {
+                    Choice c = st[cur];
+                    int L = cur;
+                    uint32_t covered = 0;
+                    for (int nl : seq) {
+                        if (nl != L) {
+                            c.ops.push_back(Op{OP_XCHG, (uint8_t)nl, 0, 0});
+                            c.cost += 1;
+                            L = nl;
+                        }
+                        const uint32_t add = tc.regMask(L) & target & ~covered;
+                        covered |= add;
+                        c.ops.push_back(Op{OP_RX, (uint8_t)L, (uint16_t)(add >> tc.regLo(L)), lo.arg});
+                    }
+                    if (c.cost < nx[L].cost) nx[L] = c;
+                }
+            }
+            st = nx;
+        }
+        // finish in a coalesced layout when storing
+        Choice best;
+        for (int cur = 0; cur < 3; ++cur) {
+            if (st[cur].cost == INT_MAX) continue;
+            Choice c = st[cur];
+            int L = cur;
+            if (ps.store) {
+                if (L == 2) {
+                    c.ops.push_back(Op{OP_XCHG, 0, 0, 0});
+                    c.cost += 1;
+                    L = 0;
+                }
+                c.ops.push_back(Op{OP_STORE, (uint8_t)L, 0, 0});
+            }
+            if (c.cost < best.cost) best = c;
+        }
+        if ((int)best.ops.size() > kMaxOps) throw std::runtime_error("pass program too long");
+        ps.ops = best.ops;
+    }
+}
+
+std::vector<int32_t> describe(const Plan& plan) {
+    std::vector<int32_t> d;
+    d.push_back(plan.tc.Q);
+    d.push_back(plan.tc.R);
+    d.push_back(plan.tc.cmin);
+    d.push_back((int32_t)plan.groups.size());
+    for (const Group& g : plan.groups) {
+        d.push_back(g.lo);
+        d.push_back(g.size);
+    }
+    d.push_back((int32_t)plan.passes.size());
+    for (const Pass& ps : plan.passes) {
+        d.push_back(ps.group);
+        d.push_back((int32_t)ps.ops.size());
+        for (const Op& op : ps.ops) {
+            d.push_back(op.kind);
+            d.push_back((op.kind == OP_RX || op.kind == OP_PHASE) ? op.arg : op.layout);
+            d.push_back(op.kind == OP_RX ? (int32_t)(op.mask << plan.tc.regLo(op.layout)) : 0);
+        }
+    }
+    return d;
+}
+
+}  // namespace qaoa

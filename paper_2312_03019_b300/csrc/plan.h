@@ -1,0 +1,119 @@
+// plan.h -- host-side planning of the state passes (no CUDA dependency).
+//
+// A QAOA level is a diagonal cost phase (Eq. UC_opt) followed by RX on every qubit (the mixer
+// layer of Algorithm 1).  On the GPU the 2^n amplitudes are processed in tiles of 2^Q
+// amplitudes held in shared memory.  A tile covers Q index bits ("local bits"): the lowest
+// c' global bits (contiguous rows of 2^c' amplitudes, for coalesced HBM access) plus one
+// "mixer group" of Q - c' higher global bits.  One pass streams the whole state once through
+// such tiles and applies, inside each tile, the RX gates of the group's qubits; single-qubit
+// RX gates on different qubits commute and the cost phase is elementwise, so a level is
+// ceil-many passes over groups that together cover all n qubits.
+//
+// Consecutive levels alternate the group order (0,1,..,g-1 then g-1,..,0), so the last
+// group of level k is the first group of level k+1: one pass then applies RX(level k) on
+// that group, the phase of level k+1 and RX(level k+1) on the same group.  A run of p levels
+// costs p*(g-1)+1 passes instead of p*g.
+//
+// Inside a tile each thread holds 2^R amplitudes in registers.  Three register layouts
+// assign R of the Q local bits to the register index (where the RX butterflies are computed
+// in registers); exchanges through shared memory switch between layouts:
+//   layout 0: register bits [Q-R, Q), thread bits [0, Q-R)
+//   layout 1: register bits [Q-2R, Q-R), thread bits [0, Q-2R) + [Q-R, Q)
+//   layout 2: register bits [0, R),      thread bits [R, Q)
+// The first five thread bits are the lane bits.  Layouts 0 and 1 keep lanes on the lowest
+// local bits, so global loads and stores from them are coalesced.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace qaoa {
+
+constexpr int kMaxN = 34;
+constexpr int kMaxOps = 48;
+constexpr int kLayerChunk = 64;  // levels per coefficient table upload
+
+enum OpKind : uint8_t {
+    OP_NONE = 0,
+    OP_LOAD = 1,
+    OP_SYNTH = 2,
+    OP_XCHG = 3,
+    OP_RX = 4,
+    OP_PHASE = 5,
+    OP_EXPECT = 6,
+    OP_STORE = 7,
+    OP_CUTVAL = 8,
+};
+
+struct Op {
+    uint8_t kind;
+    uint8_t layout;  // layout after this op (LOAD/SYNTH/XCHG), or current layout
+    uint16_t mask;   // RX: register-bit mask (bits of the register index)
+    int32_t arg;     // RX/PHASE: level index within the chunk
+};
+
+struct TileConfig {
+    int Q;     // local bits per tile
+    int R;     // register bits per thread
+    int cmin;  // minimum contiguous row bits in a high-group pass
+    int regLo(int layout) const { return layout == 0 ? Q - R : (layout == 1 ? Q - 2 * R : 0); }
+    uint32_t regMask(int layout) const { return ((1u << R) - 1u) << regLo(layout); }
+    int threads() const { return 1 << (Q - R); }
+};
+
+TileConfig tile_config_for(int prec /*0 = c64, 1 = c128*/);
+
+struct Group {
+    int lo;    // first global qubit of the group
+    int size;  // number of qubits
+};
+
+struct Geometry {
+    int cprime;  // local bits [0, c') = global bits [0, c')
+    int g0;      // local bit c' + j = global bit g0 + j
+};
+
+// Logical op of a pass before layout assignment.
+struct LOp {
+    uint8_t kind;  // OP_PHASE, OP_RX (as a whole-group mixer), OP_EXPECT, OP_CUTVAL
+    int32_t arg;   // level
+};
+
+struct Pass {
+    int group;        // index into the group list
+    bool synth;       // first op synthesises |+>^n instead of loading
+    bool store;       // last op writes the tile back
+    std::vector<LOp> lops;
+    std::vector<Op> ops;  // physical program after layout assignment
+};
+
+struct Plan {
+    int n = 0;
+    TileConfig tc{};
+    std::vector<Group> groups;
+    std::vector<Pass> passes;
+};
+
+// Mixer groups for n >= Q qubits: group 0 = [0, Q), the rest of [Q, n) split into balanced
+// contiguous groups of at most Q - cmin qubits.
+std::vector<Group> make_groups(int n, const TileConfig& tc);
+Geometry group_geometry(const Group& g, const TileConfig& tc);
+uint32_t group_target_mask(const Group& g, const TileConfig& tc);
+
+// Passes for `levels` levels starting from a materialised state (or a deferred |+>^n when
+// `synth_first`), with the expectation fused into the last pass when `expect_last`.
+Plan plan_levels(int n, const TileConfig& tc, int levels, bool synth_first, bool expect_last);
+
+// Single pass over group 0 that only evaluates (no store): expectation or cut values.
+Plan plan_readonly(int n, const TileConfig& tc, bool synth, uint8_t kind, int group = 0,
+                   int layout = 0);
+
+// Assigns register layouts and shared-memory exchanges to every pass of the plan
+// (minimum number of exchanges; programs start and end in layout 0 or 1).
+void assign_layouts(Plan& plan);
+
+// Flattened description (see qaoa_plan_describe in qaoa.h).
+std::vector<int32_t> describe(const Plan& plan);
+
+}  // namespace qaoa

@@ -1,0 +1,286 @@
+"""GPU parity of the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances: cut values bit-exact; complex128 <C> within 1e-12 relative and the state within
+1e-12 in the 2-norm; complex64 <C> within 1e-5 * |E| and state fidelity >= 1 - 1e-5.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2312_03019_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2312_03019_b300 import build
+    build.build()
+    from paper_2312_03019_b300 import binding
+    return binding
+
+
+def run(B, g, gamma, beta, prec):
+    s = B.QAOAState(g, prec)
+    s.apply_layers(gamma, beta)
+    c, nrm = s.expectation()
+    psi = s.amplitudes()
+    s.close()
+    return c, nrm, psi.astype(np.complex128)
+
+
+def check_c128(g, c, nrm, psi, ref_psi):
+    ref_c, _ = oracle_expectation(g, ref_psi)
+    assert abs(c - ref_c) <= 1e-12 * max(1.0, abs(ref_c))
+    assert abs(nrm - 1.0) < 1e-12
+    assert np.linalg.norm(psi - ref_psi) <= 1e-12
+
+
+def check_c64(g, c, nrm, psi, ref_psi):
+    ref_c, _ = oracle_expectation(g, ref_psi)
+    assert abs(c - ref_c) <= 1e-5 * max(1, g.m)
+    assert abs(nrm - 1.0) < 1e-5
+    fid = abs(np.vdot(ref_psi, psi)) ** 2
+    assert fid >= 1 - 1e-5
+
+
+def oracle_expectation(g, psi):
+    import oracle
+    return oracle.expectation(g, psi)
+
+
+# ----------------------------------------------------------------------------- cut values
+
+CUT_GRAPHS = [
+    lambda n: I.empty(n), lambda n: I.complete(n), lambda n: I.star(n), lambda n: I.ring(n) if n >= 3 else I.empty(n),
+    lambda n: I.gnp(n, 0.5, n), lambda n: I.gnp(n, 0.2, 100 + n),
+    lambda n: I.regular3(n, n) if n >= 4 else I.empty(n),
+]
+
+
+@pytest.mark.parametrize("n", list(range(1, 23)))
+def test_cut_table_bit_exact(B, n):
+    import oracle
+    for mk in CUT_GRAPHS:
+        g = mk(n)
+        if n > 18 and g.m > 120:
+            continue  # keep the oracle's edge loop quick
+        got = B.qaoa_cut_table(g)
+        assert np.array_equal(got, oracle.cut_table(g)), g.name
+
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+@pytest.mark.parametrize("n", [15, 17, 20, 23, 26])
+def test_cut_count_every_tile_geometry(B, prec, n):
+    """The tile kernels split C(z) per CTA / thread / register (the on-the-fly Algorithm 3);
+    every group geometry and register layout must reproduce the plain edge-loop count."""
+    import oracle
+    groups = B.qaoa_plan_describe(n, prec, 1)[3]
+    for g in (I.gnp(n, 0.5, 7), I.regular3(n, 3) if n % 2 == 0 else I.gnp(n, 0.15, 9), I.complete(min(n, 26))):
+        if g.n != n:
+            continue
+        ref = oracle.cut_table(g)
+        for grp in range(groups):
+            for layout in range(3):
+                got = B.qaoa_cut_table_geometry(g, prec, grp, layout)
+                assert np.array_equal(got, ref), (g.name, grp, layout)
+
+
+# ----------------------------------------------------------------------------- small and mid sizes
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("n,p,mk", [
+    (1, 2, lambda n: I.empty(1)), (2, 3, lambda n: I._canonical(2, [(0, 1)], "edge")),
+    (5, 2, lambda n: I.complete(5)), (8, 4, lambda n: I.gnp(8, 0.5, 1)), (10, 3, lambda n: I.regular3(10, 0)),
+    (12, 2, lambda n: I.gnp(12, 0.3, 2)), (13, 5, lambda n: I.regular3(13, 1)), (14, 3, lambda n: I.gnp(14, 0.5, 3)),
+    (15, 3, lambda n: I.gnp(15, 0.4, 4)), (16, 4, lambda n: I.regular3(16, 5)), (17, 2, lambda n: I.complete(17)),
+    (18, 5, lambda n: I.gnp(18, 0.3, 6)), (19, 3, lambda n: I.regular3(19, 7)), (21, 2, lambda n: I.gnp(21, 0.25, 8)),
+])
+def test_state_parity(B, prec, n, p, mk):
+    import oracle
+    g = mk(n)
+    gamma, beta = I.angles(p, seed=n)
+    ref = oracle.qaoa_state(g, gamma, beta)
+    c, nrm, psi = run(B, g, gamma, beta, prec)
+    (check_c128 if prec == "c128" else check_c64)(g, c, nrm, psi, ref)
+
+
+def test_config_n10_regular3_p1(B):
+    """3-regular n=10, p=1, gamma=0.4, beta=0.3, complex128: full state, <C>, closed form."""
+    import oracle
+    from tests.test_oracle_pins import p1_closed_form
+    g, gamma, beta = I.workload_n10_regular3_p1()
+    ref = oracle.qaoa_state(g, gamma, beta)
+    c, nrm, psi = run(B, g, gamma, beta, "c128")
+    check_c128(g, c, nrm, psi, ref)
+    assert abs(c - p1_closed_form(g, 0.4, 0.3)) < 1e-12 * g.m
+
+
+@pytest.mark.parametrize("name,prec", [("regular3_n22_p6", "c128"), ("regular3_n22_p6", "c64"),
+                                       ("gnp24_p10", "c128"), ("gnp24_p10", "c64"),
+                                       ("gnp26_p4", "c128"), ("gnp26_p4", "c64")])
+def test_golden_large(B, name, prec):
+    """Stored oracle results (written by tests/golden/make_golden.py from the oracle only)."""
+    path = os.path.join(GOLDEN, f"{name}.json")
+    if not os.path.exists(path):
+        pytest.skip(f"{name}.json not generated")
+    rec = json.load(open(path))
+    g = I.Graph(rec["n"], np.array(rec["edges"], dtype=np.int32))
+    s = B.QAOAState(g, prec)
+    s.apply_layers(rec["gamma"], rec["beta"])
+    c, nrm = s.expectation()
+    t = s.as_tensor()
+    import torch
+    idx = torch.tensor(rec["sample_index"], dtype=torch.int64, device=t.device)
+    samp = t[idx].cpu().numpy().astype(np.complex128)
+    s.close()
+    ref = np.array(rec["sample_re"]) + 1j * np.array(rec["sample_im"])
+    if prec == "c128":
+        assert abs(c - rec["expectation"]) <= 1e-12 * abs(rec["expectation"])
+        assert abs(nrm - 1) < 1e-12
+        assert np.max(np.abs(samp - ref)) < 1e-14
+    else:
+        assert abs(c - rec["expectation"]) <= 1e-5 * rec["m"]
+        assert abs(nrm - 1) < 1e-5
+        amp = 2 ** (-rec["n"] / 2)
+        assert np.max(np.abs(samp - ref)) < 2e-5 * amp * math.sqrt(len(rec["gamma"]))
+
+
+def test_c64_matches_c128_full_state_n26(B):
+    g, gamma, beta = I.workload_gnp26_p4()
+    c1, n1, a = run(B, g, gamma, beta, "c128")
+    c2, n2, b = run(B, g, gamma, beta, "c64")
+    assert abs(c1 - c2) <= 1e-5 * g.m
+    assert abs(np.vdot(a, b)) ** 2 >= 1 - 1e-5
+
+
+# ----------------------------------------------------------------------------- semantics / edge cases
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+@pytest.mark.parametrize("n", [9, 18])
+def test_split_calls_equal_one_call(B, prec, n):
+    g = I.gnp(n, 0.4, 3)
+    gamma, beta = I.angles(5, 3)
+    s1 = B.QAOAState(g, prec)
+    s1.apply_layers(gamma, beta)
+    a = s1.amplitudes()
+    s2 = B.QAOAState(g, prec)
+    s2.apply_layers(gamma[:2], beta[:2])
+    s2.apply_layers(gamma[2:], beta[2:])
+    b = s2.amplitudes()
+    tol = 1e-13 if prec == "c128" else 1e-6
+    assert np.max(np.abs(a - b)) < tol * 2 ** (-n / 2) * 10
+
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+@pytest.mark.parametrize("n", [6, 16])
+def test_initial_state_and_zero_levels(B, prec, n):
+    g = I.gnp(n, 0.5, 1)
+    s = B.QAOAState(g, prec)
+    c, nrm = s.expectation()  # deferred |+>^n
+    assert abs(c - g.m / 2) < 1e-12 * g.m + (1e-6 * g.m if prec == "c64" else 0)
+    s.apply_layers([], [])  # p = 0 writes |+>^n out
+    psi = s.amplitudes()
+    assert np.allclose(psi, 2 ** (-n / 2), rtol=0, atol=1e-7 * 2 ** (-n / 2))
+    c2, _ = s.expectation()
+    assert abs(c2 - c) < 1e-6 * g.m
+
+
+def test_invalid_angles_rejected(B):
+    s = B.QAOAState(I.ring(6), "c64")
+    with pytest.raises(B.QAOAError):
+        s.apply_layers([float("nan")], [0.1])
+    with pytest.raises(B.QAOAError):
+        s.apply_layers([0.1], [float("inf")])
+
+
+def test_deterministic_expectation(B):
+    g, gamma, beta = I.workload_gnp24_p10()
+    vals = []
+    for _ in range(2):
+        s = B.QAOAState(g, "c64")
+        s.apply_layers(gamma, beta)
+        vals.append(s.expectation())
+        s.close()
+    assert vals[0] == vals[1]
+
+
+def test_many_levels_crosses_coefficient_chunks(B):
+    import oracle
+    g = I.regular3(16, 2)
+    gamma, beta = I.angles(70, 2)
+    ref = oracle.qaoa_state(g, gamma, beta)
+    c, nrm, psi = run(B, g, gamma, beta, "c128")
+    check_c128(g, c, nrm, psi, ref)
+
+
+# ----------------------------------------------------------------------------- full size (n = 33)
+
+@pytest.mark.slow
+def test_full_size_n33_properties(B):
+    """Near-3-regular n = 33 in complex64 (64 GiB): the run of the benchmark, checked where the
+    oracle can compute values one by one: beta = 0 gives psi_z = 2^(-n/2) exp(-i sum gamma C(z))
+    amplitude by amplitude; p = 1 matches the closed-form <C>; the p = 8 run keeps the norm,
+    the complement symmetry and 0 <= <C> <= |E|."""
+    import oracle
+    import torch
+    from tests.test_oracle_pins import p1_closed_form
+    g, gamma, beta = I.workload_regular3_n33_p8()
+    n = g.n
+    rng = np.random.default_rng(7)
+    idx = np.unique(np.concatenate([rng.integers(0, 1 << n, 256), [0, (1 << n) - 1, 1 << 32, (1 << 32) + 5]]))
+    s = B.QAOAState(g, "c64")
+    # beta = 0: pure cost phases, sampled amplitude by amplitude against the oracle's cut value
+    s.apply_layers(gamma[:3], np.zeros(3))
+    t = s.as_tensor()
+    samp = t[torch.tensor(idx, device=t.device)].cpu().numpy().astype(np.complex128)
+    amp = 2 ** (-n / 2)
+    ref = np.array([amp * np.exp(-1j * gamma[:3].sum() * oracle.cut_value(g, int(z))) for z in idx])
+    assert np.max(np.abs(samp - ref)) < 1e-5 * amp
+    s.close()
+    del t
+    torch.cuda.empty_cache()
+    # p = 1 closed form
+    s = B.QAOAState(g, "c64")
+    s.apply_layers([0.4], [0.3])
+    c, nrm = s.expectation()
+    assert abs(c - p1_closed_form(g, 0.4, 0.3)) <= 1e-5 * g.m
+    assert abs(nrm - 1) < 1e-5
+    s.close()
+    torch.cuda.empty_cache()
+    # the benchmark's p = 8 run
+    s = B.QAOAState(g, "c64")
+    s.apply_layers(gamma, beta)
+    c, nrm = s.expectation()
+    assert abs(nrm - 1) < 1e-4 and 0 <= c <= g.m
+    t = s.as_tensor()
+    a = t[torch.tensor(idx, device=t.device)].cpu().numpy()
+    b = t[torch.tensor(((1 << n) - 1) ^ idx, device=t.device)].cpu().numpy()
+    assert np.max(np.abs(a - b)) < 1e-5 * amp
+    s.close()
+    del t
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.slow
+def test_full_size_n33_c128_closed_form(B):
+    """complex128 at n = 33 (128 GiB): p = 1 <C> equals the closed form to 1e-12 relative."""
+    import torch
+    from tests.test_oracle_pins import p1_closed_form
+    g, _, _ = I.workload_regular3_n33_p8()
+    s = B.QAOAState(g, "c128")
+    s.apply_layers([0.4], [0.3])
+    c, nrm = s.expectation()
+    ref = p1_closed_form(g, 0.4, 0.3)
+    assert abs(c - ref) <= 1e-12 * ref
+    assert abs(nrm - 1) < 1e-12
+    s.close()
+    torch.cuda.empty_cache()
