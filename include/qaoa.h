@@ -145,6 +145,27 @@ qaoa_status qaoa_profile_enable(qaoa_state s, int32_t enable);
 /* Synchronises the stream and returns the counters since the last enable. */
 qaoa_status qaoa_profile_read(qaoa_state s, qaoa_profile_stats *out);
 
+/* <C> and the squared norm of a complex64 / complex128 state that the caller already holds on the
+ * device, computed without allocating anything.  The paper has no counterpart: this entry
+ * exists for callers that cannot call cudaMalloc -- for example a runtime that has handed all
+ * of the GPU's memory to its own pool, or a loop that must not pay the device-wide
+ * synchronisation an allocation can cause.  It takes the graph (as for qaoa_state_init), the
+ * state (2^n amplitudes at dev_state, state_bytes >= qaoa_state_bytes(n, prec), 16-byte
+ * aligned, read only) and a CUDA stream (NULL = legacy default stream), and returns both sums
+ * through the host pointers, synchronising the stream.
+ *
+ * Scratch space is a fixed 1 MiB array in the library's device memory (one partial pair per
+ * tile of the state plus the result), which every GPU that loads the library keeps until the
+ * process exits.  That bounds the size: n <= 29 for complex64 and n <= 28 for complex128
+ * (larger n returns QAOA_ERR_INVALID with a message).  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls share the one array: every entry a call reads is written earlier in the
+ * same call, so nothing has to be cleared, but two calls whose work overlaps on the GPU (on
+ * different streams or host threads) race on it and give wrong results. */
+qaoa_status qaoa_expectation_static(const qaoa_graph *g, qaoa_prec prec, const void *dev_state,
+                                    size_t state_bytes, void *cuda_stream, double *out_c,
+                                    double *out_norm);
+
 /* Message of the last error on the calling thread ("" if none). */
 const char *qaoa_last_error(void);
 

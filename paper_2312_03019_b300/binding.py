@@ -84,6 +84,7 @@ _sig("qaoa_plan_describe", ctypes.c_int, [_i32, ctypes.c_int, _i32, ctypes.POINT
                                            ctypes.POINTER(_i32)])
 _sig("qaoa_profile_enable", ctypes.c_int, [_vp, _i32])
 _sig("qaoa_profile_read", ctypes.c_int, [_vp, ctypes.POINTER(ProfileStats)])
+_sig("qaoa_expectation_static", ctypes.c_int, [ctypes.POINTER(_Graph), ctypes.c_int, _vp, ctypes.c_size_t, _vp, _dp, _dp])
 _sig("qaoa_last_error", ctypes.c_char_p, [])
 
 
@@ -142,6 +143,16 @@ def qaoa_expectation(h: int):
     c = ctypes.c_double()
     nn = ctypes.c_double()
     _check(_lib.qaoa_expectation(_vp(h), ctypes.byref(c), ctypes.byref(nn)))
+    return c.value, nn.value
+
+
+def qaoa_expectation_static(g, prec, dev_ptr: int, nbytes: int, stream: int = 0):
+    """<C> and norm of a device state without any allocation (scratch is a static device array)."""
+    gs, keep = _graph(g)
+    c = ctypes.c_double()
+    nn = ctypes.c_double()
+    _check(_lib.qaoa_expectation_static(ctypes.byref(gs), _prec(prec), _vp(dev_ptr), nbytes, _vp(stream),
+                                        ctypes.byref(c), ctypes.byref(nn)))
     return c.value, nn.value
 
 

@@ -14,6 +14,7 @@
 #include <mutex>
 #include <new>
 #include <set>
+#include <type_traits>
 #include <string>
 #include <utility>
 #include <vector>
@@ -434,6 +435,116 @@ qaoa_status cut_table_impl(const HostGraph& hg, int prec, int group, int layout,
 
 }  // namespace
 
+// ---------------------------------------------------------------------------------- allocation-free <C>
+//
+// qaoa_expectation_static keeps its scratch (one partial-sum pair per tile plus the final
+// pair) in this file-scope device array instead of allocating workspace.  In host code
+// `g_static_scratch` only names a host-side shadow, so the device address is looked up once per
+// device with cudaGetSymbolAddress and passed to the kernels.
+namespace {
+
+constexpr uint64_t kStaticPartials = 1ull << 16;  // tiles per call (2^16 x 16 B = 1 MiB)
+constexpr int kStaticMaxDevices = 64;
+
+}  // namespace
+
+static __device__ __align__(256) double2 g_static_scratch[kStaticPartials + 1];
+
+namespace {
+
+double2* g_static_ptr[kStaticMaxDevices] = {};
+std::mutex g_static_mu;
+
+// Graph checks of encode_graph without any heap use (repeated edges found in the bitmasks).
+qaoa_status encode_graph_static(const qaoa_graph* g, HostGraph& hg) {
+    if (!g) return fail(QAOA_ERR_INVALID, "graph is NULL");
+    if (g->n < 1 || g->n > kMaxN) return fail(QAOA_ERR_INVALID, "n must be in [1, 34]");
+    if (g->m < 0) return fail(QAOA_ERR_INVALID, "m must be >= 0");
+    if (g->m > 0 && !g->edges) return fail(QAOA_ERR_INVALID, "edges is NULL");
+    if (g->weights) return fail(QAOA_ERR_UNSUPPORTED, "weighted graphs are not supported by this entry point");
+    hg.n = g->n;
+    hg.m = g->m;
+    for (int e = 0; e < g->m; ++e) {
+        int u = g->edges[2 * e], v = g->edges[2 * e + 1];
+        if (u < 0 || v < 0 || u >= g->n || v >= g->n) return fail(QAOA_ERR_INVALID, "edge endpoint out of range");
+        if (u == v) return fail(QAOA_ERR_INVALID, "self loop");
+        if (u > v) std::swap(u, v);
+        if ((hg.adj[u] >> v) & 1ull) return fail(QAOA_ERR_INVALID, "repeated edge");
+        hg.upper[u] |= 1ull << v;
+        hg.adj[u] |= 1ull << v;
+        hg.adj[v] |= 1ull << u;
+    }
+    return QAOA_OK;
+}
+
+// Device address of the scratch array on the current device (looked up on first use).
+qaoa_status static_scratch(double2** out) {
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kStaticMaxDevices) return fail(QAOA_ERR_UNSUPPORTED, "device ordinal too large");
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void* p = nullptr;
+        CUDA_TRY(cudaGetSymbolAddress(&p, g_static_scratch));
+        g_static_ptr[dev] = reinterpret_cast<double2*>(p);
+    }
+    *out = g_static_ptr[dev];
+    return QAOA_OK;
+}
+
+template <typename real>
+qaoa_status expectation_static_impl(const HostGraph& hg, const void* dev_state, cudaStream_t stream,
+                                    double2* scratch, double* out_c, double* out_norm) {
+    constexpr int Q = PrecTraits<real>::Q, R = PrecTraits<real>::R;
+    using C2 = typename C2T<real>::type;
+    const int n = hg.n;
+    uint64_t count = 1;
+    if (is_small(n, std::is_same<real, float>::value ? QAOA_C64 : QAOA_C128)) {
+        SmallJob j;
+        std::memset(&j, 0, sizeof(j));
+        j.n = n;
+        j.E1 = hg.m + 1;
+        j.expect = 1;
+        j.init_amp = std::pow(2.0, -0.5 * n);
+        for (int v = 0; v < kMaxN; ++v) j.gmask[v] = v < n ? hg.upper[v] : 0;
+        j.state = const_cast<void*>(dev_state);
+        j.partials = scratch;
+        auto kfn = small_kernel<real>;
+        CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024));
+        kfn<<<1, kSmallThreads, ((size_t)1 << n) * sizeof(C2), stream>>>(j);
+        CUDA_TRY(cudaGetLastError());
+    } else {
+        const TileConfig tc = tile_config_for(std::is_same<real, float>::value ? 0 : 1);
+        count = 1ull << (n - Q);
+        TileArgs<Q> a;
+        std::memset(&a, 0, sizeof(a));
+        fill_geometry(a, hg, Geometry{Q, Q}, tc);
+        a.nops = 2;
+        a.ops[0] = Op{OP_LOAD, 0, 0, 0};
+        a.ops[1] = Op{OP_EXPECT, 0, 0, 0};
+        a.need_cut = 1;
+        a.E1 = hg.m + 1;
+        a.init_amp = std::pow(2.0, -0.5 * n);
+        a.state = const_cast<void*>(dev_state);
+        a.partials = scratch;
+        auto kfn = tile_kernel<real, Q, R>;
+        const size_t smem = (size_t)(1u << Q) * sizeof(C2);
+        CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kfn<<<(unsigned)count, 1u << (Q - R), smem, stream>>>(a);
+        CUDA_TRY(cudaGetLastError());
+    }
+    finalize_kernel<<<1, 1024, 0, stream>>>(scratch, count, scratch + kStaticPartials);
+    CUDA_TRY(cudaGetLastError());
+    double2 res;
+    CUDA_TRY(cudaMemcpyAsync(&res, scratch + kStaticPartials, sizeof(double2), cudaMemcpyDeviceToHost, stream));
+    CUDA_TRY(cudaStreamSynchronize(stream));
+    if (out_c) *out_c = res.x;
+    if (out_norm) *out_norm = res.y;
+    return QAOA_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 size_t qaoa_state_bytes(int32_t n, qaoa_prec prec) {
@@ -605,6 +716,27 @@ qaoa_status qaoa_profile_read(qaoa_state s, qaoa_profile_stats* out) {
         }
     }
     return QAOA_OK;
+}
+
+qaoa_status qaoa_expectation_static(const qaoa_graph* g, qaoa_prec prec, const void* dev_state,
+                                    size_t state_bytes, void* cuda_stream, double* out_c, double* out_norm) {
+    if (prec != QAOA_C64 && prec != QAOA_C128) return fail(QAOA_ERR_INVALID, "unknown precision");
+    if (!dev_state) return fail(QAOA_ERR_INVALID, "device state is NULL");
+    if (((uintptr_t)dev_state & 15u) != 0) return fail(QAOA_ERR_INVALID, "device state not 16-byte aligned");
+    HostGraph hg;
+    qaoa_status st = encode_graph_static(g, hg);
+    if (st != QAOA_OK) return st;
+    const int q = prec == QAOA_C64 ? PrecTraits<float>::Q : PrecTraits<double>::Q;
+    if (!is_small(hg.n, prec) && (1ull << (hg.n - q)) > kStaticPartials)
+        return fail(QAOA_ERR_INVALID, prec == QAOA_C64 ? "qaoa_expectation_static supports n <= 29 for complex64"
+                                                       : "qaoa_expectation_static supports n <= 28 for complex128");
+    if (state_bytes < qaoa_state_bytes(hg.n, prec)) return fail(QAOA_ERR_INVALID, "device state too small");
+    double2* scratch = nullptr;
+    st = static_scratch(&scratch);
+    if (st != QAOA_OK) return st;
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    return prec == QAOA_C64 ? expectation_static_impl<float>(hg, dev_state, stream, scratch, out_c, out_norm)
+                            : expectation_static_impl<double>(hg, dev_state, stream, scratch, out_c, out_norm);
 }
 
 const char* qaoa_last_error(void) { return g_last_error.c_str(); }
