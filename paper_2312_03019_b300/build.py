@@ -38,6 +38,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
            "-o", LIB + ".tmp"] + [os.path.join(CSRC, s) for s in SOURCES]
     if verbose:
         cmd += ["-Xptxas", "-v"]
+    cmd += os.environ.get("QAOA_NVCC_EXTRA", "").split()
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         sys.stderr.write(r.stdout + r.stderr)

@@ -582,7 +582,7 @@ qaoa_status qaoa_state_init(const qaoa_graph* g, qaoa_prec prec, void* dev_buf, 
     }
     const size_t eb = elem_bytes(prec);
     cudaError_t e = cudaMalloc(&s->d_phase, (size_t)kLayerChunk * (hg.m + 1) * eb);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_mix, (size_t)kLayerChunk * eb);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_mix, (size_t)3 * kLayerChunk * eb);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_partials, (size_t)s->ntiles * sizeof(double2));
     if (e == cudaSuccess) e = cudaMalloc(&s->d_result, sizeof(double2));
     if (e == cudaSuccess) e = cudaMallocHost(&s->h_result, sizeof(double2));

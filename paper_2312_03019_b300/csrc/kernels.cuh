@@ -2,7 +2,8 @@
 //
 // Kernels:
 //   coeff_kernel   per level k: phase table T_k[c] = exp(-i gamma_k c), c = 0..|E| (FP64
-//                  sincos, rounded to the state precision) and the mixer pair (cos b, sin b).
+//                  sincos, rounded to the state precision) and the mixer coefficients: (cos b,
+//                  sin b) and the factored butterfly (A, T), (scale, mode) described at `rx`.
 //   tile_kernel    one pass over the state in tiles of 2^Q amplitudes (see plan.h): loads a
 //                  tile (or synthesises |+>^n), runs the pass program (RX butterflies in
 //                  registers, register-layout exchanges through swizzled shared memory, the
@@ -59,7 +60,7 @@ struct TileArgs {
     Op ops[kMaxOps];
     void* state;
     const void* phase;   // [level][E1] complex<real>
-    const void* mix;     // [level] (cos beta, sin beta) as complex<real>
+    const void* mix;     // [3 * level + i]: (cos b, sin b), (A, T), (scale, mode) as complex<real>
     double2* partials;   // [tile] (sum |psi|^2 C, sum |psi|^2)
     uint16_t* cutout;    // [2^n] cut values (OP_CUTVAL)
 };
@@ -175,35 +176,49 @@ struct Tile {
         return o;
     }
 
+    // Byte steps between consecutive register indices x -> x+1: the lowest zero bit j of x is
+    // set and the bits below it cleared, so the offset changes by st[j] - sum_{i<j} st[i].
+    template <int L>
+    static __device__ __forceinline__ void steps(const TileArgs<Q>& a, int64_t (&d)[R]) {
+        uint64_t st[R];
+        strides<L>(a, st);
+        uint64_t below = 0;
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            d[j] = (int64_t)((st[j] - below) * sizeof(C2));
+            below += st[j];
+        }
+    }
+
+    static __host__ __device__ constexpr int ctz_next(int x) {
+        int j = 0;
+        while ((((x + 1) >> j) & 1) == 0) ++j;
+        return j;
+    }
+
     template <int L>
     static __device__ __forceinline__ void load(C2 (&v)[NE], const Ctx& c, uint32_t tid) {
         const TileArgs<Q>& a = *c.a;
-        const C2* __restrict__ g = reinterpret_cast<const C2*>(a.state) + c.zb + gofs(a, tbits(L, tid));
-        uint64_t st[R];
-        strides<L>(a, st);
+        const char* g = reinterpret_cast<const char*>(reinterpret_cast<const C2*>(a.state) + c.zb + gofs(a, tbits(L, tid)));
+        int64_t d[R];
+        steps<L>(a, d);
 #pragma unroll
         for (int x = 0; x < NE; ++x) {
-            uint64_t o = 0;
-#pragma unroll
-            for (int j = 0; j < R; ++j)
-                if ((x >> j) & 1) o += st[j];
-            v[x] = g[o];
+            v[x] = *reinterpret_cast<const C2*>(g);
+            if (x + 1 < NE) g += d[ctz_next(x)];
         }
     }
 
     template <int L>
     static __device__ __forceinline__ void store(const C2 (&v)[NE], const Ctx& c, uint32_t tid) {
         const TileArgs<Q>& a = *c.a;
-        C2* __restrict__ g = reinterpret_cast<C2*>(a.state) + c.zb + gofs(a, tbits(L, tid));
-        uint64_t st[R];
-        strides<L>(a, st);
+        char* g = reinterpret_cast<char*>(reinterpret_cast<C2*>(a.state) + c.zb + gofs(a, tbits(L, tid)));
+        int64_t d[R];
+        steps<L>(a, d);
 #pragma unroll
         for (int x = 0; x < NE; ++x) {
-            uint64_t o = 0;
-#pragma unroll
-            for (int j = 0; j < R; ++j)
-                if ((x >> j) & 1) o += st[j];
-            g[o] = v[x];
+            *reinterpret_cast<C2*>(g) = v[x];
+            if (x + 1 < NE) g += d[ctz_next(x)];
         }
     }
 
@@ -312,20 +327,53 @@ struct Tile {
         }
     }
 
-    static __device__ __forceinline__ void rx(C2 (&v)[NE], uint32_t mask, real cb, real sb) {
+    // RX(2b) = [[c, -is], [-is, c]] up to a real factor, one FMA per output component:
+    //   mode 0 (|tan b| <= 1): a' = a - i t b, b' = b - i t a   (t = tan b, factor cos b)
+    //   mode 1 (|cot b| <  1): a' = k a - i b, b' = k b - i a   (k = cot b, factor sin b)
+    // The factors of all RX gates in a pass are multiplied up and applied once (`scale_all`).
+    static __device__ __forceinline__ void rx(C2 (&v)[NE], uint32_t mask, real A, real T, int mode) {
+        if (mode == 0) {
+            const real nT = -T;
 #pragma unroll
-        for (int j = 0; j < R; ++j) {
-            if (mask & (1u << j)) {
+            for (int j = 0; j < R; ++j) {
+                if (mask & (1u << j)) {
 #pragma unroll
-                for (int x = 0; x < NE; ++x)
-                    if (!(x & (1 << j))) rx_pair(v[x], v[x | (1 << j)], cb, sb);
+                    for (int x = 0; x < NE; ++x)
+                        if (!(x & (1 << j))) {
+                            const C2 p = v[x], q = v[x | (1 << j)];
+                            v[x] = make_c2(fma(T, q.y, p.x), fma(nT, q.x, p.y));
+                            v[x | (1 << j)] = make_c2(fma(T, p.y, q.x), fma(nT, p.x, q.y));
+                        }
+                }
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                if (mask & (1u << j)) {
+#pragma unroll
+                    for (int x = 0; x < NE; ++x)
+                        if (!(x & (1 << j))) {
+                            const C2 p = v[x], q = v[x | (1 << j)];
+                            v[x] = make_c2(fma(A, p.x, q.y), fma(A, p.y, -q.x));
+                            v[x | (1 << j)] = make_c2(fma(A, q.x, p.y), fma(A, q.y, -p.x));
+                        }
+                }
             }
         }
     }
+
+    static __device__ __forceinline__ void scale_all(C2 (&v)[NE], real f) {
+#pragma unroll
+        for (int x = 0; x < NE; ++x) v[x] = make_c2(v[x].x * f, v[x].y * f);
+    }
 };
 
+#ifndef QAOA_TILE_MIN_BLOCKS
+#define QAOA_TILE_MIN_BLOCKS 2  // resident CTAs per SM the register budget is sized for
+#endif
+
 template <typename real, int Q, int R>
-__global__ void __launch_bounds__(1 << (Q - R), 2) tile_kernel(const __grid_constant__ TileArgs<Q> a) {
+__global__ void __launch_bounds__(1 << (Q - R), QAOA_TILE_MIN_BLOCKS) tile_kernel(const __grid_constant__ TileArgs<Q> a) {
     using T = Tile<real, Q, R>;
     using C2 = typename T::C2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -362,6 +410,7 @@ __global__ void __launch_bounds__(1 << (Q - R), 2) tile_kernel(const __grid_cons
 
     C2 v[T::NE];
     int L = 0;
+    real scale = (real)1;  // product of the deferred RX factors not yet applied
     double accC = 0.0, accN = 0.0;
     bool did_expect = false;
 
@@ -393,8 +442,10 @@ __global__ void __launch_bounds__(1 << (Q - R), 2) tile_kernel(const __grid_cons
                 else T::template from_smem<2>(v, tile, tid);
                 break;
             case OP_RX: {
-                const C2 cs = reinterpret_cast<const C2*>(a.mix)[op.arg];
-                T::rx(v, op.mask, cs.x, cs.y);
+                const C2* m = reinterpret_cast<const C2*>(a.mix) + 3 * op.arg;
+                const C2 at = m[1], sm = m[2];
+                T::rx(v, op.mask, at.x, at.y, sm.y != (real)0);
+                for (uint32_t k = op.mask; k; k &= k - 1) scale *= sm.x;
                 break;
             }
             case OP_PHASE:
@@ -403,6 +454,10 @@ __global__ void __launch_bounds__(1 << (Q - R), 2) tile_kernel(const __grid_cons
                 else T::template phase<2>(v, c, tid, op.arg);
                 break;
             case OP_EXPECT:
+                if (scale != (real)1) {
+                    T::scale_all(v, scale);
+                    scale = (real)1;
+                }
                 did_expect = true;
                 if (L == 0) T::template expect<0>(v, c, tid, accC, accN);
                 else if (L == 1) T::template expect<1>(v, c, tid, accC, accN);
@@ -414,6 +469,10 @@ __global__ void __launch_bounds__(1 << (Q - R), 2) tile_kernel(const __grid_cons
                 else T::template cutval<2>(c, tid);
                 break;
             case OP_STORE:
+                if (scale != (real)1) {
+                    T::scale_all(v, scale);
+                    scale = (real)1;
+                }
                 if (L == 0) T::template store<0>(v, c, tid);
                 else if (L == 1) T::template store<1>(v, c, tid);
                 else T::template store<2>(v, c, tid);
@@ -466,7 +525,7 @@ __device__ __forceinline__ void small_body(const SmallJob& j) {
     for (int k = 0; k < j.levels; ++k) {
         const C2* T = reinterpret_cast<const C2*>(j.phase) + (size_t)k * j.E1;
         for (uint32_t z = tid; z < dim; z += kSmallThreads) st[z] = cmul(st[z], __ldg(T + cut_count_full(gm, n, z)));
-        const C2 cs = mix[k];
+        const C2 cs = mix[3 * k];
         for (int q = 0; q < n; ++q) {
             __syncthreads();
             for (uint32_t i = tid; i < dim / 2; i += kSmallThreads) {
@@ -533,7 +592,15 @@ __global__ void coeff_kernel(const __grid_constant__ CoeffArgs a) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         double s, co;
         sincos(a.beta[k], &s, &co);
-        reinterpret_cast<C2*>(a.mix)[k] = make_c2((real)co, (real)s);
+        C2* m = reinterpret_cast<C2*>(a.mix) + 3 * k;
+        m[0] = make_c2((real)co, (real)s);
+        if (fabs(s) <= fabs(co)) {
+            m[1] = make_c2((real)1, (real)(s / co));  // a - i tan(b) b, factor cos b
+            m[2] = make_c2((real)co, (real)0);
+        } else {
+            m[1] = make_c2((real)(co / s), (real)1);  // cot(b) a - i b, factor sin b
+            m[2] = make_c2((real)s, (real)1);
+        }
     }
 }
 
