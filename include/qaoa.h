@@ -85,11 +85,20 @@ qaoa_status qaoa_state_init(const qaoa_graph *g, qaoa_prec prec, void *dev_buf, 
  * and workspace: the initial layer of Algorithm 1 by launch control (Section 2.2). */
 qaoa_status qaoa_state_reset(qaoa_state s);
 
+/* Makes the caller's buffer hold psi_z at index z: writes out a still-deferred |+>^n and
+ * resolves a pending index complement.  (When |tan beta_k| > 1 the tile passes evaluate
+ * RX(2 beta) as -i X RX(2 beta - pi) with X on every qubit; X maps index z to ~z and commutes with
+ * the cost phase and the mixer, so the library records it instead of moving data, and <C> is
+ * unaffected.)  Stream-ordered, no host synchronisation.  qaoa_state_copy_out does this itself;
+ * call it before reading the buffer directly. */
+qaoa_status qaoa_state_sync(qaoa_state s);
+
 /* Applies p levels (Algorithm 1's level loop) with angles gamma[0..p-1], beta[0..p-1] on top
  * of the current state: per level, the rotation-compressed cost phase (Eq. UC_opt with the
  * popcount count of Algorithm 3, evaluated on the fly) and the RX mixer on every qubit.
  * Asynchronous on the state's stream; the angle arrays are copied before return.  p == 0
- * only writes out a still-deferred |+>^n.  QAOA_ERR_INVALID on p < 0 or non-finite angles. */
+ * does what qaoa_state_sync does.  QAOA_ERR_INVALID on p < 0 or non-finite angles.  Until
+ * qaoa_state_sync, the buffer may hold the state with its indices complemented (see there). */
 qaoa_status qaoa_apply_layers(qaoa_state s, int32_t p, const double *gamma, const double *beta);
 
 /* <C> = sum_z |psi_z|^2 C(z) and the squared norm sum_z |psi_z|^2 of the current state,

@@ -74,6 +74,7 @@ _sig("qaoa_state_bytes", ctypes.c_size_t, [_i32, ctypes.c_int])
 _sig("qaoa_state_init", ctypes.c_int, [ctypes.POINTER(_Graph), ctypes.c_int, _vp, ctypes.c_size_t, _vp,
                                         ctypes.POINTER(_vp)])
 _sig("qaoa_state_reset", ctypes.c_int, [_vp])
+_sig("qaoa_state_sync", ctypes.c_int, [_vp])
 _sig("qaoa_apply_layers", ctypes.c_int, [_vp, _i32, _dp, _dp])
 _sig("qaoa_expectation", ctypes.c_int, [_vp, _dp, _dp])
 _sig("qaoa_state_copy_out", ctypes.c_int, [_vp, _vp, ctypes.c_size_t])
@@ -129,6 +130,10 @@ def qaoa_state_init(g, prec, dev_ptr: int, nbytes: int, stream: int = 0) -> int:
 
 def qaoa_state_reset(h: int) -> None:
     _check(_lib.qaoa_state_reset(_vp(h)))
+
+
+def qaoa_state_sync(h: int) -> None:
+    _check(_lib.qaoa_state_sync(_vp(h)))
 
 
 def qaoa_apply_layers(h: int, gamma, beta) -> None:
@@ -233,8 +238,10 @@ class QAOAState:
         return qaoa_state_copy_out(self.handle, self.n, self.prec)
 
     def as_tensor(self):
-        """The device buffer viewed as a complex torch tensor (call after apply_layers)."""
+        """The device buffer viewed as a complex torch tensor, index z = amplitude of z."""
         import torch
+
+        qaoa_state_sync(self.handle)
 
         dt = torch.complex64 if self.prec == QAOA_C64 else torch.complex128
         return self.buffer.view(dt)

@@ -87,26 +87,52 @@ size_t elem_bytes(int prec) { return prec == QAOA_C64 ? 8 : 16; }
 template <int Q>
 void fill_geometry(TileArgs<Q>& a, const HostGraph& hg, const Geometry& geo, const TileConfig& tc) {
     a.n = hg.n;
-    a.cprime = geo.cprime;
-    a.g0 = geo.g0;
     for (int v = 0; v < kMaxN; ++v) a.gmask[v] = v < hg.n ? hg.upper[v] : 0;
-    auto gpos = [&](int u) { return u < geo.cprime ? u : geo.g0 + (u - geo.cprime); };
-    auto lpos = [&](int w) -> int {
-        if (w < geo.cprime) return w;
-        if (w >= geo.g0 && w < geo.g0 + (Q - geo.cprime)) return geo.cprime + (w - geo.g0);
-        return -1;
-    };
+    int lpos[kMaxN];
+    for (int w = 0; w < kMaxN; ++w) lpos[w] = -1;
     uint64_t tileMask = 0;
-    for (int u = 0; u < Q; ++u) tileMask |= 1ull << gpos(u);
+    for (int u = 0; u < Q; ++u) {
+        lpos[geo.gpos[u]] = u;
+        tileMask |= 1ull << geo.gpos[u];
+    }
+    // tile id bits -> outer index bits, as runs of consecutive positions (ascending)
+    a.nruns = 0;
+    int src = 0;
+    for (int w = 0; w < hg.n;) {
+        if (lpos[w] >= 0) {
+            ++w;
+            continue;
+        }
+        int len = 0;
+        while (w + len < hg.n && lpos[w + len] < 0) ++len;
+        a.run_src[a.nruns] = (uint8_t)src;
+        a.run_len[a.nruns] = (uint8_t)len;
+        a.run_dst[a.nruns] = (uint8_t)w;
+        ++a.nruns;
+        src += len;
+        w += len;
+    }
+    // per register layout: index bits of the thread bits, strides and steps of the register bits
+    const int R = tc.R;
+    for (int L = 0; L < 3; ++L) {
+        for (int k = 0; k < Q - R; ++k) {
+            const int local = L == 0 ? k : (L == 1 ? (k < Q - 2 * R ? k : k + R) : k + R);
+            a.tpos[L][k] = (uint8_t)geo.gpos[local];
+        }
+        int64_t below = 0;
+        for (int j = 0; j < R; ++j) {
+            const int64_t st = (int64_t)1 << geo.gpos[tc.regLo(L) + j];
+            a.rstride[L][j] = st;
+            a.rstep[L][j] = st - below;
+            below += st;
+        }
+    }
     const uint64_t nMask = hg.n >= 64 ? ~0ull : ((1ull << hg.n) - 1ull);
     for (int u = 0; u < Q; ++u) {
-        const int gu = gpos(u);
+        const int gu = geo.gpos[u];
         uint32_t la = 0;
         for (int w = 0; w < hg.n; ++w)
-            if ((hg.adj[gu] >> w) & 1ull) {
-                const int lw = lpos(w);
-                if (lw >= 0) la |= 1u << lw;
-            }
+            if (((hg.adj[gu] >> w) & 1ull) && lpos[w] >= 0) la |= 1u << lpos[w];
         a.locAdj[u] = la;
         a.locUpper[u] = la & ~((2u << u) - 1u);
         a.outAdj[u] = hg.adj[gu] & ~tileMask & nMask;
@@ -117,8 +143,8 @@ void fill_geometry(TileArgs<Q>& a, const HostGraph& hg, const Geometry& geo, con
             int c = 0;
             if (x < (1 << tc.R))
                 for (int j = 0; j < tc.R; ++j)
-                    for (int k = j + 1; k < tc.R; ++k)
-                        if ((a.locAdj[rl + j] >> (rl + k)) & 1u) c += ((x >> j) ^ (x >> k)) & 1;
+                    for (int m = j + 1; m < tc.R; ++m)
+                        if ((a.locAdj[rl + j] >> (rl + m)) & 1u) c += ((x >> j) ^ (x >> m)) & 1;
             a.crtab[L][x] = (uint8_t)c;
         }
     }
@@ -162,6 +188,7 @@ struct qaoa_state_s {
     uint64_t partial_count = 0;
     bool lazy = true;
     bool exp_valid = false;
+    bool compl_ = false;  // buffer index z holds the amplitude of ~z (pending X on every qubit)
     // profiling
     bool prof = false;
     std::vector<EventPair> events;
@@ -260,10 +287,23 @@ qaoa_status apply_chunk(qaoa_state s, int levels, const double* gamma, const dou
     std::memset(&ca, 0, sizeof(ca));
     ca.levels = levels;
     ca.E1 = s->g.m + 1;
+    ca.n = s->n;
+    ca.fold_factors = s->small ? 0 : 1;
+    int folded = 0;
     for (int k = 0; k < levels; ++k) {
         ca.gamma[k] = gamma[k];
         ca.beta[k] = beta[k];
+        // Tile passes use RX(2b) = -i X RX(2b - pi) when |tan b| > 1, so that every butterfly
+        // coefficient has |t| <= 1.  X on every qubit maps index z to ~z; it commutes with the
+        // cost phase (C(~z) = C(z)) and the mixer, so it is only recorded (compl_).  The factors
+        // (-i)^n are folded exactly into the last phase table of the chunk.
+        ca.fold[k] = (!s->small && std::fabs(std::sin(beta[k])) > std::fabs(std::cos(beta[k]))) ? 1 : 0;
+        folded += ca.fold[k];
     }
+    const int quarter = (int)(((int64_t)folded * s->n) % 4);  // (-i)^quarter
+    ca.gre = quarter == 0 ? 1 : (quarter == 2 ? -1 : 0);
+    ca.gim = quarter == 1 ? -1 : (quarter == 3 ? 1 : 0);
+    if (folded & 1) s->compl_ = !s->compl_;
     ca.phase = s->d_phase;
     ca.mix = s->d_mix;
     dim3 grid((unsigned)std::max(1, (ca.E1 + 255) / 256), (unsigned)levels);
@@ -305,11 +345,19 @@ qaoa_status apply_chunk(qaoa_state s, int levels, const double* gamma, const dou
 
 template <typename real>
 qaoa_status materialize(qaoa_state s) {
-    if (!s->lazy) return QAOA_OK;
-    fill_kernel<real><<<148 * 8, 256, 0, s->stream>>>(s->buf, s->dim, std::pow(2.0, -0.5 * s->n));
-    CUDA_TRY(cudaGetLastError());
-    s->launches++;
-    s->lazy = false;
+    if (s->lazy) {
+        fill_kernel<real><<<148 * 8, 256, 0, s->stream>>>(s->buf, s->dim, std::pow(2.0, -0.5 * s->n));
+        CUDA_TRY(cudaGetLastError());
+        s->launches++;
+        s->lazy = false;
+        s->compl_ = false;  // |+>^n is its own complement
+    }
+    if (s->compl_) {
+        complement_kernel<real><<<148 * 8, 256, 0, s->stream>>>(s->buf, s->dim);
+        CUDA_TRY(cudaGetLastError());
+        s->launches++;
+        s->compl_ = false;
+    }
     return QAOA_OK;
 }
 
@@ -518,7 +566,7 @@ qaoa_status expectation_static_impl(const HostGraph& hg, const void* dev_state, 
         count = 1ull << (n - Q);
         TileArgs<Q> a;
         std::memset(&a, 0, sizeof(a));
-        fill_geometry(a, hg, Geometry{Q, Q}, tc);
+        fill_geometry(a, hg, low_geometry(tc), tc);
         a.nops = 2;
         a.ops[0] = Op{OP_LOAD, 0, 0, 0};
         a.ops[1] = Op{OP_EXPECT, 0, 0, 0};
@@ -601,7 +649,14 @@ qaoa_status qaoa_state_reset(qaoa_state s) {
     if (!s) return fail(QAOA_ERR_INVALID, "state is NULL");
     s->lazy = true;
     s->exp_valid = false;
+    s->compl_ = false;
     return QAOA_OK;
+}
+
+qaoa_status qaoa_state_sync(qaoa_state s) {
+    if (!s) return fail(QAOA_ERR_INVALID, "state is NULL");
+    CUDA_TRY(cudaSetDevice(s->dev));
+    return s->prec == QAOA_C64 ? materialize<float>(s) : materialize<double>(s);
 }
 
 qaoa_status qaoa_apply_layers(qaoa_state s, int32_t p, const double* gamma, const double* beta) {

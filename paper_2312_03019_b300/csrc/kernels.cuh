@@ -3,7 +3,7 @@
 // Kernels:
 //   coeff_kernel   per level k: phase table T_k[c] = exp(-i gamma_k c), c = 0..|E| (FP64
 //                  sincos, rounded to the state precision) and the mixer coefficients: (cos b,
-//                  sin b) and the factored butterfly (A, T), (scale, mode) described at `rx`.
+//                  sin b) and the factored butterfly t, f described at `rx`.
 //   tile_kernel    one pass over the state in tiles of 2^Q amplitudes (see plan.h): loads a
 //                  tile (or synthesises |+>^n), runs the pass program (RX butterflies in
 //                  registers, register-layout exchanges through swizzled shared memory, the
@@ -48,10 +48,15 @@ __device__ __forceinline__ double2 make_c2(double x, double y) { return make_dou
 
 template <int Q>
 struct TileArgs {
-    int32_t n, cprime, g0, nops;
+    int32_t n, nops, nruns;
     int32_t E1;        // entries per phase table (|E| + 1)
     int32_t need_cut;  // program evaluates C(z)
     double init_amp;   // 2^(-n/2)
+    // Addressing, precomputed on the host for the pass geometry:
+    uint8_t tpos[3][16];     // index bit of thread bit k (k < Q - R) in layout L
+    int64_t rstep[3][8];     // element step x -> x + 1 of the register index, by ctz(x + 1)
+    int64_t rstride[3][8];   // element stride of register bit j in layout L
+    uint8_t run_src[kMaxN], run_len[kMaxN], run_dst[kMaxN];  // tile id bits -> outer index bits
     uint64_t gmask[kMaxN];  // graph_I rows (Table 1): bit v of gmask[u] iff edge (u, v), v > u
     uint32_t locUpper[Q];   // tile-internal upper neighbours of local bit u (local bit order)
     uint32_t locAdj[Q];     // all tile-internal neighbours of local bit u
@@ -60,7 +65,7 @@ struct TileArgs {
     Op ops[kMaxOps];
     void* state;
     const void* phase;   // [level][E1] complex<real>
-    const void* mix;     // [3 * level + i]: (cos b, sin b), (A, T), (scale, mode) as complex<real>
+    const void* mix;     // [3 * level + i]: (cos b, sin b), (t, 0), (f, 0) as complex<real>
     double2* partials;   // [tile] (sum |psi|^2 C, sum |psi|^2)
     uint16_t* cutout;    // [2^n] cut values (OP_CUTVAL)
 };
@@ -79,6 +84,10 @@ struct SmallJob {
 
 struct CoeffArgs {
     int32_t levels, E1;
+    int32_t n;                  // qubits: each level's mixer carries its factor f to the power n
+    int32_t fold_factors;       // 1: multiply the phase tables by the mixers' factors (tile passes)
+    int32_t fold[kLayerChunk];  // 1: the tile passes apply level k as -i X RX(2 beta - pi)
+    int32_t gre, gim;           // exact factor in {1, -i, -1, i} folded into the last phase table
     double gamma[kLayerChunk];
     double beta[kLayerChunk];
     void* phase;
@@ -129,11 +138,21 @@ struct Tile {
     using C2 = typename C2T<real>::type;
     static constexpr int NT = 1 << (Q - R);
     static constexpr int NE = 1 << R;
-    // swizzle shift: 8-byte elements are conflict-free per half warp, 16-byte per quarter warp
-    static constexpr int SW = sizeof(C2) == 8 ? 5 : 4;
+    static constexpr bool kPair = sizeof(C2) == 8;  // two amplitudes per 16-byte vector
 
     static __host__ __device__ constexpr int rlo(int L) { return L == 0 ? Q - R : (L == 1 ? Q - 2 * R : 0); }
-    static __host__ __device__ constexpr uint32_t swz(uint32_t l) { return l ^ ((l >> SW) & 31u); }
+
+    // Shared-memory index swizzle.  It is linear over GF(2) (phys(a ^ b) = phys(a) ^ phys(b)), so
+    // an element's address is a per-thread constant XOR a compile-time constant.
+    //   complex64 (8 B, Q = 13): bits 1..3 ^= (l5, l6, l7 ^ l8).  Bit 0 is kept, so each pair
+    //     (l, l ^ 1) stays one aligned 16-byte vector.  8-byte accesses of layouts 0 and 1 hit 16
+    //     distinct 8-byte slots per half warp; layout 2 moves pairs with 16-byte accesses, 8
+    //     distinct 16-byte slots per quarter warp.
+    //   complex128 (16 B, Q = 12): bits 0..4 ^= bits 4..8; 8 distinct slots per quarter warp in
+    //     every layout.
+    static __host__ __device__ constexpr uint32_t swz(uint32_t l) {
+        return kPair ? (l ^ (((l >> 4) & 14u) ^ ((l >> 5) & 8u))) : (l ^ ((l >> 4) & 31u));
+    }
 
     // local bits of thread `tid` in layout L (register bits zero)
     static __device__ __forceinline__ uint32_t tbits(int L, uint32_t tid) {
@@ -150,44 +169,16 @@ struct Tile {
         int K;
         const TileArgs<Q>* a;
         int* sE;
-        C2* tile;
     };
 
-    static __device__ __forceinline__ uint64_t gofs(const TileArgs<Q>& a, uint32_t l) {
-        const uint32_t cm = (1u << a.cprime) - 1u;
-        return (uint64_t)(l & cm) | ((uint64_t)(l >> a.cprime) << a.g0);
-    }
-
+    // Element offset of the thread's register-index-0 amplitude in layout L (thread bits only).
     template <int L>
-    static __device__ __forceinline__ void strides(const TileArgs<Q>& a, uint64_t (&st)[R]) {
-#pragma unroll
-        for (int j = 0; j < R; ++j) {
-            const int u = rlo(L) + j;
-            st[j] = u < a.cprime ? (1ull << u) : (1ull << (a.g0 + u - a.cprime));
-        }
-    }
-
-    template <int x>
-    static __device__ __forceinline__ uint64_t xoff(const uint64_t (&st)[R]) {
+    static __device__ __forceinline__ uint64_t toff(const TileArgs<Q>& a, uint32_t tid) {
         uint64_t o = 0;
 #pragma unroll
-        for (int j = 0; j < R; ++j)
-            if ((x >> j) & 1) o += st[j];
+        for (int k = 0; k < Q - R; ++k)
+            if ((tid >> k) & 1u) o |= 1ull << a.tpos[L][k];
         return o;
-    }
-
-    // Byte steps between consecutive register indices x -> x+1: the lowest zero bit j of x is
-    // set and the bits below it cleared, so the offset changes by st[j] - sum_{i<j} st[i].
-    template <int L>
-    static __device__ __forceinline__ void steps(const TileArgs<Q>& a, int64_t (&d)[R]) {
-        uint64_t st[R];
-        strides<L>(a, st);
-        uint64_t below = 0;
-#pragma unroll
-        for (int j = 0; j < R; ++j) {
-            d[j] = (int64_t)((st[j] - below) * sizeof(C2));
-            below += st[j];
-        }
     }
 
     static __host__ __device__ constexpr int ctz_next(int x) {
@@ -199,12 +190,13 @@ struct Tile {
     template <int L>
     static __device__ __forceinline__ void load(C2 (&v)[NE], const Ctx& c, uint32_t tid) {
         const TileArgs<Q>& a = *c.a;
-        const char* g = reinterpret_cast<const char*>(reinterpret_cast<const C2*>(a.state) + c.zb + gofs(a, tbits(L, tid)));
+        const C2* g = reinterpret_cast<const C2*>(a.state) + c.zb + toff<L>(a, tid);
         int64_t d[R];
-        steps<L>(a, d);
+#pragma unroll
+        for (int j = 0; j < R; ++j) d[j] = a.rstep[L][j];
 #pragma unroll
         for (int x = 0; x < NE; ++x) {
-            v[x] = *reinterpret_cast<const C2*>(g);
+            v[x] = *g;
             if (x + 1 < NE) g += d[ctz_next(x)];
         }
     }
@@ -212,28 +204,48 @@ struct Tile {
     template <int L>
     static __device__ __forceinline__ void store(const C2 (&v)[NE], const Ctx& c, uint32_t tid) {
         const TileArgs<Q>& a = *c.a;
-        char* g = reinterpret_cast<char*>(reinterpret_cast<C2*>(a.state) + c.zb + gofs(a, tbits(L, tid)));
+        C2* g = reinterpret_cast<C2*>(a.state) + c.zb + toff<L>(a, tid);
         int64_t d[R];
-        steps<L>(a, d);
+#pragma unroll
+        for (int j = 0; j < R; ++j) d[j] = a.rstep[L][j];
 #pragma unroll
         for (int x = 0; x < NE; ++x) {
-            *reinterpret_cast<C2*>(g) = v[x];
+            *g = v[x];
             if (x + 1 < NE) g += d[ctz_next(x)];
         }
     }
 
+    // Shared-memory exchange: byte offset = (swizzled thread part) XOR (compile-time register part).
     template <int L>
-    static __device__ __forceinline__ void to_smem(const C2 (&v)[NE], C2* tile, uint32_t tid) {
-        const uint32_t P = swz(tbits(L, tid));
+    static __device__ __forceinline__ void to_smem(const C2 (&v)[NE], unsigned char* tile, uint32_t tid) {
+        const uint32_t P = swz(tbits(L, tid)) * (uint32_t)sizeof(C2);
+        if (kPair && L == 2) {  // register bit 0 is local bit 0: store amplitude pairs
 #pragma unroll
-        for (int x = 0; x < NE; ++x) tile[P ^ swz((uint32_t)x << rlo(L))] = v[x];
+            for (int x = 0; x < NE; x += 2)
+                *reinterpret_cast<float4*>(tile + (P ^ (swz((uint32_t)x) * 8u))) =
+                    make_float4((float)v[x].x, (float)v[x].y, (float)v[x + 1].x, (float)v[x + 1].y);
+        } else {
+#pragma unroll
+            for (int x = 0; x < NE; ++x)
+                *reinterpret_cast<C2*>(tile + (P ^ (swz((uint32_t)x << rlo(L)) * (uint32_t)sizeof(C2)))) = v[x];
+        }
     }
 
     template <int L>
-    static __device__ __forceinline__ void from_smem(C2 (&v)[NE], const C2* tile, uint32_t tid) {
-        const uint32_t P = swz(tbits(L, tid));
+    static __device__ __forceinline__ void from_smem(C2 (&v)[NE], const unsigned char* tile, uint32_t tid) {
+        const uint32_t P = swz(tbits(L, tid)) * (uint32_t)sizeof(C2);
+        if (kPair && L == 2) {
 #pragma unroll
-        for (int x = 0; x < NE; ++x) v[x] = tile[P ^ swz((uint32_t)x << rlo(L))];
+            for (int x = 0; x < NE; x += 2) {
+                const float4 q = *reinterpret_cast<const float4*>(tile + (P ^ (swz((uint32_t)x) * 8u)));
+                v[x] = make_c2((real)q.x, (real)q.y);
+                v[x + 1] = make_c2((real)q.z, (real)q.w);
+            }
+        } else {
+#pragma unroll
+            for (int x = 0; x < NE; ++x)
+                v[x] = *reinterpret_cast<const C2*>(tile + (P ^ (swz((uint32_t)x << rlo(L)) * (uint32_t)sizeof(C2))));
+        }
     }
 
     // base(tau) and slopes s_j of the on-the-fly cut count in layout L
@@ -310,62 +322,47 @@ struct Tile {
         const TileArgs<Q>& a = *c.a;
         int s[R];
         const int base = cut_setup<L>(c, tid, s);
-        uint16_t* __restrict__ g = a.cutout + c.zb + gofs(a, tbits(L, tid));
-        uint64_t st[R];
-        strides<L>(a, st);
+        uint16_t* __restrict__ g = a.cutout + c.zb + toff<L>(a, tid);
 #pragma unroll
         for (int x = 0; x < NE; ++x) {
             int cidx = base + a.crtab[L][x];
-            uint64_t o = 0;
+            int64_t o = 0;
 #pragma unroll
             for (int j = 0; j < R; ++j)
                 if ((x >> j) & 1) {
                     cidx += s[j];
-                    o += st[j];
+                    o += a.rstride[L][j];
                 }
             g[o] = (uint16_t)cidx;
         }
     }
 
-    // RX(2b) = [[c, -is], [-is, c]] up to a real factor, one FMA per output component:
-    //   mode 0 (|tan b| <= 1): a' = a - i t b, b' = b - i t a   (t = tan b, factor cos b)
-    //   mode 1 (|cot b| <  1): a' = k a - i b, b' = k b - i a   (k = cot b, factor sin b)
-    // The factors of all RX gates in a pass are multiplied up and applied once (`scale_all`).
-    static __device__ __forceinline__ void rx(C2 (&v)[NE], uint32_t mask, real A, real T, int mode) {
-        if (mode == 0) {
+    // RX(2b) = [[c, -is], [-is, c]] = c * [[1, -it], [-it, 1]] with t = tan b: one FMA per
+    // output component, a' = a - i t b, b' = b - i t a.  The host only hands out |t| <= 1: for
+    // |tan b| > 1 it uses RX(2b) = -i X RX(2b - pi) (see coeff_kernel).  The real factors c are
+    // not applied here; coeff_kernel folds them into the phase tables.  Register bits outside
+    // the op's mask get t = 0, an exact identity, so the code has no data-dependent branches.
+    template <bool kFull>
+    static __device__ __forceinline__ void rx_bits(C2 (&v)[NE], uint32_t mask, real t) {
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            const real T = (kFull || ((mask >> j) & 1u)) ? t : (real)0;
             const real nT = -T;
 #pragma unroll
-            for (int j = 0; j < R; ++j) {
-                if (mask & (1u << j)) {
-#pragma unroll
-                    for (int x = 0; x < NE; ++x)
-                        if (!(x & (1 << j))) {
-                            const C2 p = v[x], q = v[x | (1 << j)];
-                            v[x] = make_c2(fma(T, q.y, p.x), fma(nT, q.x, p.y));
-                            v[x | (1 << j)] = make_c2(fma(T, p.y, q.x), fma(nT, p.x, q.y));
-                        }
+            for (int x = 0; x < NE; ++x)
+                if (!(x & (1 << j))) {
+                    const C2 p = v[x], q = v[x | (1 << j)];
+                    v[x] = make_c2(fma(T, q.y, p.x), fma(nT, q.x, p.y));
+                    v[x | (1 << j)] = make_c2(fma(T, p.y, q.x), fma(nT, p.x, q.y));
                 }
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < R; ++j) {
-                if (mask & (1u << j)) {
-#pragma unroll
-                    for (int x = 0; x < NE; ++x)
-                        if (!(x & (1 << j))) {
-                            const C2 p = v[x], q = v[x | (1 << j)];
-                            v[x] = make_c2(fma(A, p.x, q.y), fma(A, p.y, -q.x));
-                            v[x | (1 << j)] = make_c2(fma(A, q.x, p.y), fma(A, q.y, -p.x));
-                        }
-                }
-            }
         }
     }
 
-    static __device__ __forceinline__ void scale_all(C2 (&v)[NE], real f) {
-#pragma unroll
-        for (int x = 0; x < NE; ++x) v[x] = make_c2(v[x].x * f, v[x].y * f);
+    static __device__ __forceinline__ void rx(C2 (&v)[NE], uint32_t mask, real t) {
+        if (mask == (1u << R) - 1u) rx_bits<true>(v, mask, t);
+        else rx_bits<false>(v, mask, t);
     }
+
 };
 
 #ifndef QAOA_TILE_MIN_BLOCKS
@@ -381,11 +378,11 @@ __global__ void __launch_bounds__(1 << (Q - R), QAOA_TILE_MIN_BLOCKS) tile_kerne
     __shared__ int sK;
     __shared__ double sred[2][T::NT / 32];
 
-    C2* tile = reinterpret_cast<C2*>(smem_raw);
+    unsigned char* tile = smem_raw;
     const uint32_t tid = threadIdx.x;
     const uint64_t t = blockIdx.x;
-    const int nb = a.g0 - a.cprime;
-    const uint64_t zb = ((t & ((1ull << nb) - 1ull)) << a.cprime) | ((t >> nb) << (a.g0 + Q - a.cprime));
+    uint64_t zb = 0;  // outer index bits of tile t: runs of tile-id bits deposited in place
+    for (int r = 0; r < a.nruns; ++r) zb |= ((t >> a.run_src[r]) & ((1ull << a.run_len[r]) - 1ull)) << a.run_dst[r];
 
     if (a.need_cut) {
         if (tid < 32) {
@@ -406,11 +403,9 @@ __global__ void __launch_bounds__(1 << (Q - R), QAOA_TILE_MIN_BLOCKS) tile_kerne
     c.K = a.need_cut ? sK : 0;
     c.a = &a;
     c.sE = sE;
-    c.tile = tile;
 
     C2 v[T::NE];
     int L = 0;
-    real scale = (real)1;  // product of the deferred RX factors not yet applied
     double accC = 0.0, accN = 0.0;
     bool did_expect = false;
 
@@ -441,23 +436,15 @@ __global__ void __launch_bounds__(1 << (Q - R), QAOA_TILE_MIN_BLOCKS) tile_kerne
                 else if (L == 1) T::template from_smem<1>(v, tile, tid);
                 else T::template from_smem<2>(v, tile, tid);
                 break;
-            case OP_RX: {
-                const C2* m = reinterpret_cast<const C2*>(a.mix) + 3 * op.arg;
-                const C2 at = m[1], sm = m[2];
-                T::rx(v, op.mask, at.x, at.y, sm.y != (real)0);
-                for (uint32_t k = op.mask; k; k &= k - 1) scale *= sm.x;
+            case OP_RX:
+                T::rx(v, op.mask, reinterpret_cast<const C2*>(a.mix)[3 * op.arg + 1].x);
                 break;
-            }
             case OP_PHASE:
                 if (L == 0) T::template phase<0>(v, c, tid, op.arg);
                 else if (L == 1) T::template phase<1>(v, c, tid, op.arg);
                 else T::template phase<2>(v, c, tid, op.arg);
                 break;
             case OP_EXPECT:
-                if (scale != (real)1) {
-                    T::scale_all(v, scale);
-                    scale = (real)1;
-                }
                 did_expect = true;
                 if (L == 0) T::template expect<0>(v, c, tid, accC, accN);
                 else if (L == 1) T::template expect<1>(v, c, tid, accC, accN);
@@ -469,10 +456,6 @@ __global__ void __launch_bounds__(1 << (Q - R), QAOA_TILE_MIN_BLOCKS) tile_kerne
                 else T::template cutval<2>(c, tid);
                 break;
             case OP_STORE:
-                if (scale != (real)1) {
-                    T::scale_all(v, scale);
-                    scale = (real)1;
-                }
                 if (L == 0) T::template store<0>(v, c, tid);
                 else if (L == 1) T::template store<1>(v, c, tid);
                 else T::template store<2>(v, c, tid);
@@ -579,28 +562,66 @@ __global__ void __launch_bounds__(kSmallThreads) small_batch_kernel(const SmallJ
 
 // ---------------------------------------------------------------------------------- coefficients
 
+// Per level k: T_k[c] = exp(-i gamma_k c) for c = 0..|E| (the last level's table times the
+// exact factor g = gre + i gim), and the mixer entries (cos b, sin b), (t, 0), (f, 0) with
+// RX(2b) = f [[1, -it], [-it, 1]] (fold = 0: t = tan b, f = cos b) or
+// RX(2b - pi) = f [[1, -it], [-it, 1]] (fold = 1: t = -cot b, f = sin b).
+// With fold_factors, the tile passes never multiply by f: the n factors of level k-1's mixer are
+// folded into T_k, and those of the chunk's last mixer into the last table as well (real
+// scalars commute with every gate; between two phases the state is off by at most
+// (1 / |f|)^n <= 2^(n/2), far inside the floating-point range).
+__device__ __forceinline__ double mixer_factor(double beta, int fold) {
+    double s, co;
+    sincos(beta, &s, &co);
+    return fold ? s : co;
+}
+
 template <typename real>
 __global__ void coeff_kernel(const __grid_constant__ CoeffArgs a) {
     using C2 = typename C2T<real>::type;
     const int k = blockIdx.y;
     C2* T = reinterpret_cast<C2*>(a.phase) + (size_t)k * a.E1;
+    const bool last = k == a.levels - 1;
+    double mult = 1.0;
+    if (a.fold_factors) {
+        if (k > 0) mult *= pow(mixer_factor(a.beta[k - 1], a.fold[k - 1]), (double)a.n);
+        if (last) mult *= pow(mixer_factor(a.beta[k], a.fold[k]), (double)a.n);
+    }
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < a.E1; c += gridDim.x * blockDim.x) {
         double s, co;
         sincos(a.gamma[k] * (double)c, &s, &co);
-        T[c] = make_c2((real)co, (real)(-s));
+        double re = co * mult, im = -s * mult;
+        if (last) {  // (re + i im)(gre + i gim), exact for g in {1, -i, -1, i}
+            const double r2 = re * a.gre - im * a.gim, i2 = re * a.gim + im * a.gre;
+            re = r2;
+            im = i2;
+        }
+        T[c] = make_c2((real)re, (real)im);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         double s, co;
         sincos(a.beta[k], &s, &co);
         C2* m = reinterpret_cast<C2*>(a.mix) + 3 * k;
         m[0] = make_c2((real)co, (real)s);
-        if (fabs(s) <= fabs(co)) {
-            m[1] = make_c2((real)1, (real)(s / co));  // a - i tan(b) b, factor cos b
+        if (!a.fold[k]) {
+            m[1] = make_c2((real)(s / co), (real)0);
             m[2] = make_c2((real)co, (real)0);
         } else {
-            m[1] = make_c2((real)(co / s), (real)1);  // cot(b) a - i b, factor sin b
-            m[2] = make_c2((real)s, (real)1);
+            m[1] = make_c2((real)(-co / s), (real)0);
+            m[2] = make_c2((real)s, (real)0);
         }
+    }
+}
+
+// Reverses the index order of a state in place (psi_z <-> psi_{~z}), one swap per thread.
+template <typename real>
+__global__ void complement_kernel(void* state, uint64_t dim) {
+    using C2 = typename C2T<real>::type;
+    C2* s = reinterpret_cast<C2*>(state);
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < dim / 2; i += (uint64_t)gridDim.x * blockDim.x) {
+        const C2 a = s[i], b = s[dim - 1 - i];
+        s[i] = b;
+        s[dim - 1 - i] = a;
     }
 }
 

@@ -10,41 +10,49 @@ namespace qaoa {
 
 TileConfig tile_config_for(int prec) {
     // complex64: 2^13 amplitudes x 8 B = 64 KiB tile, 32 amplitudes per thread, 256 threads,
-    //            high-group rows of >= 2^3 amplitudes (64 B).
+    //            high-group rows of >= 2^3 amplitudes (64 B); 2 MiB = 2^18 amplitudes.
     // complex128: 2^12 x 16 B = 64 KiB tile, 16 amplitudes per thread, 256 threads,
-    //            high-group rows of >= 2^4 amplitudes (256 B).
-    if (prec == 0) return TileConfig{13, 5, 3};
-    return TileConfig{12, 4, 4};
+    //            high-group rows of >= 2^4 amplitudes (256 B); 2 MiB = 2^17 amplitudes.
+    if (prec == 0) return TileConfig{13, 5, 3, 18};
+    return TileConfig{12, 4, 4, 17};
 }
 
 std::vector<Group> make_groups(int n, const TileConfig& tc) {
-    std::vector<Group> g;
-    g.push_back(Group{0, std::min(n, tc.Q)});
-    int rest = n - tc.Q;
+    std::vector<Group> g(1);
+    for (int b = 0; b < std::min(n, tc.Q); ++b) g[0].bits.push_back(b);
+    const int rest = n - tc.Q;
     if (rest > 0) {
         const int cap = tc.Q - tc.cmin;
         const int ng = (rest + cap - 1) / cap;
-        const int base = rest / ng, extra = rest % ng;
-        int lo = tc.Q;
-        for (int i = 0; i < ng; ++i) {
-            // larger groups go last (highest bits): their rows are shortest, the others' longest
-            const int sz = base + (i >= ng - extra ? 1 : 0);
-            g.push_back(Group{lo, sz});
-            lo += sz;
-        }
+        g.resize(1 + ng);
+        int i = 0;
+        for (int b = n - 1; b >= tc.Q; --b, ++i) g[1 + i % ng].bits.push_back(b);
+        for (int k = 1; k <= ng; ++k) std::sort(g[k].bits.begin(), g[k].bits.end());
     }
     return g;
 }
 
 Geometry group_geometry(const Group& g, const TileConfig& tc) {
-    if (g.lo == 0) return Geometry{tc.Q, tc.Q};
-    return Geometry{tc.Q - g.size, g.lo};
+    Geometry geo;
+    const bool low = !g.bits.empty() && g.bits[0] == 0;
+    geo.cprime = low ? tc.Q : tc.Q - g.size();
+    for (int u = 0; u < geo.cprime; ++u) geo.gpos[u] = u;
+    if (!low)
+        for (int j = 0; j < g.size(); ++j) geo.gpos[geo.cprime + j] = g.bits[j];
+    return geo;
+}
+
+Geometry low_geometry(const TileConfig& tc) {
+    Geometry geo;
+    geo.cprime = tc.Q;
+    for (int u = 0; u < tc.Q; ++u) geo.gpos[u] = u;
+    return geo;
 }
 
 uint32_t group_target_mask(const Group& g, const TileConfig& tc) {
     const uint32_t all = (1u << tc.Q) - 1u;
-    if (g.lo == 0) return all;
     const Geometry geo = group_geometry(g, tc);
+    if (geo.cprime == tc.Q) return all;
     return all & ~((1u << geo.cprime) - 1u);
 }
 
@@ -54,9 +62,17 @@ Plan plan_levels(int n, const TileConfig& tc, int levels, bool synth_first, bool
     plan.tc = tc;
     plan.groups = make_groups(n, tc);
     const int g = (int)plan.groups.size();
+    std::vector<int> order;  // group order of even levels; odd levels run it backwards
+    if (g >= 3) {
+        order.push_back(1);
+        order.push_back(0);
+        for (int i = 2; i < g; ++i) order.push_back(i);
+    } else {
+        for (int i = 0; i < g; ++i) order.push_back(i);
+    }
     for (int k = 0; k < levels; ++k) {
         for (int idx = 0; idx < g; ++idx) {
-            const int grp = (k % 2 == 0) ? idx : g - 1 - idx;
+            const int grp = (k % 2 == 0) ? order[idx] : order[g - 1 - idx];
             if (idx == 0 && k > 0) {
                 // same group as the last pass of level k-1: fuse phase + mixer into it
                 Pass& cur = plan.passes.back();
@@ -195,8 +211,8 @@ std::vector<int32_t> describe(const Plan& plan) {
     d.push_back(plan.tc.cmin);
     d.push_back((int32_t)plan.groups.size());
     for (const Group& g : plan.groups) {
-        d.push_back(g.lo);
-        d.push_back(g.size);
+        d.push_back(g.size());
+        for (int b : g.bits) d.push_back(b);
     }
     d.push_back((int32_t)plan.passes.size());
     for (const Pass& ps : plan.passes) {

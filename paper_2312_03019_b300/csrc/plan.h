@@ -9,10 +9,11 @@
 // RX gates on different qubits commute and the cost phase is elementwise, so a level is
 // ceil-many passes over groups that together cover all n qubits.
 //
-// Consecutive levels alternate the group order (0,1,..,g-1 then g-1,..,0), so the last
-// group of level k is the first group of level k+1: one pass then applies RX(level k) on
-// that group, the phase of level k+1 and RX(level k+1) on the same group.  A run of p levels
-// costs p*(g-1)+1 passes instead of p*g.
+// Consecutive levels reverse the group order, so the last group of level k is the first group
+// of level k+1: one pass then applies RX(level k) on that group, the phase of level k+1 and
+// RX(level k+1) on the same group.  A run of p levels costs p*(g-1)+1 passes instead of p*g.
+// With three or more groups the order is (1, 0, 2, .., g-1): group 0, whose pass needs the most
+// register-layout exchanges, is never one of the fused boundary passes.
 //
 // Inside a tile each thread holds 2^R amplitudes in registers.  Three register layouts
 // assign R of the Q local bits to the register index (where the RX butterflies are computed
@@ -54,9 +55,10 @@ struct Op {
 };
 
 struct TileConfig {
-    int Q;     // local bits per tile
-    int R;     // register bits per thread
-    int cmin;  // minimum contiguous row bits in a high-group pass
+    int Q;         // local bits per tile
+    int R;         // register bits per thread
+    int cmin;      // minimum contiguous row bits in a high-group pass
+    int page_bit;  // lowest index bit whose stride is >= 2 MiB (a GPU page) for this element size
     int regLo(int layout) const { return layout == 0 ? Q - R : (layout == 1 ? Q - 2 * R : 0); }
     uint32_t regMask(int layout) const { return ((1u << R) - 1u) << regLo(layout); }
     int threads() const { return 1 << (Q - R); }
@@ -64,14 +66,17 @@ struct TileConfig {
 
 TileConfig tile_config_for(int prec /*0 = c64, 1 = c128*/);
 
+// A mixer group: the index bits (qubits) whose RX gates one pass applies, ascending.
 struct Group {
-    int lo;    // first global qubit of the group
-    int size;  // number of qubits
+    std::vector<int> bits;
+    int size() const { return (int)bits.size(); }
 };
 
+// Tile geometry of a pass: local bits [0, cprime) are the lowest index bits (contiguous rows);
+// local bit u >= cprime is index bit gpos[u].
 struct Geometry {
-    int cprime;  // local bits [0, c') = global bits [0, c')
-    int g0;      // local bit c' + j = global bit g0 + j
+    int cprime = 0;
+    int gpos[16] = {};
 };
 
 // Logical op of a pass before layout assignment.
@@ -95,10 +100,15 @@ struct Plan {
     std::vector<Pass> passes;
 };
 
-// Mixer groups for n >= Q qubits: group 0 = [0, Q), the rest of [Q, n) split into balanced
-// contiguous groups of at most Q - cmin qubits.
+// Mixer groups for n >= Q qubits: group 0 = bits [0, Q); the bits of [Q, n) are dealt from the
+// top down, round robin, into balanced groups of at most Q - cmin bits.  Dealing spreads the
+// bits above page_bit evenly, so no tile's rows fall into more distinct 2 MiB pages than
+// necessary (rows of a tile whose group bits all lie above page_bit sit in 2^|G| different
+// pages, which measurably slows the pass down).
 std::vector<Group> make_groups(int n, const TileConfig& tc);
 Geometry group_geometry(const Group& g, const TileConfig& tc);
+// Geometry of group 0 (the contiguous tile of bits [0, Q)); allocates nothing.
+Geometry low_geometry(const TileConfig& tc);
 uint32_t group_target_mask(const Group& g, const TileConfig& tc);
 
 // Passes for `levels` levels starting from a materialised state (or a deferred |+>^n when

@@ -75,8 +75,9 @@ def _parse_plan(d):
     pos = 4
     groups = []
     for _ in range(ng):
-        groups.append((d[pos], d[pos + 1]))
-        pos += 2
+        sz = d[pos]
+        groups.append(list(d[pos + 1: pos + 1 + sz]))
+        pos += 1 + sz
     npass = d[pos]
     pos += 1
     passes = []
@@ -98,13 +99,18 @@ def test_plan_applies_each_rx_once_per_level(lib, prec, n, p):
         pytest.skip("small-state kernel")
     d = lib.qaoa_plan_describe(n, prec, p)
     Q, R, cmin, groups, passes = _parse_plan(d)
-    # groups partition [0, n); group 0 is [0, Q); high groups leave >= cmin row bits
+    # groups partition [0, n); group 0 is [0, Q); high groups leave >= cmin row bits and hold
+    # balanced numbers of bits, and of bits above the 2 MiB page boundary
     cover = []
-    for lo, sz in groups:
-        cover += list(range(lo, lo + sz))
+    for bits in groups:
+        cover += bits
     assert sorted(cover) == list(range(n))
-    assert groups[0] == (0, Q)
-    assert all(sz <= Q - cmin for lo, sz in groups[1:])
+    assert groups[0] == list(range(Q))
+    sizes = [len(b) for b in groups[1:]]
+    assert all(sz <= Q - cmin for sz in sizes) and max(sizes) - min(sizes) <= 1
+    page_bit = 18 if prec == "c64" else 17
+    high = [sum(1 for b in bits if b >= page_bit) for bits in groups[1:]]
+    assert max(high) - min(high) <= 1
     g = len(groups)
     assert len(passes) == p * (g - 1) + 1
 
@@ -114,9 +120,10 @@ def test_plan_applies_each_rx_once_per_level(lib, prec, n, p):
     expect_at = None
     events = []  # sequence of ("rx", level) / ("phase", level)
     for pi, (grp, ops) in enumerate(passes):
-        lo, sz = groups[grp]
-        cprime, g0 = (Q, Q) if lo == 0 else (Q - sz, lo)
-        target = (1 << Q) - 1 if lo == 0 else ((1 << Q) - 1) & ~((1 << cprime) - 1)
+        bits = groups[grp]
+        cprime = Q if grp == 0 else Q - len(bits)
+        gpos = list(range(Q)) if grp == 0 else list(range(cprime)) + bits
+        target = (1 << Q) - 1 if grp == 0 else ((1 << Q) - 1) & ~((1 << cprime) - 1)
         kind0, lay0, _ = ops[0]
         assert kind0 == (2 if pi == 0 else 1)  # synthesise |+> only in the first pass
         assert lay0 in (0, 1)
@@ -130,7 +137,7 @@ def test_plan_applies_each_rx_once_per_level(lib, prec, n, p):
                 assert mask and (mask & ~regmask) == 0 and (mask & ~target) == 0
                 for u in range(Q):
                     if (mask >> u) & 1:
-                        rx_seen[arg].append(u if u < cprime else g0 + u - cprime)
+                        rx_seen[arg].append(gpos[u])
                 events.append(("rx", arg))
             elif kind == 5:
                 phases.append(arg)
@@ -148,6 +155,10 @@ def test_plan_applies_each_rx_once_per_level(lib, prec, n, p):
             assert all(kk < k for w, kk in events[:idx] if w == "rx")
             assert all(kk >= k for w, kk in events[idx + 1:] if w == "rx")
     assert expect_at == (len(passes) - 1, len(events))
+    if g >= 3:  # group 0 is never a fused boundary pass
+        for grp, ops in passes:
+            if grp == 0:
+                assert sum(1 for k, _, _ in ops if k == 5) == 0
 
 
 def test_small_states_have_no_pass_plan(lib):
