@@ -28,6 +28,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "plan.h"
 
 namespace qaoa {
@@ -101,6 +103,23 @@ __device__ __forceinline__ C2 cmul(C2 a, C2 b) {
     return make_c2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
+// d = a * b + c on two float lanes at once (one packed FMA instruction on sm_100 and later).
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+
+__host__ __device__ constexpr bool odd_parity(int x) {
+    int p = 0;
+    for (; x; x &= x - 1) p ^= 1;
+    return p != 0;
+}
+
 // RX(2 beta) = [[c, -i s], [-i s, c]] on the pair (a, b) = (bit 0, bit 1).
 template <typename C2, typename real>
 __device__ __forceinline__ void rx_pair(C2& a, C2& b, real c, real s) {
@@ -139,6 +158,19 @@ struct Tile {
     static constexpr int NT = 1 << (Q - R);
     static constexpr int NE = 1 << R;
     static constexpr bool kPair = sizeof(C2) == 8;  // two amplitudes per 16-byte vector
+
+    // complex64 register representation: register slot x holds (re, im) when x has an even
+    // number of set bits and (im, re) when odd.  Every butterfly then pairs one slot of each
+    // kind and becomes two packed FMAs (see rx_bits); the swap is undone wherever amplitudes
+    // leave registers (HBM, shared memory) and re-applied when they come back.
+    static constexpr bool kSwapOdd = kPair;
+    template <int x>
+    static __device__ __forceinline__ C2 to_reg(C2 z) {
+        if constexpr (kSwapOdd && odd_parity(x)) return make_c2(z.y, z.x);
+        else return z;
+    }
+    template <int x>
+    static __device__ __forceinline__ C2 from_reg(C2 z) { return to_reg<x>(z); }
 
     static __host__ __device__ constexpr int rlo(int L) { return L == 0 ? Q - R : (L == 1 ? Q - 2 * R : 0); }
 
@@ -181,6 +213,15 @@ struct Tile {
         return o;
     }
 
+    // Calls f(std::integral_constant<int, x>) for x = 0 .. N-1 (compile-time register indices).
+    template <int N, typename F, int x = 0>
+    static __device__ __forceinline__ void for_x(F&& f) {
+        if constexpr (x < N) {
+            f(std::integral_constant<int, x>{});
+            for_x<N, F, x + 1>(static_cast<F&&>(f));
+        }
+    }
+
     static __host__ __device__ constexpr int ctz_next(int x) {
         int j = 0;
         while ((((x + 1) >> j) & 1) == 0) ++j;
@@ -194,11 +235,11 @@ struct Tile {
         int64_t d[R];
 #pragma unroll
         for (int j = 0; j < R; ++j) d[j] = a.rstep[L][j];
-#pragma unroll
-        for (int x = 0; x < NE; ++x) {
-            v[x] = *g;
-            if (x + 1 < NE) g += d[ctz_next(x)];
-        }
+        for_x<NE>([&](auto X) {
+            constexpr int x = decltype(X)::value;
+            v[x] = to_reg<x>(*g);
+            if constexpr (x + 1 < NE) g += d[ctz_next(x)];
+        });
     }
 
     template <int L>
@@ -208,43 +249,47 @@ struct Tile {
         int64_t d[R];
 #pragma unroll
         for (int j = 0; j < R; ++j) d[j] = a.rstep[L][j];
-#pragma unroll
-        for (int x = 0; x < NE; ++x) {
-            *g = v[x];
-            if (x + 1 < NE) g += d[ctz_next(x)];
-        }
+        for_x<NE>([&](auto X) {
+            constexpr int x = decltype(X)::value;
+            *g = from_reg<x>(v[x]);
+            if constexpr (x + 1 < NE) g += d[ctz_next(x)];
+        });
     }
 
     // Shared-memory exchange: byte offset = (swizzled thread part) XOR (compile-time register part).
     template <int L>
     static __device__ __forceinline__ void to_smem(const C2 (&v)[NE], unsigned char* tile, uint32_t tid) {
         const uint32_t P = swz(tbits(L, tid)) * (uint32_t)sizeof(C2);
-        if (kPair && L == 2) {  // register bit 0 is local bit 0: store amplitude pairs
-#pragma unroll
-            for (int x = 0; x < NE; x += 2)
+        if constexpr (kPair && L == 2) {  // register bit 0 is local bit 0: store amplitude pairs
+            for_x<NE / 2>([&](auto H) {
+                constexpr int x = 2 * decltype(H)::value;
+                const C2 a = from_reg<x>(v[x]), b = from_reg<x + 1>(v[x + 1]);
                 *reinterpret_cast<float4*>(tile + (P ^ (swz((uint32_t)x) * 8u))) =
-                    make_float4((float)v[x].x, (float)v[x].y, (float)v[x + 1].x, (float)v[x + 1].y);
+                    make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
+            });
         } else {
-#pragma unroll
-            for (int x = 0; x < NE; ++x)
-                *reinterpret_cast<C2*>(tile + (P ^ (swz((uint32_t)x << rlo(L)) * (uint32_t)sizeof(C2)))) = v[x];
+            for_x<NE>([&](auto X) {
+                constexpr int x = decltype(X)::value;
+                *reinterpret_cast<C2*>(tile + (P ^ (swz((uint32_t)x << rlo(L)) * (uint32_t)sizeof(C2)))) = from_reg<x>(v[x]);
+            });
         }
     }
 
     template <int L>
     static __device__ __forceinline__ void from_smem(C2 (&v)[NE], const unsigned char* tile, uint32_t tid) {
         const uint32_t P = swz(tbits(L, tid)) * (uint32_t)sizeof(C2);
-        if (kPair && L == 2) {
-#pragma unroll
-            for (int x = 0; x < NE; x += 2) {
+        if constexpr (kPair && L == 2) {
+            for_x<NE / 2>([&](auto H) {
+                constexpr int x = 2 * decltype(H)::value;
                 const float4 q = *reinterpret_cast<const float4*>(tile + (P ^ (swz((uint32_t)x) * 8u)));
-                v[x] = make_c2((real)q.x, (real)q.y);
-                v[x + 1] = make_c2((real)q.z, (real)q.w);
-            }
+                v[x] = to_reg<x>(make_c2((real)q.x, (real)q.y));
+                v[x + 1] = to_reg<x + 1>(make_c2((real)q.z, (real)q.w));
+            });
         } else {
-#pragma unroll
-            for (int x = 0; x < NE; ++x)
-                v[x] = *reinterpret_cast<const C2*>(tile + (P ^ (swz((uint32_t)x << rlo(L)) * (uint32_t)sizeof(C2))));
+            for_x<NE>([&](auto X) {
+                constexpr int x = decltype(X)::value;
+                v[x] = to_reg<x>(*reinterpret_cast<const C2*>(tile + (P ^ (swz((uint32_t)x << rlo(L)) * (uint32_t)sizeof(C2)))));
+            });
         }
     }
 
@@ -285,15 +330,19 @@ struct Tile {
         int s[R];
         const int base = cut_setup<L>(c, tid, s);
         const C2* __restrict__ T = reinterpret_cast<const C2*>(a.phase) + (size_t)level * a.E1;
-#pragma unroll
-        for (int x = 0; x < NE; ++x) {
+        for_x<NE>([&](auto X) {
+            constexpr int x = decltype(X)::value;
             int cidx = base + a.crtab[L][x];
 #pragma unroll
             for (int j = 0; j < R; ++j)
                 if ((x >> j) & 1) cidx += s[j];
             // the count is always in [0, |E|]; the unsigned clamp keeps every table read in bounds
-            v[x] = cmul(v[x], __ldg(T + min((unsigned)cidx, (unsigned)(a.E1 - 1))));
-        }
+            const C2 f = __ldg(T + min((unsigned)cidx, (unsigned)(a.E1 - 1)));
+            if constexpr (kSwapOdd && odd_parity(x))  // slot holds (im, re)
+                v[x] = make_c2(v[x].x * f.x + v[x].y * f.y, v[x].y * f.x - v[x].x * f.y);
+            else
+                v[x] = cmul(v[x], f);
+        });
     }
 
     template <int L>
@@ -342,19 +391,36 @@ struct Tile {
     // |tan b| > 1 it uses RX(2b) = -i X RX(2b - pi) (see coeff_kernel).  The real factors c are
     // not applied here; coeff_kernel folds them into the phase tables.  Register bits outside
     // the op's mask get t = 0, an exact identity, so the code has no data-dependent branches.
+    // complex64: with N the (re, im) slot and S the (im, re) slot of a pair,
+    //   N' = (t, -t) * S + N   and   S' = (-t, t) * N + S   (two packed FMAs per pair).
     template <bool kFull>
     static __device__ __forceinline__ void rx_bits(C2 (&v)[NE], uint32_t mask, real t) {
 #pragma unroll
         for (int j = 0; j < R; ++j) {
             const real T = (kFull || ((mask >> j) & 1u)) ? t : (real)0;
             const real nT = -T;
-#pragma unroll
-            for (int x = 0; x < NE; ++x)
+            for_x<NE>([&](auto X) {
+                constexpr int x = decltype(X)::value;
                 if (!(x & (1 << j))) {
-                    const C2 p = v[x], q = v[x | (1 << j)];
-                    v[x] = make_c2(fma(T, q.y, p.x), fma(nT, q.x, p.y));
-                    v[x | (1 << j)] = make_c2(fma(T, p.y, q.x), fma(nT, p.x, q.y));
+                    const int y = x | (1 << j);
+                    if constexpr (kSwapOdd) {
+                        const C2 cp = make_c2(T, nT), cm = make_c2(nT, T);
+                        if constexpr (!odd_parity(x)) {
+                            const C2 n0 = v[x], s0 = v[y];
+                            v[x] = ffma2(cp, s0, n0);
+                            v[y] = ffma2(cm, n0, s0);
+                        } else {
+                            const C2 n0 = v[y], s0 = v[x];
+                            v[y] = ffma2(cp, s0, n0);
+                            v[x] = ffma2(cm, n0, s0);
+                        }
+                    } else {
+                        const C2 p = v[x], q = v[y];
+                        v[x] = make_c2(fma(T, q.y, p.x), fma(nT, q.x, p.y));
+                        v[y] = make_c2(fma(T, p.y, q.x), fma(nT, p.x, q.y));
+                    }
                 }
+            });
         }
     }
 
@@ -414,8 +480,10 @@ __global__ void __launch_bounds__(1 << (Q - R), QAOA_TILE_MIN_BLOCKS) tile_kerne
         switch (op.kind) {
             case OP_SYNTH: {
                 const real amp = (real)a.init_amp;
-#pragma unroll
-                for (int x = 0; x < T::NE; ++x) v[x] = make_c2(amp, (real)0);
+                T::template for_x<T::NE>([&](auto X) {
+                    constexpr int x = decltype(X)::value;
+                    v[x] = T::template to_reg<x>(make_c2(amp, (real)0));
+                });
                 L = op.layout;
                 break;
             }
