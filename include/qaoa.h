@@ -105,6 +105,22 @@ qaoa_status qaoa_apply_layers(qaoa_state s, int32_t p, const double *gamma, cons
  * reduced in FP64 in a fixed order (run-to-run identical).  Synchronises the stream. */
 qaoa_status qaoa_expectation(qaoa_state s, double *out_c, double *out_norm);
 
+/* <C> of the p-level circuit from |+>^n and its gradient d<C>/d gamma_k, d<C>/d beta_k
+ * (k = 0..p-1), by one forward run and one adjoint sweep (no per-level storage).  With
+ * psi_k the state after level k and lambda_k = (U_p .. U_{k+1})^dagger C psi_p:
+ *   d<C>/d beta_k  = 2 Im <lambda_k| sum_j X_j |psi_k>,
+ *   d<C>/d gamma_k = 2 Im <M_k^dagger lambda_k| C |M_k^dagger psi_k>,
+ * and psi, lambda are uncomputed level by level with the inverse mixer and phase.  The sweep
+ * keeps psi in the state buffer and lambda in dev_work, a caller-owned device buffer of at
+ * least qaoa_state_bytes(n, prec) bytes (16-byte aligned, not the state buffer), which it
+ * overwrites.  Sums are reduced in FP64 in a fixed order.  Afterwards the state is |+>^n
+ * (deferred).  Writes <C> to *out_c (may be NULL) and the 2p derivatives to d_gamma[0..p-1] and
+ * d_beta[0..p-1]; synchronises the stream.  Allocates gradient workspace on first use (p phase
+ * tables, 2 doubles per tile).  QAOA_ERR_INVALID on p < 1, non-finite angles or a bad buffer. */
+qaoa_status qaoa_gradient(qaoa_state s, int32_t p, const double *gamma, const double *beta,
+                          void *dev_work, size_t work_bytes, double *out_c, double *d_gamma,
+                          double *d_beta);
+
 /* Copies the current state (bytes = qaoa_state_bytes) to host memory, writing out a deferred
  * |+>^n first.  Synchronises the stream.  Parity hook. */
 qaoa_status qaoa_state_copy_out(qaoa_state s, void *host_dst, size_t bytes);

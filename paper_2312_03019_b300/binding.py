@@ -77,6 +77,7 @@ _sig("qaoa_state_reset", ctypes.c_int, [_vp])
 _sig("qaoa_state_sync", ctypes.c_int, [_vp])
 _sig("qaoa_apply_layers", ctypes.c_int, [_vp, _i32, _dp, _dp])
 _sig("qaoa_expectation", ctypes.c_int, [_vp, _dp, _dp])
+_sig("qaoa_gradient", ctypes.c_int, [_vp, _i32, _dp, _dp, _vp, ctypes.c_size_t, _dp, _dp, _dp])
 _sig("qaoa_state_copy_out", ctypes.c_int, [_vp, _vp, ctypes.c_size_t])
 _sig("qaoa_state_free", ctypes.c_int, [_vp])
 _sig("qaoa_cut_table", ctypes.c_int, [ctypes.POINTER(_Graph), _vp])
@@ -149,6 +150,20 @@ def qaoa_expectation(h: int):
     nn = ctypes.c_double()
     _check(_lib.qaoa_expectation(_vp(h), ctypes.byref(c), ctypes.byref(nn)))
     return c.value, nn.value
+
+
+def qaoa_gradient(h: int, gamma, beta, work_ptr: int, work_bytes: int):
+    """(<C>, d<C>/d gamma, d<C>/d beta) by a forward run and an adjoint sweep on the GPU."""
+    ga = np.ascontiguousarray(np.asarray(gamma, dtype=np.float64).reshape(-1))
+    be = np.ascontiguousarray(np.asarray(beta, dtype=np.float64).reshape(-1))
+    if ga.size != be.size:
+        raise ValueError("gamma and beta must have the same length")
+    dg = np.zeros(ga.size)
+    db = np.zeros(ga.size)
+    c = ctypes.c_double()
+    _check(_lib.qaoa_gradient(_vp(h), int(ga.size), ga.ctypes.data_as(_dp), be.ctypes.data_as(_dp), _vp(work_ptr),
+                              work_bytes, ctypes.byref(c), dg.ctypes.data_as(_dp), db.ctypes.data_as(_dp)))
+    return c.value, dg, db
 
 
 def qaoa_expectation_static(g, prec, dev_ptr: int, nbytes: int, stream: int = 0):

@@ -186,6 +186,12 @@ struct qaoa_state_s {
     double2* d_result = nullptr;
     double2* h_result = nullptr;
     uint64_t partial_count = 0;
+    // adjoint sweep workspace (allocated on the first qaoa_gradient call, grown as needed)
+    int grad_levels = 0;
+    void* d_gtab = nullptr;       // plain phase tables, [level][E1]
+    void* d_gmix = nullptr;       // [3 * level] mixer entries
+    double* d_gacc = nullptr;     // [2 * levels]
+    double2* d_gpart = nullptr;   // [2 * tiles]
     bool lazy = true;
     bool exp_valid = false;
     bool compl_ = false;  // buffer index z holds the amplitude of ~z (pending X on every qubit)
@@ -418,6 +424,10 @@ void release(qaoa_state s) {
     cudaFree(s->d_mix);
     cudaFree(s->d_partials);
     cudaFree(s->d_result);
+    cudaFree(s->d_gtab);
+    cudaFree(s->d_gmix);
+    cudaFree(s->d_gacc);
+    cudaFree(s->d_gpart);
     if (s->h_result) cudaFreeHost(s->h_result);
     delete s;
 }
@@ -593,6 +603,142 @@ qaoa_status expectation_static_impl(const HostGraph& hg, const void* dev_state, 
 
 }  // namespace
 
+namespace {
+
+qaoa_status grad_workspace(qaoa_state s, int p) {
+    if (p <= s->grad_levels && s->d_gtab) return QAOA_OK;
+    cudaFree(s->d_gtab);
+    cudaFree(s->d_gmix);
+    cudaFree(s->d_gacc);
+    cudaFree(s->d_gpart);
+    s->d_gtab = s->d_gmix = nullptr;
+    s->d_gacc = nullptr;
+    s->d_gpart = nullptr;
+    s->grad_levels = 0;
+    const size_t eb = elem_bytes(s->prec);
+    cudaError_t e = cudaMalloc(&s->d_gtab, (size_t)p * (s->g.m + 1) * eb);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_gmix, (size_t)3 * p * eb);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_gacc, (size_t)2 * p * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_gpart, (size_t)2 * s->ntiles * sizeof(double2));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(QAOA_ERR_OOM, std::string("gradient workspace allocation failed: ") + cudaGetErrorString(e));
+    }
+    s->grad_levels = p;
+    return QAOA_OK;
+}
+
+template <typename real>
+qaoa_status gradient_impl(qaoa_state s, int p, const double* gamma, const double* beta, void* work,
+                          double* out_c, double* d_gamma, double* d_beta) {
+    // forward levels from |+>^n, <C> from the fused reduction
+    s->lazy = true;
+    s->exp_valid = false;
+    s->compl_ = false;
+    qaoa_status st = QAOA_OK;
+    for (int k0 = 0; k0 < p && st == QAOA_OK; k0 += kLayerChunk) {
+        const int levels = std::min(kLayerChunk, p - k0);
+        st = apply_chunk<real>(s, levels, gamma + k0, beta + k0, k0 + levels == p);
+    }
+    if (st != QAOA_OK) return st;
+    st = expectation_impl<real>(s, out_c, nullptr);
+    if (st != QAOA_OK) return st;
+    st = grad_workspace(s, p);
+    if (st != QAOA_OK) return st;
+    using C2 = typename C2T<real>::type;
+    // plain per-level tables (no folded factors) for the sweep
+    for (int k0 = 0; k0 < p; k0 += kLayerChunk) {
+        const int levels = std::min(kLayerChunk, p - k0);
+        CoeffArgs ca;
+        std::memset(&ca, 0, sizeof(ca));
+        ca.levels = levels;
+        ca.E1 = s->g.m + 1;
+        ca.n = s->n;
+        ca.fold_factors = 0;
+        ca.gre = 1;
+        ca.gim = 0;
+        for (int k = 0; k < levels; ++k) {
+            ca.gamma[k] = gamma[k0 + k];
+            ca.beta[k] = beta[k0 + k];
+        }
+        ca.phase = reinterpret_cast<C2*>(s->d_gtab) + (size_t)k0 * (s->g.m + 1);
+        ca.mix = reinterpret_cast<C2*>(s->d_gmix) + (size_t)3 * k0;
+        dim3 grid((unsigned)std::max(1, (ca.E1 + 255) / 256), (unsigned)levels);
+        coeff_kernel<real><<<grid, 256, 0, s->stream>>>(ca);
+        CUDA_TRY(cudaGetLastError());
+        s->launches++;
+    }
+    CUDA_TRY(cudaMemsetAsync(s->d_gacc, 0, (size_t)2 * p * sizeof(double), s->stream));
+    constexpr int Q = PrecTraits<real>::Q, R = PrecTraits<real>::R;
+    if (s->n <= Q) {
+        SmallGradJob j;
+        std::memset(&j, 0, sizeof(j));
+        j.n = s->n;
+        j.levels = p;
+        j.E1 = s->g.m + 1;
+        for (int v = 0; v < kMaxN; ++v) j.gmask[v] = v < s->n ? s->g.upper[v] : 0;
+        j.state = s->buf;
+        j.phase = s->d_gtab;
+        j.mix = s->d_gmix;
+        j.acc = s->d_gacc;
+        auto kfn = small_grad_kernel<real>;
+        static bool attr = false;
+        if (!attr) {
+            CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * (1 << Q) * (int)sizeof(C2)));
+            attr = true;
+        }
+        kfn<<<1, kSmallThreadsGrad, (size_t)2 * s->dim * sizeof(C2), s->stream>>>(j);
+        CUDA_TRY(cudaGetLastError());
+        s->launches++;
+    } else {
+        Plan plan;
+        try {
+            plan = plan_backward(s->n, s->tc, p);
+        } catch (const std::exception& ex) {
+            return fail(QAOA_ERR_UNSUPPORTED, ex.what());
+        }
+        auto kfn = grad_kernel<real, Q, R>;
+        const size_t smem = (size_t)(1u << Q) * sizeof(C2);
+        static bool attr = false;
+        if (!attr) {
+            CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            attr = true;
+        }
+        TileArgs<Q> a;
+        for (const Pass& ps : plan.passes) {
+            std::memset(&a, 0, sizeof(a));
+            fill_program<real>(a, s, ps);
+            a.need_cut = 1;
+            a.state2 = work;
+            a.phase = s->d_gtab;
+            a.mix = s->d_gmix;
+            a.partials = s->d_gpart;
+            int lev[2] = {-1, -1};
+            for (const Op& op : ps.ops)
+                if (op.kind == OP_RXD || op.kind == OP_GRADG) lev[(op.arg >> 16) & 1] = op.arg & 0xffff;
+            kfn<<<(unsigned)s->ntiles, 1u << (Q - R), smem, s->stream>>>(a);
+            CUDA_TRY(cudaGetLastError());
+            grad_reduce_kernel<<<1, 1024, 0, s->stream>>>(s->d_gpart, s->ntiles, lev[0], lev[1], p, s->d_gacc);
+            CUDA_TRY(cudaGetLastError());
+            s->launches += 2;
+        }
+    }
+    std::vector<double> host(2 * (size_t)p);
+    CUDA_TRY(cudaMemcpyAsync(host.data(), s->d_gacc, host.size() * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    for (int k = 0; k < p; ++k) {
+        d_beta[k] = 2.0 * host[k];
+        d_gamma[k] = 2.0 * host[p + k];
+    }
+    // the sweep consumed the state: it is |+>^n again
+    s->lazy = true;
+    s->exp_valid = false;
+    s->compl_ = false;
+    return QAOA_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 size_t qaoa_state_bytes(int32_t n, qaoa_prec prec) {
@@ -624,7 +770,7 @@ qaoa_status qaoa_state_init(const qaoa_graph* g, qaoa_prec prec, void* dev_buf, 
     s->g = hg;
     s->tc = tile_config_for(prec);
     s->small = is_small(hg.n, prec);
-    if (!s->small) {
+    if (hg.n > s->tc.Q) {  // tiled passes (and the adjoint sweep of a small state above Q)
         s->groups = make_groups(hg.n, s->tc);
         s->ntiles = 1ull << (hg.n - s->tc.Q);
     }
@@ -674,6 +820,24 @@ qaoa_status qaoa_apply_layers(qaoa_state s, int32_t p, const double* gamma, cons
         if (st != QAOA_OK) return st;
     }
     return QAOA_OK;
+}
+
+qaoa_status qaoa_gradient(qaoa_state s, int32_t p, const double* gamma, const double* beta, void* dev_work,
+                          size_t work_bytes, double* out_c, double* d_gamma, double* d_beta) {
+    if (!s) return fail(QAOA_ERR_INVALID, "state is NULL");
+    if (p < 1) return fail(QAOA_ERR_INVALID, "p must be >= 1");
+    if (!gamma || !beta || !d_gamma || !d_beta) return fail(QAOA_ERR_INVALID, "NULL array");
+    if (!angles_ok(p, gamma) || !angles_ok(p, beta)) return fail(QAOA_ERR_INVALID, "non-finite angle");
+    const size_t need = qaoa_state_bytes(s->n, (qaoa_prec)s->prec);
+    if (!dev_work || work_bytes < need) return fail(QAOA_ERR_INVALID, "work buffer missing or too small");
+    if (((uintptr_t)dev_work & 15u) != 0) return fail(QAOA_ERR_INVALID, "work buffer not 16-byte aligned");
+    if (dev_work == s->buf) return fail(QAOA_ERR_INVALID, "work buffer must differ from the state buffer");
+    CUDA_TRY(cudaSetDevice(s->dev));
+    double c = 0.0;
+    qaoa_status st = s->prec == QAOA_C64 ? gradient_impl<float>(s, p, gamma, beta, dev_work, &c, d_gamma, d_beta)
+                                         : gradient_impl<double>(s, p, gamma, beta, dev_work, &c, d_gamma, d_beta);
+    if (st == QAOA_OK && out_c) *out_c = c;
+    return st;
 }
 
 qaoa_status qaoa_expectation(qaoa_state s, double* out_c, double* out_norm) {

@@ -66,9 +66,10 @@ struct TileArgs {
     uint8_t crtab[3][32];   // C_R(x) per register layout
     Op ops[kMaxOps];
     void* state;
+    void* state2;        // adjoint sweep: lambda
     const void* phase;   // [level][E1] complex<real>
     const void* mix;     // [3 * level + i]: (cos b, sin b), (t, 0), (f, 0) as complex<real>
-    double2* partials;   // [tile] (sum |psi|^2 C, sum |psi|^2)
+    double2* partials;   // [tile] (sum |psi|^2 C, sum |psi|^2); adjoint sweep: [2 tile + slot]
     uint16_t* cutout;    // [2^n] cut values (OP_CUTVAL)
 };
 
@@ -95,6 +96,8 @@ struct CoeffArgs {
     void* phase;
     void* mix;
 };
+
+constexpr int kSmallThreadsGrad = 512;
 
 // ---------------------------------------------------------------------------------- helpers
 
@@ -171,6 +174,19 @@ struct Tile {
     }
     template <int x>
     static __device__ __forceinline__ C2 from_reg(C2 z) { return to_reg<x>(z); }
+    // real / imaginary part of the amplitude in slot x, and a slot value from (re, im)
+    template <int x>
+    static __device__ __forceinline__ real re_of(C2 z) {
+        if constexpr (kSwapOdd && odd_parity(x)) return z.y;
+        else return z.x;
+    }
+    template <int x>
+    static __device__ __forceinline__ real im_of(C2 z) {
+        if constexpr (kSwapOdd && odd_parity(x)) return z.x;
+        else return z.y;
+    }
+    template <int x>
+    static __device__ __forceinline__ C2 mk(real re, real im) { return to_reg<x>(make_c2(re, im)); }
 
     static __host__ __device__ constexpr int rlo(int L) { return L == 0 ? Q - R : (L == 1 ? Q - 2 * R : 0); }
 
@@ -230,8 +246,18 @@ struct Tile {
 
     template <int L>
     static __device__ __forceinline__ void load(C2 (&v)[NE], const Ctx& c, uint32_t tid) {
+        load_from<L>(v, c, tid, c.a->state);
+    }
+
+    template <int L>
+    static __device__ __forceinline__ void store(const C2 (&v)[NE], const Ctx& c, uint32_t tid) {
+        store_to<L>(v, c, tid, c.a->state);
+    }
+
+    template <int L>
+    static __device__ __forceinline__ void load_from(C2 (&v)[NE], const Ctx& c, uint32_t tid, const void* base) {
         const TileArgs<Q>& a = *c.a;
-        const C2* g = reinterpret_cast<const C2*>(a.state) + c.zb + toff<L>(a, tid);
+        const C2* g = reinterpret_cast<const C2*>(base) + c.zb + toff<L>(a, tid);
         int64_t d[R];
 #pragma unroll
         for (int j = 0; j < R; ++j) d[j] = a.rstep[L][j];
@@ -243,9 +269,9 @@ struct Tile {
     }
 
     template <int L>
-    static __device__ __forceinline__ void store(const C2 (&v)[NE], const Ctx& c, uint32_t tid) {
+    static __device__ __forceinline__ void store_to(const C2 (&v)[NE], const Ctx& c, uint32_t tid, void* base) {
         const TileArgs<Q>& a = *c.a;
-        C2* g = reinterpret_cast<C2*>(a.state) + c.zb + toff<L>(a, tid);
+        C2* g = reinterpret_cast<C2*>(base) + c.zb + toff<L>(a, tid);
         int64_t d[R];
 #pragma unroll
         for (int j = 0; j < R; ++j) d[j] = a.rstep[L][j];
@@ -384,6 +410,102 @@ struct Tile {
                 }
             g[o] = (uint16_t)cidx;
         }
+    }
+
+    // ------------------------------------------------------------ adjoint sweep (psi v, lambda w)
+
+    // lambda <- C psi
+    template <int L>
+    static __device__ __forceinline__ void lambda_init(const C2 (&v)[NE], C2 (&w)[NE], const Ctx& c, uint32_t tid) {
+        const TileArgs<Q>& a = *c.a;
+        int s[R];
+        const int base = cut_setup<L>(c, tid, s);
+        for_x<NE>([&](auto X) {
+            constexpr int x = decltype(X)::value;
+            int cidx = base + a.crtab[L][x];
+#pragma unroll
+            for (int j = 0; j < R; ++j)
+                if ((x >> j) & 1) cidx += s[j];
+            const real cc = (real)cidx;
+            w[x] = make_c2(cc * v[x].x, cc * v[x].y);
+        });
+    }
+
+    // RX(2b)^dagger = [[c, is], [is, c]] on both states for the masked register bits; before each
+    // butterfly adds Im(conj(l_a) p_b + conj(l_b) p_a), the pair terms of Im <lambda| X_j |psi>.
+    static __device__ __forceinline__ real rx_dual(C2 (&v)[NE], C2 (&w)[NE], uint32_t mask, real cb, real sb) {
+        real acc = 0;
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            if (!((mask >> j) & 1u)) continue;
+            for_x<NE>([&](auto X) {
+                constexpr int x = decltype(X)::value;
+                if (!(x & (1 << j))) {
+                    const int y = x | (1 << j);
+                    const real ar = re_of<x>(v[x]), ai = im_of<x>(v[x]);
+                    // y differs from x in one bit: its slot form is the opposite one
+                    const real br = (kSwapOdd && !odd_parity(x)) ? v[y].y : v[y].x;
+                    const real bi = (kSwapOdd && !odd_parity(x)) ? v[y].x : v[y].y;
+                    const real lar = re_of<x>(w[x]), lai = im_of<x>(w[x]);
+                    const real lbr = (kSwapOdd && !odd_parity(x)) ? w[y].y : w[y].x;
+                    const real lbi = (kSwapOdd && !odd_parity(x)) ? w[y].x : w[y].y;
+                    acc += (lar * bi - lai * br) + (lbr * ai - lbi * ar);
+                    const real nar = cb * ar - sb * bi, nai = cb * ai + sb * br;
+                    const real nbr = cb * br - sb * ai, nbi = cb * bi + sb * ar;
+                    const real nlar = cb * lar - sb * lbi, nlai = cb * lai + sb * lbr;
+                    const real nlbr = cb * lbr - sb * lai, nlbi = cb * lbi + sb * lar;
+                    v[x] = mk<x>(nar, nai);
+                    w[x] = mk<x>(nlar, nlai);
+                    if (kSwapOdd && !odd_parity(x)) {
+                        v[y] = make_c2(nbi, nbr);
+                        w[y] = make_c2(nlbi, nlbr);
+                    } else {
+                        v[y] = make_c2(nbr, nbi);
+                        w[y] = make_c2(nlbr, nlbi);
+                    }
+                }
+            });
+        }
+        return acc;
+    }
+
+    // sum_z C(z) Im(conj(lambda_z) psi_z) over the thread's amplitudes
+    template <int L>
+    static __device__ __forceinline__ real grad_gamma(const C2 (&v)[NE], const C2 (&w)[NE], const Ctx& c, uint32_t tid) {
+        const TileArgs<Q>& a = *c.a;
+        int s[R];
+        const int base = cut_setup<L>(c, tid, s);
+        real acc = 0;
+        for_x<NE>([&](auto X) {
+            constexpr int x = decltype(X)::value;
+            int cidx = base + a.crtab[L][x];
+#pragma unroll
+            for (int j = 0; j < R; ++j)
+                if ((x >> j) & 1) cidx += s[j];
+            acc += (real)cidx * (re_of<x>(w[x]) * im_of<x>(v[x]) - im_of<x>(w[x]) * re_of<x>(v[x]));
+        });
+        return acc;
+    }
+
+    // exp(+i gamma C(z)) on both states (conjugate phase table entries)
+    template <int L>
+    static __device__ __forceinline__ void phase_dual(C2 (&v)[NE], C2 (&w)[NE], const Ctx& c, uint32_t tid, int level) {
+        const TileArgs<Q>& a = *c.a;
+        int s[R];
+        const int base = cut_setup<L>(c, tid, s);
+        const C2* __restrict__ T = reinterpret_cast<const C2*>(a.phase) + (size_t)level * a.E1;
+        for_x<NE>([&](auto X) {
+            constexpr int x = decltype(X)::value;
+            int cidx = base + a.crtab[L][x];
+#pragma unroll
+            for (int j = 0; j < R; ++j)
+                if ((x >> j) & 1) cidx += s[j];
+            const C2 f = __ldg(T + min((unsigned)cidx, (unsigned)(a.E1 - 1)));
+            const real pr = re_of<x>(v[x]), pi = im_of<x>(v[x]);
+            v[x] = mk<x>(pr * f.x + pi * f.y, pi * f.x - pr * f.y);
+            const real lr = re_of<x>(w[x]), li = im_of<x>(w[x]);
+            w[x] = mk<x>(lr * f.x + li * f.y, li * f.x - lr * f.y);
+        });
     }
 
     // RX(2b) = [[c, -is], [-is, c]] = c * [[1, -it], [-it, 1]] with t = tan b: one FMA per
@@ -548,6 +670,238 @@ __global__ void __launch_bounds__(1 << (Q - R), QAOA_TILE_MIN_BLOCKS) tile_kerne
                 sn += sred[1][w];
             }
             a.partials[t] = make_double2(sc, sn);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------- adjoint sweep
+
+// One pass of the adjoint sweep over psi (a.state) and lambda (a.state2), same tiling as
+// tile_kernel.  Per CTA it writes, for accumulator slots 0 and 1, (sum of RXD pair terms,
+// sum of GRADG terms) to partials[2 t + slot].
+template <typename real, int Q, int R>
+__global__ void __launch_bounds__(1 << (Q - R), 1) grad_kernel(const __grid_constant__ TileArgs<Q> a) {
+    using T = Tile<real, Q, R>;
+    using C2 = typename T::C2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int sE[Q];
+    __shared__ int sK;
+    __shared__ double sred[4][T::NT / 32];
+
+    unsigned char* tile = smem_raw;
+    const uint32_t tid = threadIdx.x;
+    const uint64_t t = blockIdx.x;
+    uint64_t zb = 0;
+    for (int r = 0; r < a.nruns; ++r) zb |= ((t >> a.run_src[r]) & ((1ull << a.run_len[r]) - 1ull)) << a.run_dst[r];
+    if (tid < 32) {
+        int acc = 0;
+        for (int v = (int)tid; v < a.n; v += 32) {
+            const uint64_t bI = 0ull - ((zb >> v) & 1ull);
+            acc += __popcll(a.gmask[v] & (bI ^ zb));
+        }
+        acc = warp_sum_int(acc);
+        if (tid == 0) sK = acc;
+        if (tid < (uint32_t)Q) sE[tid] = __popcll(a.outAdj[tid]) - 2 * __popcll(a.outAdj[tid] & zb);
+    }
+    __syncthreads();
+    typename T::Ctx c;
+    c.zb = zb;
+    c.K = sK;
+    c.a = &a;
+    c.sE = sE;
+
+    C2 v[T::NE], w[T::NE];
+    int L = 0;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};  // (pair terms, gamma terms) for slots 0 and 1
+    const bool lam_init = a.nops > 1 && a.ops[1].kind == OP_LAMBDA;
+
+#define QAOA_BY_LAYOUT(F, ...)                     \
+    do {                                           \
+        if (L == 0) T::template F<0>(__VA_ARGS__); \
+        else if (L == 1) T::template F<1>(__VA_ARGS__); \
+        else T::template F<2>(__VA_ARGS__);        \
+    } while (0)
+
+    for (int i = 0; i < a.nops; ++i) {
+        const Op op = a.ops[i];
+        switch (op.kind) {
+            case OP_LOAD:
+                L = op.layout;
+                QAOA_BY_LAYOUT(load_from, v, c, tid, a.state);
+                if (!lam_init) QAOA_BY_LAYOUT(load_from, w, c, tid, a.state2);
+                break;
+            case OP_LAMBDA:
+                QAOA_BY_LAYOUT(lambda_init, v, w, c, tid);
+                break;
+            case OP_XCHG: {
+                const int Lold = L;
+                __syncthreads();
+                QAOA_BY_LAYOUT(to_smem, v, tile, tid);
+                __syncthreads();
+                L = op.layout;
+                QAOA_BY_LAYOUT(from_smem, v, tile, tid);
+                __syncthreads();
+                L = Lold;
+                QAOA_BY_LAYOUT(to_smem, w, tile, tid);
+                __syncthreads();
+                L = op.layout;
+                QAOA_BY_LAYOUT(from_smem, w, tile, tid);
+                break;
+            }
+            case OP_RXD: {
+                const int level = op.arg & 0xffff, slot = op.arg >> 16;
+                const C2 cs = reinterpret_cast<const C2*>(a.mix)[3 * level];
+                acc[2 * slot] += (double)T::rx_dual(v, w, op.mask, cs.x, cs.y);
+                break;
+            }
+            case OP_GRADG: {
+                const int slot = op.arg >> 16;
+                real g = 0;
+                if (L == 0) g = T::template grad_gamma<0>(v, w, c, tid);
+                else if (L == 1) g = T::template grad_gamma<1>(v, w, c, tid);
+                else g = T::template grad_gamma<2>(v, w, c, tid);
+                acc[2 * slot + 1] += (double)g;
+                break;
+            }
+            case OP_PHASED:
+                QAOA_BY_LAYOUT(phase_dual, v, w, c, tid, op.arg);
+                break;
+            case OP_STORE:
+                L = op.layout;
+                QAOA_BY_LAYOUT(store_to, v, c, tid, a.state);
+                QAOA_BY_LAYOUT(store_to, w, c, tid, a.state2);
+                break;
+            default:
+                break;
+        }
+    }
+#undef QAOA_BY_LAYOUT
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const double r = warp_sum_double(acc[k]);
+        if ((tid & 31u) == 0) sred[k][tid >> 5] = r;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double r[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int wi = 0; wi < T::NT / 32; ++wi)
+            for (int k = 0; k < 4; ++k) r[k] += sred[k][wi];
+        a.partials[2 * t] = make_double2(r[0], r[1]);
+        a.partials[2 * t + 1] = make_double2(r[2], r[3]);
+    }
+}
+
+// Adds, in a fixed order, the per-tile adjoint partials of one pass to the per-level sums:
+// slot s of the pass belongs to level lev[s] (-1: unused); acc[level] gets the pair terms
+// (d/d beta) and acc[p + level] the gamma terms.
+__global__ void __launch_bounds__(1024) grad_reduce_kernel(const double2* __restrict__ partials, uint64_t tiles,
+                                                           int lev0, int lev1, int p, double* __restrict__ acc) {
+    __shared__ double sm[4][1024];
+    double r[4] = {0.0, 0.0, 0.0, 0.0};
+    for (uint64_t i = threadIdx.x; i < tiles; i += 1024) {
+        const double2 a = partials[2 * i], b = partials[2 * i + 1];
+        r[0] += a.x;
+        r[1] += a.y;
+        r[2] += b.x;
+        r[3] += b.y;
+    }
+    for (int k = 0; k < 4; ++k) sm[k][threadIdx.x] = r[k];
+    __syncthreads();
+    for (int s = 512; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s)
+            for (int k = 0; k < 4; ++k) sm[k][threadIdx.x] += sm[k][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (lev0 >= 0) {
+            acc[lev0] += sm[0][0];
+            acc[p + lev0] += sm[1][0];
+        }
+        if (lev1 >= 0) {
+            acc[lev1] += sm[2][0];
+            acc[p + lev1] += sm[3][0];
+        }
+    }
+}
+
+// Whole-state adjoint sweep for small n (psi and lambda both in shared memory, one CTA).
+struct SmallGradJob {
+    int32_t n, levels, E1;
+    uint64_t gmask[kMaxN];
+    const void* state;   // psi after the forward levels
+    const void* phase;   // plain tables [level][E1]
+    const void* mix;     // [3 * level]: (cos b, sin b)
+    double* acc;         // [2 * levels]: pair sums, gamma sums
+};
+
+template <typename real>
+__global__ void __launch_bounds__(kSmallThreadsGrad) small_grad_kernel(const __grid_constant__ SmallGradJob j) {
+    using C2 = typename C2T<real>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n = j.n;
+    const uint32_t dim = 1u << n;
+    C2* ps = reinterpret_cast<C2*>(smem_raw);
+    C2* lm = ps + dim;
+    __shared__ uint64_t gm[kMaxN];
+    __shared__ double sred[kSmallThreadsGrad / 32];
+    const uint32_t tid = threadIdx.x;
+    if (tid < (uint32_t)n) gm[tid] = j.gmask[tid];
+    __syncthreads();
+    const C2* src = reinterpret_cast<const C2*>(j.state);
+    for (uint32_t z = tid; z < dim; z += kSmallThreadsGrad) {
+        const C2 q = src[z];
+        const real cc = (real)cut_count_full(gm, n, z);
+        ps[z] = q;
+        lm[z] = make_c2(cc * q.x, cc * q.y);
+    }
+    auto block_sum = [&](double v) -> double {
+        v = warp_sum_double(v);
+        __syncthreads();
+        if ((tid & 31u) == 0) sred[tid >> 5] = v;
+        __syncthreads();
+        double r = 0.0;
+        for (int w = 0; w < kSmallThreadsGrad / 32; ++w) r += sred[w];
+        return r;
+    };
+    const C2* mix = reinterpret_cast<const C2*>(j.mix);
+    for (int k = j.levels - 1; k >= 0; --k) {
+        __syncthreads();
+        double pb = 0.0;
+        for (int q = 0; q < n; ++q)
+            for (uint32_t i = tid; i < dim / 2; i += kSmallThreadsGrad) {
+                const uint32_t lo = i & ((1u << q) - 1u);
+                const uint32_t za = ((i >> q) << (q + 1)) | lo, zb = za | (1u << q);
+                const C2 a = ps[za], b = ps[zb], la = lm[za], lb = lm[zb];
+                pb += (double)((la.x * b.y - la.y * b.x) + (lb.x * a.y - lb.y * a.x));
+            }
+        const double sb = block_sum(pb);
+        if (tid == 0) j.acc[k] = sb;
+        const C2 cs = mix[3 * k];
+        for (int q = 0; q < n; ++q) {
+            __syncthreads();
+            for (uint32_t i = tid; i < dim / 2; i += kSmallThreadsGrad) {
+                const uint32_t lo = i & ((1u << q) - 1u);
+                const uint32_t za = ((i >> q) << (q + 1)) | lo, zb = za | (1u << q);
+                rx_pair(ps[za], ps[zb], cs.x, -cs.y);
+                rx_pair(lm[za], lm[zb], cs.x, -cs.y);
+            }
+        }
+        __syncthreads();
+        double pg = 0.0;
+        for (uint32_t z = tid; z < dim; z += kSmallThreadsGrad) {
+            const C2 p = ps[z], l = lm[z];
+            pg += (double)cut_count_full(gm, n, z) * (double)(l.x * p.y - l.y * p.x);
+        }
+        const double sg = block_sum(pg);
+        if (tid == 0) j.acc[j.levels + k] = sg;
+        if (k > 0) {
+            const C2* Tk = reinterpret_cast<const C2*>(j.phase) + (size_t)k * j.E1;
+            for (uint32_t z = tid; z < dim; z += kSmallThreadsGrad) {
+                const C2 f = Tk[cut_count_full(gm, n, z)];
+                const C2 fc = make_c2(f.x, -f.y);
+                ps[z] = cmul(ps[z], fc);
+                lm[z] = cmul(lm[z], fc);
+            }
         }
     }
 }

@@ -56,13 +56,11 @@ uint32_t group_target_mask(const Group& g, const TileConfig& tc) {
     return all & ~((1u << geo.cprime) - 1u);
 }
 
-Plan plan_levels(int n, const TileConfig& tc, int levels, bool synth_first, bool expect_last) {
-    Plan plan;
-    plan.n = n;
-    plan.tc = tc;
-    plan.groups = make_groups(n, tc);
-    const int g = (int)plan.groups.size();
-    std::vector<int> order;  // group order of even levels; odd levels run it backwards
+namespace {
+
+// Group order of even levels; odd levels run it backwards.
+std::vector<int> group_order(int g) {
+    std::vector<int> order;
     if (g >= 3) {
         order.push_back(1);
         order.push_back(0);
@@ -70,6 +68,20 @@ Plan plan_levels(int n, const TileConfig& tc, int levels, bool synth_first, bool
     } else {
         for (int i = 0; i < g; ++i) order.push_back(i);
     }
+    return order;
+}
+
+bool is_rx_like(uint8_t kind) { return kind == OP_RX || kind == OP_RXD; }
+
+}  // namespace
+
+Plan plan_levels(int n, const TileConfig& tc, int levels, bool synth_first, bool expect_last) {
+    Plan plan;
+    plan.n = n;
+    plan.tc = tc;
+    plan.groups = make_groups(n, tc);
+    const int g = (int)plan.groups.size();
+    const std::vector<int> order = group_order(g);
     for (int k = 0; k < levels; ++k) {
         for (int idx = 0; idx < g; ++idx) {
             const int grp = (k % 2 == 0) ? order[idx] : order[g - 1 - idx];
@@ -90,6 +102,39 @@ Plan plan_levels(int n, const TileConfig& tc, int levels, bool synth_first, bool
         }
     }
     if (expect_last && !plan.passes.empty()) plan.passes.back().lops.push_back(LOp{OP_EXPECT, 0});
+    assign_layouts(plan);
+    return plan;
+}
+
+Plan plan_backward(int n, const TileConfig& tc, int levels) {
+    Plan plan;
+    plan.n = n;
+    plan.tc = tc;
+    plan.groups = make_groups(n, tc);
+    const int g = (int)plan.groups.size();
+    const std::vector<int> order = group_order(g);
+    int slot = 0;  // accumulator slot of the current pass for level k
+    for (int s = 0; s < levels; ++s) {
+        const int k = levels - 1 - s;
+        for (int idx = 0; idx < g; ++idx) {
+            const int grp = (s % 2 == 0) ? order[idx] : order[g - 1 - idx];
+            if (idx == 0 && s > 0) {
+                slot = 1;  // second level of the fused pass
+            } else {
+                Pass ps;
+                ps.group = grp;
+                ps.synth = false;
+                ps.store = true;
+                if (s == 0 && idx == 0) ps.lops.push_back(LOp{OP_LAMBDA, 0});
+                plan.passes.push_back(ps);
+                slot = 0;
+            }
+            plan.passes.back().lops.push_back(LOp{OP_RXD, k | (slot << 16)});
+        }
+        plan.passes.back().lops.push_back(LOp{OP_GRADG, k | (slot << 16)});
+        if (k > 0) plan.passes.back().lops.push_back(LOp{OP_PHASED, k});
+    }
+    if (!plan.passes.empty()) plan.passes.back().store = false;
     assign_layouts(plan);
     return plan;
 }
@@ -158,7 +203,7 @@ void assign_layouts(Plan& plan) {
             std::array<Choice, 3> nx;
             for (int cur = 0; cur < 3; ++cur) {
                 if (st[cur].cost == INT_MAX) continue;
-                if (lo.kind != OP_RX) {
+                if (!is_rx_like(lo.kind)) {
                     Choice c = st[cur];
                     c.ops.push_back(Op{lo.kind, (uint8_t)cur, 0, lo.arg});
                     if (c.cost < nx[cur].cost) nx[cur] = c;
@@ -176,7 +221,7 @@ void assign_layouts(Plan& plan) {
                         }
                         const uint32_t add = tc.regMask(L) & target & ~covered;
                         covered |= add;
-                        c.ops.push_back(Op{OP_RX, (uint8_t)L, (uint16_t)(add >> tc.regLo(L)), lo.arg});
+                        c.ops.push_back(Op{lo.kind, (uint8_t)L, (uint16_t)(add >> tc.regLo(L)), lo.arg});
                     }
                     if (c.cost < nx[L].cost) nx[L] = c;
                 }

@@ -45,6 +45,12 @@ enum OpKind : uint8_t {
     OP_EXPECT = 6,
     OP_STORE = 7,
     OP_CUTVAL = 8,
+    // adjoint sweep (two states: psi and lambda)
+    OP_LAMBDA = 9,   // lambda <- C psi
+    OP_RXD = 10,     // RX(2 beta)^dagger on both on the masked register bits, accumulating the
+                     // pair terms of Im <lambda| X_j |psi> (arg = level | slot << 16)
+    OP_GRADG = 11,   // accumulate sum_z C(z) Im(conj(lambda_z) psi_z) (arg = level | slot << 16)
+    OP_PHASED = 12,  // exp(+i gamma_k C) on both (arg = level)
 };
 
 struct Op {
@@ -114,6 +120,12 @@ uint32_t group_target_mask(const Group& g, const TileConfig& tc);
 // Passes for `levels` levels starting from a materialised state (or a deferred |+>^n when
 // `synth_first`), with the expectation fused into the last pass when `expect_last`.
 Plan plan_levels(int n, const TileConfig& tc, int levels, bool synth_first, bool expect_last);
+
+// Adjoint sweep over `levels` levels (level levels-1 first) of the two states psi (state
+// buffer, holding the forward result) and lambda (work buffer).  Each pass carries at most two
+// levels; the level of each RXD / GRADG op and its accumulator slot are encoded in the op arg.
+// The last pass stores nothing.
+Plan plan_backward(int n, const TileConfig& tc, int levels);
 
 // Single pass over group 0 that only evaluates (no store): expectation or cut values.
 Plan plan_readonly(int n, const TileConfig& tc, bool synth, uint8_t kind, int group = 0,

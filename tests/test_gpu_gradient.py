@@ -1,0 +1,140 @@
+"""GPU adjoint gradient d<C>/d(gamma_k, beta_k) (qaoa_gradient) against the FP64 CPU oracle adjoint
+and against central finite differences (h = 1e-4) evaluated in complex128 on the GPU."""
+import numpy as np
+import pytest
+
+from paper_2312_03019_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2312_03019_b300 import build
+    build.build()
+    from paper_2312_03019_b300 import binding
+    return binding
+
+
+def gpu_gradient(B, g, gamma, beta, prec):
+    import torch
+    s = B.QAOAState(g, prec)
+    work = torch.empty(s.nbytes, dtype=torch.uint8, device="cuda")
+    c, dg, db = B.qaoa_gradient(s.handle, gamma, beta, work.data_ptr(), s.nbytes)
+    s.close()
+    return c, dg, db
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("n,p,mk", [
+    (2, 2, lambda: I._canonical(2, [(0, 1)], "edge")), (6, 3, lambda: I.complete(6)),
+    (10, 4, lambda: I.regular3(10, 0)), (12, 2, lambda: I.gnp(12, 0.5, 1)),
+    (13, 3, lambda: I.regular3(13, 2)), (14, 5, lambda: I.gnp(14, 0.5, 0)),
+    (16, 3, lambda: I.regular3(16, 4)), (18, 2, lambda: I.gnp(18, 0.3, 5)),
+])
+def test_gradient_matches_oracle_adjoint(B, prec, n, p, mk):
+    import oracle
+    g = mk()
+    gamma, beta = I.angles(p, seed=n + 7)
+    ref_c, ref_dg, ref_db = oracle.adjoint_gradient(g, gamma, beta)
+    c, dg, db = gpu_gradient(B, g, gamma, beta, prec)
+    scale = max(1.0, np.max(np.abs(np.concatenate([ref_dg, ref_db]))))
+    if prec == "c128":
+        assert abs(c - ref_c) <= 1e-12 * max(1.0, abs(ref_c))
+        assert np.max(np.abs(dg - ref_dg)) <= 1e-10 * scale
+        assert np.max(np.abs(db - ref_db)) <= 1e-10 * scale
+    else:
+        assert abs(c - ref_c) <= 1e-5 * g.m
+        assert np.max(np.abs(dg - ref_dg)) <= 1e-4 * g.m
+        assert np.max(np.abs(db - ref_db)) <= 1e-4 * g.m
+
+
+def test_gradient_workload_g24_p10_against_finite_differences(B):
+    """G(24, 0.5), p = 10, complex64 adjoint gradient vs central differences (h = 1e-4) of <C>
+    evaluated in complex128 on the GPU (40 evaluations)."""
+    g, gamma, beta = I.workload_gnp24_p10()
+    c, dg, db = gpu_gradient(B, g, gamma, beta, "c64")
+    s = B.QAOAState(g, "c128")
+    h = 1e-4
+
+    def f(ga, be):
+        s.reset()
+        s.apply_layers(ga, be)
+        return s.expectation()[0]
+
+    c128 = f(gamma, beta)
+    assert abs(c - c128) <= 1e-5 * g.m
+    fd_g = np.zeros(10)
+    fd_b = np.zeros(10)
+    for k in range(10):
+        e = np.zeros(10)
+        e[k] = h
+        fd_g[k] = (f(gamma + e, beta) - f(gamma - e, beta)) / (2 * h)
+        fd_b[k] = (f(gamma, beta + e) - f(gamma, beta - e)) / (2 * h)
+    s.close()
+    scale = np.max(np.abs(np.concatenate([fd_g, fd_b])))
+    assert np.max(np.abs(dg - fd_g)) <= 1e-3 * scale + 1e-3
+    assert np.max(np.abs(db - fd_b)) <= 1e-3 * scale + 1e-3
+
+
+def test_gradient_fp64_cpu_adjoint_n14_p10(B):
+    """The FP64 CPU adjoint on G(14, 0.5), p = 10 against both GPU precisions."""
+    import oracle
+    g = I.gnp(14, 0.5, 0)
+    gamma, beta = I.angles(10, 0)
+    ref_c, ref_dg, ref_db = oracle.adjoint_gradient(g, gamma, beta)
+    scale = max(1.0, np.max(np.abs(np.concatenate([ref_dg, ref_db]))))
+    c, dg, db = gpu_gradient(B, g, gamma, beta, "c128")
+    assert np.max(np.abs(np.concatenate([dg - ref_dg, db - ref_db]))) <= 1e-10 * scale
+    c, dg, db = gpu_gradient(B, g, gamma, beta, "c64")
+    assert np.max(np.abs(np.concatenate([dg - ref_dg, db - ref_db]))) <= 1e-4 * g.m
+
+
+def test_gradient_then_state_is_plus_and_reusable(B):
+    import torch
+    g = I.regular3(18, 1)
+    gamma, beta = I.angles(3, 1)
+    s = B.QAOAState(g, "c64")
+    work = torch.empty(s.nbytes, dtype=torch.uint8, device="cuda")
+    c1, dg1, db1 = B.qaoa_gradient(s.handle, gamma, beta, work.data_ptr(), s.nbytes)
+    c0, _ = s.expectation()  # |+>^n again
+    assert abs(c0 - g.m / 2) < 1e-4 * g.m
+    c2, dg2, db2 = B.qaoa_gradient(s.handle, gamma, beta, work.data_ptr(), s.nbytes)
+    assert c1 == c2 and np.array_equal(dg1, dg2) and np.array_equal(db1, db2)  # run to run identical
+    s.apply_layers(gamma, beta)
+    c3, _ = s.expectation()
+    assert abs(c3 - c1) < 1e-5 * g.m
+    s.close()
+
+
+def test_gradient_rejects_bad_work_buffer(B):
+    import torch
+    g = I.ring(16)
+    s = B.QAOAState(g, "c64")
+    small = torch.empty(64, dtype=torch.uint8, device="cuda")
+    with pytest.raises(B.QAOAError):
+        B.qaoa_gradient(s.handle, [0.1], [0.2], small.data_ptr(), 64)
+    with pytest.raises(B.QAOAError):
+        B.qaoa_gradient(s.handle, [0.1], [0.2], s.buffer.data_ptr(), s.nbytes)
+    with pytest.raises(B.QAOAError):
+        B.qaoa_gradient(s.handle, [], [], s.buffer.data_ptr(), s.nbytes)
+    s.close()
+
+
+def test_autograd_function(B):
+    import torch
+    from paper_2312_03019_b300.autograd import qaoa_expectation_fn
+    g = I.regular3(16, 3)
+    gamma = torch.tensor(I.angles(4, 3)[0], requires_grad=True)
+    beta = torch.tensor(I.angles(4, 3)[1], requires_grad=True)
+    s = B.QAOAState(g, "c128")
+    val = qaoa_expectation_fn(gamma, beta, s)
+    (2.0 * val).backward()
+    c, dg, db = gpu_gradient(B, g, gamma.detach().numpy(), beta.detach().numpy(), "c128")
+    assert abs(val.item() - c) < 1e-12 * abs(c)
+    assert np.allclose(gamma.grad.numpy(), 2.0 * dg, rtol=0, atol=1e-12)
+    assert np.allclose(beta.grad.numpy(), 2.0 * db, rtol=0, atol=1e-12)
+    s.close()
