@@ -8,6 +8,7 @@ vertex, since a 3-regular graph on an odd vertex count does not exist), seed 0, 
 levels, complex64 state of 2^33 amplitudes (64 GiB), larger than L2, so no L2 flush is needed.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--n 33] [--p 8]
+  python bench.py --serve      # request-serving mode (qaoa_submit / qaoa_poll), its own JSON line
 
 Prints ONE JSON line on rank 0.  `--impl reference` times the CPU oracle (gate-level complex128
 simulator, the paper's Algorithm 1) on a bounded sample of the same workload on the host cores.
@@ -48,6 +49,11 @@ def parse_args():
     ap.add_argument("--cpu-sample-n", type=int, default=24)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--serve", action="store_true",
+                    help="serving mode: an open-loop Poisson request stream through qaoa_submit/qaoa_poll")
+    ap.add_argument("--serve-requests", type=int, default=4096)
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--serve-budget-gib", type=float, default=64.0)
     return ap.parse_args()
 
 
@@ -328,8 +334,90 @@ def run_ours(args):
     return 0
 
 
+def serve_stream(B, reqs, cfg):
+    """Submit every request at its arrival time (open loop), then collect all results.
+    Latency and makespan come from the server's own clock (t_submit, t_done)."""
+    sv = B.qaoa_server_create(**cfg)
+    try:
+        # warm-up: one request of each kind and size, so graph capture and first-use costs stay out
+        seen = {}
+        for r in reqs:
+            seen.setdefault((r.graph.n, r.want_grad), r)
+        warm = [B.qaoa_submit(sv, r.graph, r.gamma, r.beta, r.want_grad) for r in seen.values()]
+        while warm:
+            warm = [t for t in warm if B.qaoa_poll(sv, t) is None]
+            time.sleep(0.001)
+        base = B.qaoa_server_stats_read(sv)
+        t0 = B.qaoa_server_time(sv)
+        tickets = []
+        for r in reqs:
+            while B.qaoa_server_time(sv) - t0 < r.arrival_s:
+                pass
+            while True:
+                try:
+                    tickets.append(B.qaoa_submit(sv, r.graph, r.gamma, r.beta, r.want_grad))
+                    break
+                except B.QAOAError as e:
+                    if e.status != B.QAOA_ERR_AGAIN:
+                        raise
+                    time.sleep(0.0002)
+        res = {}
+        while len(res) < len(tickets):
+            for t in tickets:
+                if t not in res:
+                    out = B.qaoa_poll(sv, t)
+                    if out is not None:
+                        res[t] = out
+            time.sleep(0.002)
+        stats = B.qaoa_server_stats_read(sv)
+    finally:
+        B.qaoa_server_destroy(sv)
+    done = [res[t] for t in tickets]
+    bad = [d for d in done if d["status"] != 0]
+    if bad:
+        raise RuntimeError(f"{len(bad)} requests failed")
+    lat = sorted(d["t_done"] - d["t_submit"] for d in done)
+    span = max(d["t_done"] for d in done) - min(d["t_submit"] for d in done)
+    q = lambda f: lat[min(len(lat) - 1, int(f * len(lat)))] * 1e3
+    stats = {k: stats[k] - base.get(k, 0) if k != "arena_peak_bytes" else stats[k] for k in stats}
+    return {"requests_per_s": len(done) / span, "p50_ms": q(0.50), "p99_ms": q(0.99), "makespan_s": span,
+            "stats": stats}, done
+
+
+def run_serve(args):
+    import torch
+
+    if not torch.cuda.is_available():
+        raise SystemExit("the serving benchmark needs a CUDA device")
+    from paper_2312_03019_b300 import binding as B
+
+    stream = I.request_stream(count=args.serve_requests, rate_hz=args.serve_rate, seed=0)
+    reqs = stream.requests
+    budget = int(args.serve_budget_gib * (1 << 30))
+    served, done = serve_stream(B, reqs, dict(hbm_budget_bytes=budget, prec=args.prec, max_inflight=64,
+                                              queue_capacity=8192, max_batch=64, streams=8, use_graphs=True))
+    serial, done_serial = serve_stream(B, reqs, dict(hbm_budget_bytes=budget, prec=args.prec, max_inflight=1,
+                                                     queue_capacity=8192, max_batch=1, streams=1, use_graphs=False))
+    # the two configurations must agree request by request (same kernels, same reduction order)
+    for a, b in zip(done, done_serial):
+        if a["expectation"] != b["expectation"]:
+            raise RuntimeError("served and serial results differ")
+    rec = {"metric": "QAOA serving throughput", "value": served["requests_per_s"], "unit": "requests/s",
+           "higher_is_better": True, "n_gpus": 1, "dtype": "f32" if args.prec == "c64" else "f64",
+           "data": "synthetic", "mode": "serve",
+           "config": {"workload": f"{len(reqs)} requests, Poisson {args.serve_rate:g}/s, n 14-28 "
+                                  "(half 3-regular, half G(n,0.3)), p 1-6, 25% with gradient",
+                      "prec": args.prec, "hbm_budget_gib": args.serve_budget_gib},
+           "served": served, "serial": serial,
+           "speedup_vs_serial": served["requests_per_s"] / serial["requests_per_s"]}
+    print(json.dumps(rec), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
+    if args.serve:
+        return run_serve(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

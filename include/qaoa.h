@@ -191,6 +191,78 @@ qaoa_status qaoa_expectation_static(const qaoa_graph *g, qaoa_prec prec, const v
                                     size_t state_bytes, void *cuda_stream, double *out_c,
                                     double *out_norm);
 
+/* ------------------------------------------------------------------------- serving
+ * A request loop for QAOA evaluations as a classical optimiser emits them (the paper's Fig. 1
+ * workflow; the paper itself describes no server).  A scheduler thread owns the GPU work:
+ *   - admission in arrival order, by HBM footprint: each request needs its state (2^n amplitudes)
+ *     plus, for gradients, the adjoint buffer and small tables, carved from one device arena of
+ *     hbm_budget_bytes allocated at qaoa_server_create; at most max_inflight requests at once;
+ *   - continuous batching: every scheduler turn packs all admitted small forward requests (whole
+ *     state in one CTA: n <= 14 for complex64, n <= 13 for complex128) into one batched launch,
+ *     one CTA per request, while larger requests run concurrently on a pool of `streams` CUDA
+ *     streams; with use_graphs each launch sequence is recorded into a CUDA graph and replayed
+ *     through an executable graph cached per request shape;
+ *   - completion is detected with CUDA events; results land in pinned host memory.
+ * Each result is computed by the same kernels and reduction order as a lone request, so it is
+ * identical alone and in the mix. */
+#define QAOA_SERVE_MAX_P 64
+
+typedef struct {
+    size_t hbm_budget_bytes;  /* device arena size for states and per-request workspace */
+    int32_t max_inflight;     /* requests on the GPU at once (>= 1) */
+    int32_t queue_capacity;   /* queued requests before qaoa_submit returns QAOA_ERR_AGAIN */
+    int32_t max_batch;        /* small requests packed per launch (1..256) */
+    int32_t streams;          /* CUDA streams for concurrent requests (1..64) */
+    int32_t use_graphs;       /* 1: replay captured CUDA graphs; 0: plain launches */
+    qaoa_prec prec;           /* precision of every state of this server */
+} qaoa_server_config;
+
+typedef struct {
+    qaoa_graph graph;     /* copied at submit */
+    int32_t p;            /* 1 <= p <= QAOA_SERVE_MAX_P */
+    const double *gamma;  /* p angles, copied at submit */
+    const double *beta;   /* p angles, copied at submit */
+    int32_t want_grad;    /* 1: also d<C>/d gamma, d<C>/d beta (adjoint sweep) */
+} qaoa_request;
+
+typedef struct {
+    int32_t status;       /* QAOA_OK or the error the request failed with */
+    int32_t p;
+    int32_t has_grad;
+    int32_t batched;      /* 1: ran in a packed small-request launch */
+    double expectation;   /* <C> */
+    double norm;          /* sum |psi|^2 */
+    double t_submit;      /* server clock (qaoa_server_time) at submit */
+    double t_start;       /* ... when dispatched to the GPU */
+    double t_done;        /* ... when the scheduler saw it complete */
+    double d_gamma[QAOA_SERVE_MAX_P];
+    double d_beta[QAOA_SERVE_MAX_P];
+} qaoa_result;
+
+typedef struct {
+    int64_t submitted, completed, failed, rejected_full;
+    int64_t batches, batched_requests, single_requests, graph_launches;
+    size_t arena_peak_bytes;
+} qaoa_server_stats;
+
+typedef struct qaoa_server_s *qaoa_server;
+
+/* Creates the server and starts its scheduler thread on the current device.  Allocates the arena,
+ * pinned result buffers, streams and events (QAOA_ERR_OOM if the arena does not fit). */
+qaoa_status qaoa_server_create(const qaoa_server_config *cfg, qaoa_server *out);
+/* Queues a request (graph and angles are copied); *ticket identifies it.  QAOA_ERR_AGAIN when the
+ * queue is full; QAOA_ERR_INVALID for a bad request; QAOA_ERR_OOM when its footprint exceeds the
+ * whole arena.  Thread-safe. */
+qaoa_status qaoa_submit(qaoa_server sv, const qaoa_request *r, uint64_t *ticket);
+/* Non-blocking: QAOA_PENDING while the request is queued or running; QAOA_OK with *out filled
+ * (the ticket is then released); QAOA_ERR_INVALID for an unknown ticket.  Thread-safe. */
+qaoa_status qaoa_poll(qaoa_server sv, uint64_t ticket, qaoa_result *out);
+/* Seconds on the server's monotonic clock (the time base of qaoa_result). */
+double qaoa_server_time(qaoa_server sv);
+qaoa_status qaoa_server_stats_read(qaoa_server sv, qaoa_server_stats *out);
+/* Stops the scheduler after the requests already admitted finish, frees everything. */
+qaoa_status qaoa_server_destroy(qaoa_server sv);
+
 /* Message of the last error on the calling thread ("" if none). */
 const char *qaoa_last_error(void);
 

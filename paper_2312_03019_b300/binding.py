@@ -87,6 +87,38 @@ _sig("qaoa_plan_describe", ctypes.c_int, [_i32, ctypes.c_int, _i32, ctypes.POINT
 _sig("qaoa_profile_enable", ctypes.c_int, [_vp, _i32])
 _sig("qaoa_profile_read", ctypes.c_int, [_vp, ctypes.POINTER(ProfileStats)])
 _sig("qaoa_expectation_static", ctypes.c_int, [ctypes.POINTER(_Graph), ctypes.c_int, _vp, ctypes.c_size_t, _vp, _dp, _dp])
+SERVE_MAX_P = 64
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_inflight", _i32), ("queue_capacity", _i32),
+                ("max_batch", _i32), ("streams", _i32), ("use_graphs", _i32), ("prec", ctypes.c_int)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("graph", _Graph), ("p", _i32), ("gamma", _dp), ("beta", _dp), ("want_grad", _i32)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", _i32), ("p", _i32), ("has_grad", _i32), ("batched", _i32),
+                ("expectation", ctypes.c_double), ("norm", ctypes.c_double), ("t_submit", ctypes.c_double),
+                ("t_start", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("d_gamma", ctypes.c_double * SERVE_MAX_P), ("d_beta", ctypes.c_double * SERVE_MAX_P)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("rejected_full", ctypes.c_int64), ("batches", ctypes.c_int64), ("batched_requests", ctypes.c_int64),
+                ("single_requests", ctypes.c_int64), ("graph_launches", ctypes.c_int64),
+                ("arena_peak_bytes", ctypes.c_size_t)]
+
+
+_sig("qaoa_server_create", ctypes.c_int, [ctypes.POINTER(ServerConfig), ctypes.POINTER(_vp)])
+_sig("qaoa_submit", ctypes.c_int, [_vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)])
+_sig("qaoa_poll", ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.POINTER(Result)])
+_sig("qaoa_server_time", ctypes.c_double, [_vp])
+_sig("qaoa_server_stats_read", ctypes.c_int, [_vp, ctypes.POINTER(ServerStats)])
+_sig("qaoa_server_destroy", ctypes.c_int, [_vp])
 _sig("qaoa_last_error", ctypes.c_char_p, [])
 
 
@@ -276,3 +308,49 @@ class QAOAState:
 
 def uniform_amplitude(n: int) -> float:
     return math.pow(2.0, -0.5 * n)
+
+
+def qaoa_server_create(hbm_budget_bytes: int, prec="c64", max_inflight: int = 64, queue_capacity: int = 8192,
+                       max_batch: int = 64, streams: int = 8, use_graphs: bool = True) -> int:
+    cfg = ServerConfig(int(hbm_budget_bytes), int(max_inflight), int(queue_capacity), int(max_batch), int(streams),
+                       1 if use_graphs else 0, _prec(prec))
+    h = _vp()
+    _check(_lib.qaoa_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h.value
+
+
+def qaoa_submit(sv: int, g, gamma, beta, want_grad: bool = False) -> int:
+    """Returns the ticket; raises QAOAError (status QAOA_ERR_AGAIN when the queue is full)."""
+    gs, keep = _graph(g)
+    ga = np.ascontiguousarray(np.asarray(gamma, dtype=np.float64).reshape(-1))
+    be = np.ascontiguousarray(np.asarray(beta, dtype=np.float64).reshape(-1))
+    req = Request(gs, int(ga.size), ga.ctypes.data_as(_dp), be.ctypes.data_as(_dp), 1 if want_grad else 0)
+    t = ctypes.c_uint64()
+    _check(_lib.qaoa_submit(_vp(sv), ctypes.byref(req), ctypes.byref(t)))
+    return t.value
+
+
+def qaoa_poll(sv: int, ticket: int):
+    """None while pending, else a dict with the result (the ticket is released)."""
+    r = Result()
+    st = _check(_lib.qaoa_poll(_vp(sv), ctypes.c_uint64(ticket), ctypes.byref(r)))
+    if st == QAOA_PENDING:
+        return None
+    out = {k: getattr(r, k) for k, _ in Result._fields_ if k not in ("d_gamma", "d_beta")}
+    out["d_gamma"] = np.array(r.d_gamma[: r.p]) if r.has_grad else None
+    out["d_beta"] = np.array(r.d_beta[: r.p]) if r.has_grad else None
+    return out
+
+
+def qaoa_server_time(sv: int) -> float:
+    return float(_lib.qaoa_server_time(_vp(sv)))
+
+
+def qaoa_server_stats_read(sv: int) -> dict:
+    st = ServerStats()
+    _check(_lib.qaoa_server_stats_read(_vp(sv), ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+
+def qaoa_server_destroy(sv: int) -> None:
+    _check(_lib.qaoa_server_destroy(_vp(sv)))

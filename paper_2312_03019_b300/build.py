@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libqaoa_b300.so")
 SOURCES = ["capi.cu", "plan.cpp"]
-HEADERS = ["kernels.cuh", "plan.h", os.path.join("..", "..", "include", "qaoa.h")]
+HEADERS = ["kernels.cuh", "plan.h", "server.cuh", os.path.join("..", "..", "include", "qaoa.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -216,17 +216,39 @@ EventPair* next_event(qaoa_state s, int kind) {
     return e;
 }
 
+// Dynamic shared-memory limits of the kernels, set once per process (first use, or by
+// prepare_kernels before any stream capture).
+template <typename real>
+qaoa_status ensure_attributes() {
+    static bool done = false;
+    if (done) return QAOA_OK;
+    constexpr int Q = PrecTraits<real>::Q, R = PrecTraits<real>::R;
+    using C2 = typename C2T<real>::type;
+    CUDA_TRY(cudaFuncSetAttribute(tile_kernel<real, Q, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)((1u << Q) * sizeof(C2))));
+    CUDA_TRY(cudaFuncSetAttribute(grad_kernel<real, Q, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)((1u << Q) * sizeof(C2))));
+    CUDA_TRY(cudaFuncSetAttribute(small_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024));
+    CUDA_TRY(cudaFuncSetAttribute(small_batch_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024));
+    CUDA_TRY(cudaFuncSetAttribute(small_grad_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(2 * (1u << Q) * sizeof(C2))));
+    done = true;
+    return QAOA_OK;
+}
+
+template <typename real>
+qaoa_status prepare_kernels() {
+    return ensure_attributes<real>();
+}
+
 template <typename real>
 qaoa_status launch_tile(qaoa_state s, TileArgs<PrecTraits<real>::Q>& a, int kind) {
     constexpr int Q = PrecTraits<real>::Q, R = PrecTraits<real>::R;
     using C2 = typename C2T<real>::type;
     auto kfn = tile_kernel<real, Q, R>;
     const size_t smem = (size_t)(1u << Q) * sizeof(C2);
-    static bool attr_set = false;
-    if (!attr_set) {
-        CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_set = true;
-    }
+    qaoa_status ast = ensure_attributes<real>();
+    if (ast != QAOA_OK) return ast;
     EventPair* ev = kind ? next_event(s, kind) : nullptr;
     if (ev) CUDA_TRY(cudaEventRecord(ev->a, s->stream));
     kfn<<<(unsigned)s->ntiles, 1u << (Q - R), smem, s->stream>>>(a);
@@ -241,11 +263,8 @@ qaoa_status launch_small(qaoa_state s, const SmallJob& j) {
     using C2 = typename C2T<real>::type;
     auto kfn = small_kernel<real>;
     const size_t smem = (size_t)s->dim * sizeof(C2);
-    static bool attr_set = false;
-    if (!attr_set) {
-        CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024));
-        attr_set = true;
-    }
+    qaoa_status ast = ensure_attributes<real>();
+    if (ast != QAOA_OK) return ast;
     kfn<<<1, kSmallThreads, smem, s->stream>>>(j);
     CUDA_TRY(cudaGetLastError());
     s->launches++;
@@ -398,13 +417,21 @@ qaoa_status compute_partials(qaoa_state s) {
     return QAOA_OK;
 }
 
+// Enqueues the <C> / norm reduction of the current state into s->d_result (no host sync).
 template <typename real>
-qaoa_status expectation_impl(qaoa_state s, double* out_c, double* out_norm) {
+qaoa_status expectation_async(qaoa_state s) {
     qaoa_status st = compute_partials<real>(s);
     if (st != QAOA_OK) return st;
     finalize_kernel<<<1, 1024, 0, s->stream>>>(s->d_partials, s->partial_count, s->d_result);
     CUDA_TRY(cudaGetLastError());
     s->launches++;
+    return QAOA_OK;
+}
+
+template <typename real>
+qaoa_status expectation_impl(qaoa_state s, double* out_c, double* out_norm) {
+    qaoa_status st = expectation_async<real>(s);
+    if (st != QAOA_OK) return st;
     CUDA_TRY(cudaMemcpyAsync(s->h_result, s->d_result, sizeof(double2), cudaMemcpyDeviceToHost, s->stream));
     CUDA_TRY(cudaStreamSynchronize(s->stream));
     if (out_c) *out_c = s->h_result->x;
@@ -628,10 +655,9 @@ qaoa_status grad_workspace(qaoa_state s, int p) {
     return QAOA_OK;
 }
 
+// p forward levels from |+>^n followed by the <C> reduction into s->d_result (no host sync).
 template <typename real>
-qaoa_status gradient_impl(qaoa_state s, int p, const double* gamma, const double* beta, void* work,
-                          double* out_c, double* d_gamma, double* d_beta) {
-    // forward levels from |+>^n, <C> from the fused reduction
+qaoa_status forward_async(qaoa_state s, int p, const double* gamma, const double* beta) {
     s->lazy = true;
     s->exp_valid = false;
     s->compl_ = false;
@@ -641,9 +667,15 @@ qaoa_status gradient_impl(qaoa_state s, int p, const double* gamma, const double
         st = apply_chunk<real>(s, levels, gamma + k0, beta + k0, k0 + levels == p);
     }
     if (st != QAOA_OK) return st;
-    st = expectation_impl<real>(s, out_c, nullptr);
-    if (st != QAOA_OK) return st;
-    st = grad_workspace(s, p);
+    return expectation_async<real>(s);
+}
+
+// Forward run, <C> into s->d_result and the adjoint sweep's per-level sums into s->d_gacc
+// ([0, p): pair terms of d/d beta, [p, 2p): gamma terms; both without the factor 2), all
+// enqueued on the state's stream without host synchronisation.  Needs grad_workspace(s, p).
+template <typename real>
+qaoa_status gradient_async(qaoa_state s, int p, const double* gamma, const double* beta, void* work) {
+    qaoa_status st = forward_async<real>(s, p, gamma, beta);
     if (st != QAOA_OK) return st;
     using C2 = typename C2T<real>::type;
     // plain per-level tables (no folded factors) for the sweep
@@ -682,11 +714,8 @@ qaoa_status gradient_impl(qaoa_state s, int p, const double* gamma, const double
         j.mix = s->d_gmix;
         j.acc = s->d_gacc;
         auto kfn = small_grad_kernel<real>;
-        static bool attr = false;
-        if (!attr) {
-            CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * (1 << Q) * (int)sizeof(C2)));
-            attr = true;
-        }
+        qaoa_status ast = ensure_attributes<real>();
+        if (ast != QAOA_OK) return ast;
         kfn<<<1, kSmallThreadsGrad, (size_t)2 * s->dim * sizeof(C2), s->stream>>>(j);
         CUDA_TRY(cudaGetLastError());
         s->launches++;
@@ -699,11 +728,8 @@ qaoa_status gradient_impl(qaoa_state s, int p, const double* gamma, const double
         }
         auto kfn = grad_kernel<real, Q, R>;
         const size_t smem = (size_t)(1u << Q) * sizeof(C2);
-        static bool attr = false;
-        if (!attr) {
-            CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            attr = true;
-        }
+        qaoa_status ast = ensure_attributes<real>();
+        if (ast != QAOA_OK) return ast;
         TileArgs<Q> a;
         for (const Pass& ps : plan.passes) {
             std::memset(&a, 0, sizeof(a));
@@ -723,17 +749,30 @@ qaoa_status gradient_impl(qaoa_state s, int p, const double* gamma, const double
             s->launches += 2;
         }
     }
-    std::vector<double> host(2 * (size_t)p);
-    CUDA_TRY(cudaMemcpyAsync(host.data(), s->d_gacc, host.size() * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
-    CUDA_TRY(cudaStreamSynchronize(s->stream));
-    for (int k = 0; k < p; ++k) {
-        d_beta[k] = 2.0 * host[k];
-        d_gamma[k] = 2.0 * host[p + k];
-    }
     // the sweep consumed the state: it is |+>^n again
     s->lazy = true;
     s->exp_valid = false;
     s->compl_ = false;
+    return QAOA_OK;
+}
+
+template <typename real>
+qaoa_status gradient_impl(qaoa_state s, int p, const double* gamma, const double* beta, void* work,
+                          double* out_c, double* d_gamma, double* d_beta) {
+    qaoa_status st = grad_workspace(s, p);
+    if (st != QAOA_OK) return st;
+    st = gradient_async<real>(s, p, gamma, beta, work);
+    if (st != QAOA_OK) return st;
+    std::vector<double> host(2 * (size_t)p + 2);
+    CUDA_TRY(cudaMemcpyAsync(host.data(), s->d_result, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(cudaMemcpyAsync(host.data() + 2, s->d_gacc, 2 * (size_t)p * sizeof(double), cudaMemcpyDeviceToHost,
+                             s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    if (out_c) *out_c = host[0];
+    for (int k = 0; k < p; ++k) {
+        d_beta[k] = 2.0 * host[2 + k];
+        d_gamma[k] = 2.0 * host[2 + p + k];
+    }
     return QAOA_OK;
 }
 
@@ -961,3 +1000,5 @@ qaoa_status qaoa_expectation_static(const qaoa_graph* g, qaoa_prec prec, const v
 const char* qaoa_last_error(void) { return g_last_error.c_str(); }
 
 }  // extern "C"
+
+#include "server.cuh"

@@ -1035,6 +1035,38 @@ __global__ void coeff_kernel(const __grid_constant__ CoeffArgs a) {
     }
 }
 
+// Batched coefficient tables for packed small states: CTA b builds job b's plain per-level
+// phase tables and (cos b, sin b) mixer entries (no folded factors; small states use plain RX).
+struct CoeffJob {
+    int32_t levels, E1;
+    const double* gamma;
+    const double* beta;
+    void* phase;  // [level][E1]
+    void* mix;    // [3 * level]
+};
+
+template <typename real>
+__global__ void coeff_batch_kernel(const CoeffJob* __restrict__ jobs) {
+    using C2 = typename C2T<real>::type;
+    const CoeffJob j = jobs[blockIdx.x];
+    for (int k = 0; k < j.levels; ++k) {
+        C2* T = reinterpret_cast<C2*>(j.phase) + (size_t)k * j.E1;
+        for (int c = threadIdx.x; c < j.E1; c += blockDim.x) {
+            double s, co;
+            sincos(j.gamma[k] * (double)c, &s, &co);
+            T[c] = make_c2((real)co, (real)(-s));
+        }
+        if (threadIdx.x == 0) {
+            double s, co;
+            sincos(j.beta[k], &s, &co);
+            C2* m = reinterpret_cast<C2*>(j.mix) + 3 * k;
+            m[0] = make_c2((real)co, (real)s);
+            m[1] = make_c2((real)0, (real)0);
+            m[2] = make_c2((real)1, (real)0);
+        }
+    }
+}
+
 // Reverses the index order of a state in place (psi_z <-> psi_{~z}), one swap per thread.
 template <typename real>
 __global__ void complement_kernel(void* state, uint64_t dim) {

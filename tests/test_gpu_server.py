@@ -1,0 +1,152 @@
+"""Continuous-batching server (qaoa_server_*): every result equals the same request run alone,
+admission by HBM footprint, queue limits, graphs on and off, shutdown with work in flight."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2312_03019_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2312_03019_b300 import build
+    build.build()
+    from paper_2312_03019_b300 import binding
+    return binding
+
+
+def alone(B, g, gamma, beta, grad, prec="c64"):
+    import torch
+    s = B.QAOAState(g, prec)
+    if grad:
+        work = torch.empty(s.nbytes, dtype=torch.uint8, device="cuda")
+        c, dg, db = B.qaoa_gradient(s.handle, gamma, beta, work.data_ptr(), s.nbytes)
+        s.close()
+        return c, dg, db
+    s.apply_layers(gamma, beta)
+    c, _ = s.expectation()
+    s.close()
+    return c, None, None
+
+
+def wait_all(B, sv, tickets, timeout=120.0):
+    res = {}
+    t0 = time.time()
+    while len(res) < len(tickets):
+        for t in tickets:
+            if t not in res:
+                r = B.qaoa_poll(sv, t)
+                if r is not None:
+                    res[t] = r
+        if time.time() - t0 > timeout:
+            raise TimeoutError("server did not finish")
+        time.sleep(0.001)
+    return res
+
+
+def mixed_requests(count, seed=3):
+    out = []
+    rng = np.random.default_rng(seed)
+    for i in range(count):
+        n = int(rng.integers(8, 22))
+        g = I.regular3(n, i) if (n % 2 == 0 and i % 2) else I.gnp(n, 0.3, i)
+        p = int(rng.integers(1, 5))
+        ga, be = I.angles(p, seed=100 + i)
+        out.append((g, ga, be, bool(i % 4 == 0)))
+    return out
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+def test_results_identical_alone_and_in_the_mix(B, graphs):
+    reqs = mixed_requests(48)
+    sv = B.qaoa_server_create(4 << 30, "c64", max_inflight=32, max_batch=16, streams=4, use_graphs=graphs)
+    tickets = [B.qaoa_submit(sv, g, ga, be, grad) for g, ga, be, grad in reqs]
+    res = wait_all(B, sv, tickets)
+    stats = B.qaoa_server_stats_read(sv)
+    B.qaoa_server_destroy(sv)
+    assert stats["completed"] == len(reqs) and stats["failed"] == 0
+    assert stats["batches"] >= 1 and stats["batched_requests"] >= 1
+    if graphs:
+        assert stats["graph_launches"] >= 1
+    for (g, ga, be, grad), t in zip(reqs, tickets):
+        r = res[t]
+        assert r["status"] == 0
+        c, dg, db = alone(B, g, ga, be, grad)
+        assert r["expectation"] == c, (g.name, r["expectation"], c)  # bit-identical
+        if grad:
+            assert np.array_equal(r["d_gamma"], dg) and np.array_equal(r["d_beta"], db)
+
+
+def test_admission_under_a_small_arena(B):
+    # the arena holds about one n = 22 state at a time: requests must queue and still complete
+    g = I.regular3(22, 1)
+    ga, be = I.angles(2, 1)
+    ref, _, _ = alone(B, g, ga, be, False)
+    sv = B.qaoa_server_create(48 << 20, "c64", max_inflight=16, max_batch=8, streams=4)
+    tickets = [B.qaoa_submit(sv, g, ga, be) for _ in range(6)]
+    res = wait_all(B, sv, tickets)
+    stats = B.qaoa_server_stats_read(sv)
+    B.qaoa_server_destroy(sv)
+    assert all(res[t]["expectation"] == ref for t in tickets)
+    assert stats["arena_peak_bytes"] <= 48 << 20
+
+
+def test_rejections_and_unknown_tickets(B):
+    sv = B.qaoa_server_create(16 << 20, "c64", max_inflight=1, queue_capacity=2, max_batch=1, streams=1)
+    big = I.regular3(24, 0)  # 128 MiB state: larger than the whole arena
+    with pytest.raises(B.QAOAError) as ei:
+        B.qaoa_submit(sv, big, [0.1], [0.2])
+    assert ei.value.status == B.QAOA_ERR_OOM
+    with pytest.raises(B.QAOAError) as ei:
+        B.qaoa_submit(sv, I.Graph(4, np.array([[0, 0]], dtype=np.int32)), [0.1], [0.2])
+    assert ei.value.status == B.QAOA_ERR_INVALID
+    with pytest.raises(B.QAOAError):
+        B.qaoa_submit(sv, I.ring(6), [float("nan")], [0.2])
+    with pytest.raises(B.QAOAError) as ei:
+        B.qaoa_poll(sv, 987654)
+    assert ei.value.status == B.QAOA_ERR_INVALID
+    # flood the queue: some submissions must come back with QAOA_ERR_AGAIN
+    g = I.regular3(20, 2)
+    ga, be = I.angles(6, 2)
+    tickets, again = [], 0
+    for _ in range(64):
+        try:
+            tickets.append(B.qaoa_submit(sv, g, ga, be))
+        except B.QAOAError as e:
+            assert e.status == B.QAOA_ERR_AGAIN
+            again += 1
+    assert again > 0
+    res = wait_all(B, sv, tickets)
+    assert all(r["status"] == 0 for r in res.values())
+    t = tickets[0]
+    with pytest.raises(B.QAOAError):
+        B.qaoa_poll(sv, t)  # released after the first successful poll
+    B.qaoa_server_destroy(sv)
+
+
+def test_destroy_with_work_in_flight(B):
+    sv = B.qaoa_server_create(2 << 30, "c64", max_inflight=8, max_batch=8, streams=2)
+    g = I.regular3(24, 3)
+    ga, be = I.angles(6, 3)
+    for _ in range(12):
+        B.qaoa_submit(sv, g, ga, be, True)
+    t0 = time.time()
+    B.qaoa_server_destroy(sv)  # waits for admitted work, drops the rest
+    assert time.time() - t0 < 60
+
+
+def test_c128_server_gradient(B):
+    g = I.gnp(15, 0.4, 5)
+    ga, be = I.angles(3, 5)
+    c, dg, db = alone(B, g, ga, be, True, "c128")
+    sv = B.qaoa_server_create(1 << 30, "c128", max_inflight=4, max_batch=4, streams=2)
+    t = B.qaoa_submit(sv, g, ga, be, True)
+    r = wait_all(B, sv, [t])[t]
+    B.qaoa_server_destroy(sv)
+    assert r["expectation"] == c and np.array_equal(r["d_gamma"], dg) and np.array_equal(r["d_beta"], db)
