@@ -144,10 +144,12 @@ qaoa_status qaoa_cut_table_geometry(const qaoa_graph *g, qaoa_prec prec, int32_t
 
 /* Host-only description of the pass plan for n qubits, precision prec and p levels (no GPU
  * needed).  Writes up to cap int32 values into out and returns the number needed in *count:
- *   [Q, R, c_min, n_groups, (lo, size) per group, n_passes,
+ *   [Q, R, c_min, n_groups, (size, bit indices...) per group, n_passes,
  *    per pass: (group, n_ops, (kind, arg, mask) per op)]
  * kind: 1 load, 2 synthesise |+> (arg = layout), 3 exchange (arg = layout), 4 RX (arg =
- * level, mask = local target bits), 5 phase (arg = level), 6 expectation, 7 store.  Small
+ * level, mask = local target bits), 5 phase (arg = level), 6 expectation, 7 store, 8 cut
+ * values; the adjoint sweep's plan (not described here) also uses 9 lambda = C psi, 10 inverse
+ * RX with pair sums, 11 gamma sums and 12 conjugate phase (arg = level | slot << 16).  Small
  * states (whole state in one CTA) have no pass plan: *count = 0.  For tests of the
  * planner: every level must apply RX to every qubit exactly once, phases in order. */
 qaoa_status qaoa_plan_describe(int32_t n, qaoa_prec prec, int32_t p, int32_t *out, int32_t cap,
