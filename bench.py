@@ -49,6 +49,8 @@ def parse_args():
     ap.add_argument("--cpu-sample-n", type=int, default=24)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--weighted", action="store_true",
+                    help="edge weights U[0.1, 2] on the same graph (Algorithm 2 path), for context")
     ap.add_argument("--serve", action="store_true",
                     help="serving mode: an open-loop Poisson request stream through qaoa_submit/qaoa_poll")
     ap.add_argument("--serve-requests", type=int, default=4096)
@@ -57,17 +59,22 @@ def parse_args():
     return ap.parse_args()
 
 
-def workload(n: int, p: int):
+def workload(n: int, p: int, weighted: bool = False):
     g = I.regular3(n, 0)
+    if weighted:
+        g = I.random_weights(g, seed=0, lo=0.1, hi=2.0)
     gamma, beta = I.angles(p, 0)
     return g, gamma, beta
 
 
 def workload_name(g, p, prec):
     fam = "near-3-regular (one degree-2 vertex)" if g.n % 2 else "3-regular"
+    if g.weights is not None:
+        fam += " edge-weighted U[0.1, 2]"
     elem = "complex64" if prec == "c64" else "complex128"
+    cut = "weighted C(z) in fixed point on the fly" if g.weights is not None else "cut values on the fly"
     return (f"{fam} graph n={g.n}, |E|={g.m}, seed 0, p={p} seeded levels, {elem} state of 2^{g.n} "
-            f"amplitudes, cut values on the fly, <C> and norm reduced in FP64")
+            f"amplitudes, {cut}, <C> and norm reduced in FP64")
 
 
 def measured_peaks():
@@ -222,7 +229,7 @@ def run_ours(args):
     bld.build()
     from paper_2312_03019_b300 import binding as B
 
-    g, gamma, beta = workload(args.n, args.p)
+    g, gamma, beta = workload(args.n, args.p, args.weighted)
     warm = max(3, args.warmup)
     st = B.QAOAState(g, args.prec, device=dev)
     stream = st.stream

@@ -55,8 +55,14 @@ typedef enum { QAOA_C64 = 0, QAOA_C128 = 1 } qaoa_prec;
  *   n       : 1 <= n <= 34
  *   m       : number of edges, m >= 0
  *   edges   : 2*m int32 endpoints (u0, v0, u1, v1, ...), 0 <= u, v < n, u != v, no pair twice
- *   weights : NULL for unit weights (Algorithm 3); otherwise m finite doubles (Algorithm 2)
- * Unit weights are required with more than 65535 edges' worth of cut values (never for n<=34). */
+ *   weights : NULL for unit weights (Algorithm 3); otherwise m finite doubles w_e with
+ *             |w_e| <= 1e12 (Algorithm 2: C(z) = sum_e w_e (z_u xor z_v)); negative weights
+ *             are allowed.  Weights that are all exactly 1 take the unit-weight path.
+ * With weights, the kernels evaluate two sums per amplitude in B-bit fixed point (B = 32 for
+ * complex64, 64 for complex128), each exact modulo 2^B: the phase angle gamma_k C(z) from
+ * per-edge angles gamma_k w_e / (2 pi) rounded to 2^-B turns (error at most m 2^-B turns), and
+ * the value C(z) from weights rounded to 2^-S with S the largest power such that
+ * sum |w_e| 2^S <= 2^(B-2) (error at most m 2^-(S+1)). */
 typedef struct {
     int32_t n;
     int32_t m;
@@ -75,7 +81,7 @@ size_t qaoa_state_bytes(int32_t n, qaoa_prec prec);
  * new state handle holding |+>^n (Section 2.2, launch control).  The buffer is not written
  * here: the uniform amplitudes are produced by the first kernel that needs them, so the first
  * level of qaoa_apply_layers reads nothing.  Validates the graph (QAOA_ERR_INVALID on a self
- * loop, repeated edge, endpoint out of range, non-finite or negative weight), encodes the
+ * loop, repeated edge, endpoint out of range, non-finite weight or |w| > 1e12), encodes the
  * rows graph_I of Table 1 and the pass plan, and allocates workspace (QAOA_ERR_OOM).  On
  * success *out receives the handle. */
 qaoa_status qaoa_state_init(const qaoa_graph *g, qaoa_prec prec, void *dev_buf, size_t buf_bytes,
@@ -130,10 +136,18 @@ qaoa_status qaoa_state_copy_out(qaoa_state s, void *host_dst, size_t bytes);
 qaoa_status qaoa_state_free(qaoa_state s);
 
 /* Cut value C(z) of every basis state (Algorithm 3 on the GPU, computed by the same device
- * code the cost phase uses), written to host_out[0 .. 2^n - 1].  Unit weights only;
- * n <= 30.  Runs on the current device's legacy default stream and synchronises it.  Parity
- * hook. */
+ * code the cost phase uses), written to host_out[0 .. 2^n - 1].  Unit weights only
+ * (QAOA_ERR_INVALID for a weighted graph); n <= 30.  Runs on the current device's legacy
+ * default stream and synchronises it.  Parity hook. */
 qaoa_status qaoa_cut_table(const qaoa_graph *g, uint16_t *host_out);
+
+/* C(z) of every basis state as doubles, for unit or edge-weighted graphs (Algorithm 2's cut
+ * value, from the same device code as <C> and the adjoint's C psi), evaluated in precision
+ * prec's fixed point (see qaoa_graph) under the geometry of mixer group `group` and register
+ * layout `layout` (group < 0: the path the state size uses by default).  n <= 28.  Synchronous,
+ * legacy default stream.  Parity hook. */
+qaoa_status qaoa_cut_table_f64(const qaoa_graph *g, qaoa_prec prec, int32_t group, int32_t layout,
+                               double *host_out);
 
 /* Same as qaoa_cut_table, but evaluated under the tile geometry of mixer group `group`
  * (0 = the low group) of the pass plan for precision `prec`, in register layout `layout`
@@ -188,7 +202,8 @@ qaoa_status qaoa_profile_read(qaoa_state s, qaoa_profile_stats *out);
  * array's device address (cudaGetSymbolAddress); make that first call before any stream
  * capture.  All calls share the one array: every entry a call reads is written earlier in the
  * same call, so nothing has to be cleared, but two calls whose work overlaps on the GPU (on
- * different streams or host threads) race on it and give wrong results. */
+ * different streams or host threads) race on it and give wrong results.  Unit weights only
+ * (a graph with a weights array returns QAOA_ERR_UNSUPPORTED). */
 qaoa_status qaoa_expectation_static(const qaoa_graph *g, qaoa_prec prec, const void *dev_state,
                                     size_t state_bytes, void *cuda_stream, double *out_c,
                                     double *out_norm);
@@ -252,7 +267,8 @@ typedef struct qaoa_server_s *qaoa_server;
 /* Creates the server and starts its scheduler thread on the current device.  Allocates the arena,
  * pinned result buffers, streams and events (QAOA_ERR_OOM if the arena does not fit). */
 qaoa_status qaoa_server_create(const qaoa_server_config *cfg, qaoa_server *out);
-/* Queues a request (graph and angles are copied); *ticket identifies it.  QAOA_ERR_AGAIN when the
+/* Queues a request (graph and angles are copied); *ticket identifies it.  Edge-weighted graphs
+ * are accepted and always run alone (never packed with other small requests).  QAOA_ERR_AGAIN when the
  * queue is full; QAOA_ERR_INVALID for a bad request; QAOA_ERR_OOM when its footprint exceeds the
  * whole arena.  Thread-safe. */
 qaoa_status qaoa_submit(qaoa_server sv, const qaoa_request *r, uint64_t *ticket);

@@ -82,6 +82,7 @@ _sig("qaoa_state_copy_out", ctypes.c_int, [_vp, _vp, ctypes.c_size_t])
 _sig("qaoa_state_free", ctypes.c_int, [_vp])
 _sig("qaoa_cut_table", ctypes.c_int, [ctypes.POINTER(_Graph), _vp])
 _sig("qaoa_cut_table_geometry", ctypes.c_int, [ctypes.POINTER(_Graph), ctypes.c_int, _i32, _i32, _vp])
+_sig("qaoa_cut_table_f64", ctypes.c_int, [ctypes.POINTER(_Graph), ctypes.c_int, _i32, _i32, _vp])
 _sig("qaoa_plan_describe", ctypes.c_int, [_i32, ctypes.c_int, _i32, ctypes.POINTER(_i32), _i32,
                                            ctypes.POINTER(_i32)])
 _sig("qaoa_profile_enable", ctypes.c_int, [_vp, _i32])
@@ -223,6 +224,14 @@ def qaoa_cut_table(g) -> np.ndarray:
     gs, keep = _graph(g)
     out = np.empty(1 << int(g.n), dtype=np.uint16)
     _check(_lib.qaoa_cut_table(ctypes.byref(gs), _vp(out.ctypes.data)))
+    return out
+
+
+def qaoa_cut_table_f64(g, prec="c64", group: int = -1, layout: int = 0) -> np.ndarray:
+    """C(z) for every z as doubles (unit or edge-weighted graphs), from the device evaluation."""
+    gs, keep = _graph(g)
+    out = np.empty(1 << int(g.n), dtype=np.float64)
+    _check(_lib.qaoa_cut_table_f64(ctypes.byref(gs), _prec(prec), int(group), int(layout), _vp(out.ctypes.data)))
     return out
 
 

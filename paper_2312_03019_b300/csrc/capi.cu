@@ -50,32 +50,57 @@ constexpr int kSmallMaxC128 = 13;  // 2^13 x 16 B
 
 struct HostGraph {
     int n = 0, m = 0;
-    std::vector<std::pair<int, int>> edges;  // u < v
+    std::vector<std::pair<int, int>> edges;  // u < v, ascending
     uint64_t upper[kMaxN] = {};              // graph_I rows (Table 1)
     uint64_t adj[kMaxN] = {};                // full adjacency
+    bool weighted = false;                   // false: every weight is 1 (the cut count)
+    std::vector<double> w;                   // weight of edges[e] (weighted graphs)
 };
+
+// Phase-table entries per level: |E| + 1 for the cut count, one (the folded factor) when the
+// phase comes from the weighted sums.
+int table_entries(const HostGraph& g) { return g.weighted ? 1 : g.m + 1; }
+
+// 2^S for the value weights: the largest power of two with sum |w_e| 2^S <= 2^(B-2), B the
+// fixed-point word size of the precision (32 for complex64, 64 for complex128).
+double value_mul(const HostGraph& g, int prec) {
+    double tot = 0.0;
+    for (double x : g.w) tot += std::fabs(x);
+    const int B = prec == QAOA_C64 ? 32 : 64;
+    if (!(tot > 0.0)) return std::ldexp(1.0, B - 2);
+    return std::ldexp(1.0, B - 2 - (int)std::ceil(std::log2(tot)));
+}
 
 qaoa_status encode_graph(const qaoa_graph* g, HostGraph& hg) {
     if (!g) return fail(QAOA_ERR_INVALID, "graph is NULL");
     if (g->n < 1 || g->n > kMaxN) return fail(QAOA_ERR_INVALID, "n must be in [1, 34]");
     if (g->m < 0) return fail(QAOA_ERR_INVALID, "m must be >= 0");
     if (g->m > 0 && !g->edges) return fail(QAOA_ERR_INVALID, "edges is NULL");
-    if (g->weights) return fail(QAOA_ERR_UNSUPPORTED, "weighted graphs are not supported by this entry point");
     hg.n = g->n;
     hg.m = g->m;
     std::set<std::pair<int, int>> seen;
+    std::vector<std::pair<std::pair<int, int>, double>> ew;
+    bool unit = true;
     for (int e = 0; e < g->m; ++e) {
         int u = g->edges[2 * e], v = g->edges[2 * e + 1];
         if (u < 0 || v < 0 || u >= g->n || v >= g->n) return fail(QAOA_ERR_INVALID, "edge endpoint out of range");
         if (u == v) return fail(QAOA_ERR_INVALID, "self loop");
         if (u > v) std::swap(u, v);
         if (!seen.insert({u, v}).second) return fail(QAOA_ERR_INVALID, "repeated edge");
-        hg.edges.push_back({u, v});
+        const double w = g->weights ? g->weights[e] : 1.0;
+        if (!std::isfinite(w)) return fail(QAOA_ERR_INVALID, "non-finite edge weight");
+        if (std::fabs(w) > 1e12) return fail(QAOA_ERR_INVALID, "edge weight magnitude above 1e12");
+        unit = unit && w == 1.0;
+        ew.push_back({{u, v}, w});
         hg.upper[u] |= 1ull << v;
         hg.adj[u] |= 1ull << v;
         hg.adj[v] |= 1ull << u;
     }
-    std::sort(hg.edges.begin(), hg.edges.end());
+    std::sort(ew.begin(), ew.end());
+    for (const auto& x : ew) hg.edges.push_back(x.first);
+    hg.weighted = !unit;  // all weights 1: the integer cut-count path, identical results
+    if (hg.weighted)
+        for (const auto& x : ew) hg.w.push_back(x.second);
     return QAOA_OK;
 }
 
@@ -137,6 +162,16 @@ void fill_geometry(TileArgs<Q>& a, const HostGraph& hg, const Geometry& geo, con
         a.locUpper[u] = la & ~((2u << u) - 1u);
         a.outAdj[u] = hg.adj[gu] & ~tileMask & nMask;
     }
+    // weighted split: local bit of every index bit and the tile-internal edges (edge-weighted
+    // graphs only; the allocation-free path encodes unit-weight graphs without the edge list)
+    a.m = hg.m;
+    a.wn = 0;
+    for (int v = 0; v < kMaxN; ++v) a.gl2loc[v] = (v < hg.n && lpos[v] >= 0) ? (uint8_t)lpos[v] : (uint8_t)0xff;
+    for (int e = 0; hg.weighted && e < hg.m; ++e) {
+        const int la = lpos[hg.edges[e].first], lb = lpos[hg.edges[e].second];
+        if (la < 0 || lb < 0) continue;
+        a.wloc[a.wn++] = (uint32_t)e | (uint32_t)std::min(la, lb) << 10 | (uint32_t)std::max(la, lb) << 14;
+    }
     for (int L = 0; L < 3; ++L) {
         const int rl = tc.regLo(L);
         for (int x = 0; x < 32; ++x) {
@@ -148,6 +183,54 @@ void fill_geometry(TileArgs<Q>& a, const HostGraph& hg, const Geometry& geo, con
             a.crtab[L][x] = (uint8_t)c;
         }
     }
+}
+
+// Weighted-sum slots of one pass: slot 0 is the value row (<C>, lambda, the gamma terms); each
+// level whose phase the pass applies gets the next slot, reading wfix row 2 + level.
+template <int Q>
+bool fill_weighted(TileArgs<Q>& a, const HostGraph& g, int prec, const void* wfix, const Op* ops, int nops) {
+    a.wfix = wfix;
+    a.vscale = 1.0 / value_mul(g, prec);
+    a.wrow[0] = 1;
+    a.wnslots = 1;
+    for (int i = 0; i < nops; ++i) {
+        if (ops[i].kind != OP_PHASE && ops[i].kind != OP_PHASED) continue;
+        const int level = ops[i].arg & 0xffff;
+        bool have = false;
+        for (int sl = 1; sl < a.wnslots; ++sl) have = have || a.wrow[sl] == 2 + level;
+        if (have) continue;
+        if (a.wnslots == kWSlots || level >= kLayerChunk) return false;
+        a.wslot[level] = (int8_t)a.wnslots;
+        a.wrow[a.wnslots++] = (int16_t)(2 + level);
+    }
+    return true;
+}
+
+// Weights, endpoints and the value scale of an edge-weighted graph in the coefficient launch.
+void fill_coeff_weights(CoeffArgs& ca, const HostGraph& g, int prec, void* wfix, int wrow0) {
+    if (!g.weighted) return;
+    ca.weighted = 1;
+    ca.m = g.m;
+    ca.wrow0 = wrow0;
+    ca.vmul = value_mul(g, prec);
+    ca.wfix = wfix;
+    for (int e = 0; e < g.m; ++e) {
+        ca.w[e] = g.w[e];
+        ca.uv[e] = (uint16_t)(g.edges[e].first | g.edges[e].second << 8);
+    }
+}
+
+// Device bytes of the fixed-point rows: endpoints, values and `levels` angle rows.
+size_t wfix_bytes(const HostGraph& g, int prec, int levels) {
+    return (size_t)(2 + levels) * (size_t)std::max(1, g.m) * (prec == QAOA_C64 ? 4 : 8);
+}
+
+template <typename J>
+void set_small_weights(J& j, const HostGraph& g, int prec, const void* wfix) {
+    if (!g.weighted) return;
+    j.wfix = wfix;
+    j.m = g.m;
+    j.vscale = 1.0 / value_mul(g, prec);
 }
 
 template <typename real>
@@ -182,6 +265,8 @@ struct qaoa_state_s {
     uint64_t ntiles = 1;
     void* d_phase = nullptr;
     void* d_mix = nullptr;
+    void* d_wfix = nullptr;       // weighted graphs: fixed-point rows (2 + kLayerChunk) x m
+    void* d_gwfix = nullptr;      // weighted graphs: the adjoint sweep's rows (2 + levels) x m
     double2* d_partials = nullptr;
     double2* d_result = nullptr;
     double2* h_result = nullptr;
@@ -224,9 +309,13 @@ qaoa_status ensure_attributes() {
     if (done) return QAOA_OK;
     constexpr int Q = PrecTraits<real>::Q, R = PrecTraits<real>::R;
     using C2 = typename C2T<real>::type;
-    CUDA_TRY(cudaFuncSetAttribute(tile_kernel<real, Q, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    CUDA_TRY(cudaFuncSetAttribute(tile_kernel<real, Q, R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)((1u << Q) * sizeof(C2))));
-    CUDA_TRY(cudaFuncSetAttribute(grad_kernel<real, Q, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    CUDA_TRY(cudaFuncSetAttribute(tile_kernel<real, Q, R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)((1u << Q) * sizeof(C2))));
+    CUDA_TRY(cudaFuncSetAttribute(grad_kernel<real, Q, R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)((1u << Q) * sizeof(C2))));
+    CUDA_TRY(cudaFuncSetAttribute(grad_kernel<real, Q, R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)((1u << Q) * sizeof(C2))));
     CUDA_TRY(cudaFuncSetAttribute(small_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024));
     CUDA_TRY(cudaFuncSetAttribute(small_batch_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024));
@@ -245,7 +334,7 @@ template <typename real>
 qaoa_status launch_tile(qaoa_state s, TileArgs<PrecTraits<real>::Q>& a, int kind) {
     constexpr int Q = PrecTraits<real>::Q, R = PrecTraits<real>::R;
     using C2 = typename C2T<real>::type;
-    auto kfn = tile_kernel<real, Q, R>;
+    auto kfn = s->g.weighted ? tile_kernel<real, Q, R, true> : tile_kernel<real, Q, R, false>;
     const size_t smem = (size_t)(1u << Q) * sizeof(C2);
     qaoa_status ast = ensure_attributes<real>();
     if (ast != QAOA_OK) return ast;
@@ -282,13 +371,14 @@ void fill_program(TileArgs<PrecTraits<real>::Q>& a, qaoa_state s, const Pass& ps
         const uint8_t k = ps.ops[i].kind;
         if (k == OP_PHASE || k == OP_EXPECT || k == OP_CUTVAL) a.need_cut = 1;
     }
-    a.E1 = s->g.m + 1;
+    a.E1 = table_entries(s->g);
     a.init_amp = std::pow(2.0, -0.5 * s->n);
     a.state = s->buf;
     a.phase = s->d_phase;
     a.mix = s->d_mix;
     a.partials = s->d_partials;
     a.cutout = nullptr;
+    if (s->g.weighted) fill_weighted(a, s->g, s->prec, s->d_wfix, a.ops, a.nops);
 }
 
 template <typename real>
@@ -311,9 +401,10 @@ qaoa_status apply_chunk(qaoa_state s, int levels, const double* gamma, const dou
     CoeffArgs ca;
     std::memset(&ca, 0, sizeof(ca));
     ca.levels = levels;
-    ca.E1 = s->g.m + 1;
+    ca.E1 = table_entries(s->g);
     ca.n = s->n;
     ca.fold_factors = s->small ? 0 : 1;
+    fill_coeff_weights(ca, s->g, s->prec, s->d_wfix, 2);
     int folded = 0;
     for (int k = 0; k < levels; ++k) {
         ca.gamma[k] = gamma[k];
@@ -331,7 +422,7 @@ qaoa_status apply_chunk(qaoa_state s, int levels, const double* gamma, const dou
     if (folded & 1) s->compl_ = !s->compl_;
     ca.phase = s->d_phase;
     ca.mix = s->d_mix;
-    dim3 grid((unsigned)std::max(1, (ca.E1 + 255) / 256), (unsigned)levels);
+    dim3 grid((unsigned)std::max(1, (std::max(ca.E1, ca.m) + 255) / 256), (unsigned)levels);
     coeff_kernel<real><<<grid, 256, 0, s->stream>>>(ca);
     CUDA_TRY(cudaGetLastError());
     s->launches++;
@@ -341,7 +432,7 @@ qaoa_status apply_chunk(qaoa_state s, int levels, const double* gamma, const dou
         std::memset(&j, 0, sizeof(j));
         j.n = s->n;
         j.levels = levels;
-        j.E1 = s->g.m + 1;
+        j.E1 = table_entries(s->g);
         j.synth = s->lazy ? 1 : 0;
         j.expect = expect ? 1 : 0;
         j.store = 1;
@@ -351,6 +442,7 @@ qaoa_status apply_chunk(qaoa_state s, int levels, const double* gamma, const dou
         j.phase = s->d_phase;
         j.mix = s->d_mix;
         j.partials = s->d_partials;
+        set_small_weights(j, s->g, s->prec, s->d_wfix);
         qaoa_status st = launch_small<real>(s, j);
         if (st != QAOA_OK) return st;
     } else {
@@ -365,6 +457,21 @@ qaoa_status apply_chunk(qaoa_state s, int levels, const double* gamma, const dou
     } else {
         s->exp_valid = false;
     }
+    return QAOA_OK;
+}
+
+// Endpoint and value rows of an edge-weighted graph (a coefficient launch with no levels).
+template <typename real>
+qaoa_status write_weight_rows(qaoa_state s) {
+    CoeffArgs ca;
+    std::memset(&ca, 0, sizeof(ca));
+    ca.levels = 0;
+    ca.E1 = 1;
+    ca.n = s->n;
+    fill_coeff_weights(ca, s->g, s->prec, s->d_wfix, 2);
+    coeff_kernel<real><<<(unsigned)std::max(1, (ca.m + 255) / 256), 256, 0, s->stream>>>(ca);
+    CUDA_TRY(cudaGetLastError());
+    s->launches++;
     return QAOA_OK;
 }
 
@@ -394,7 +501,7 @@ qaoa_status compute_partials(qaoa_state s) {
         std::memset(&j, 0, sizeof(j));
         j.n = s->n;
         j.levels = 0;
-        j.E1 = s->g.m + 1;
+        j.E1 = table_entries(s->g);
         j.synth = s->lazy ? 1 : 0;
         j.expect = 1;
         j.store = 0;
@@ -404,6 +511,7 @@ qaoa_status compute_partials(qaoa_state s) {
         j.phase = s->d_phase;
         j.mix = s->d_mix;
         j.partials = s->d_partials;
+        set_small_weights(j, s->g, s->prec, s->d_wfix);
         qaoa_status st = launch_small<real>(s, j);
         if (st != QAOA_OK) return st;
         s->partial_count = 1;
@@ -449,6 +557,8 @@ void release(qaoa_state s) {
     }
     cudaFree(s->d_phase);
     cudaFree(s->d_mix);
+    cudaFree(s->d_wfix);
+    cudaFree(s->d_gwfix);
     cudaFree(s->d_partials);
     cudaFree(s->d_result);
     cudaFree(s->d_gtab);
@@ -465,12 +575,16 @@ bool angles_ok(int p, const double* x) {
     return true;
 }
 
+// C(z) of every z through the device's on-the-fly evaluation: uint16 cut counts (unit weights)
+// or doubles (edge-weighted graphs, host_out_w).  group < 0: the default path for the size.
 template <typename real>
-qaoa_status cut_table_impl(const HostGraph& hg, int prec, int group, int layout, uint16_t* host_out) {
+qaoa_status cut_table_impl(const HostGraph& hg, int prec, int group, int layout, uint16_t* host_out,
+                           double* host_out_w = nullptr) {
     const int n = hg.n;
     const uint64_t dim = 1ull << n;
-    uint16_t* d_out = nullptr;
-    CUDA_TRY(cudaMalloc(&d_out, dim * sizeof(uint16_t)));
+    const size_t ob = hg.weighted ? sizeof(double) : sizeof(uint16_t);
+    void* d_out = nullptr;
+    CUDA_TRY(cudaMalloc(&d_out, dim * ob));
     qaoa_state_s tmp;
     tmp.n = n;
     tmp.prec = prec;
@@ -479,15 +593,23 @@ qaoa_status cut_table_impl(const HostGraph& hg, int prec, int group, int layout,
     tmp.tc = tile_config_for(prec);
     tmp.stream = nullptr;
     qaoa_status st = QAOA_OK;
-    if (group < 0 && is_small(n, prec)) {
+    if (hg.weighted) {
+        const cudaError_t e = cudaMalloc(&tmp.d_wfix, wfix_bytes(hg, prec, 0));
+        if (e != cudaSuccess) st = cuda_fail(e, "cudaMalloc(weight rows)");
+        if (st == QAOA_OK) st = write_weight_rows<real>(&tmp);
+    }
+    if (st != QAOA_OK) {
+    } else if (group < 0 && is_small(n, prec)) {
         SmallJob j;
         std::memset(&j, 0, sizeof(j));
         j.n = n;
         j.synth = 1;
         j.cutval = 1;
-        j.E1 = hg.m + 1;
+        j.E1 = table_entries(hg);
         for (int v = 0; v < kMaxN; ++v) j.gmask[v] = v < n ? hg.upper[v] : 0;
-        j.cutout = d_out;
+        j.cutout = static_cast<uint16_t*>(d_out);
+        j.cutout_w = static_cast<double*>(d_out);
+        set_small_weights(j, hg, prec, tmp.d_wfix);
         tmp.small = true;
         tmp.dim = dim;
         st = launch_small<real>(&tmp, j);
@@ -505,16 +627,20 @@ qaoa_status cut_table_impl(const HostGraph& hg, int prec, int group, int layout,
                 TileArgs<Q> a;
                 std::memset(&a, 0, sizeof(a));
                 fill_program<real>(a, &tmp, plan.passes[0]);
-                a.cutout = d_out;
+                a.cutout = static_cast<uint16_t*>(d_out);
+                a.cutout_w = static_cast<double*>(d_out);
                 st = launch_tile<real>(&tmp, a, 0);
             }
         }
     }
     if (st == QAOA_OK) {
-        cudaError_t e = cudaMemcpy(host_out, d_out, dim * sizeof(uint16_t), cudaMemcpyDeviceToHost);
+        cudaError_t e = cudaMemcpy(hg.weighted ? (void*)host_out_w : (void*)host_out, d_out, dim * ob,
+                                   cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) st = cuda_fail(e, "cudaMemcpy(cut table)");
     }
     cudaFree(d_out);
+    cudaFree(tmp.d_wfix);
+    tmp.d_wfix = nullptr;
     return st;
 }
 
@@ -612,7 +738,7 @@ qaoa_status expectation_static_impl(const HostGraph& hg, const void* dev_state, 
         a.init_amp = std::pow(2.0, -0.5 * n);
         a.state = const_cast<void*>(dev_state);
         a.partials = scratch;
-        auto kfn = tile_kernel<real, Q, R>;
+        auto kfn = tile_kernel<real, Q, R, false>;
         const size_t smem = (size_t)(1u << Q) * sizeof(C2);
         CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         kfn<<<(unsigned)count, 1u << (Q - R), smem, stream>>>(a);
@@ -638,12 +764,14 @@ qaoa_status grad_workspace(qaoa_state s, int p) {
     cudaFree(s->d_gmix);
     cudaFree(s->d_gacc);
     cudaFree(s->d_gpart);
-    s->d_gtab = s->d_gmix = nullptr;
+    cudaFree(s->d_gwfix);
+    s->d_gtab = s->d_gmix = s->d_gwfix = nullptr;
     s->d_gacc = nullptr;
     s->d_gpart = nullptr;
     s->grad_levels = 0;
     const size_t eb = elem_bytes(s->prec);
-    cudaError_t e = cudaMalloc(&s->d_gtab, (size_t)p * (s->g.m + 1) * eb);
+    cudaError_t e = cudaMalloc(&s->d_gtab, (size_t)p * table_entries(s->g) * eb);
+    if (e == cudaSuccess && s->g.weighted) e = cudaMalloc(&s->d_gwfix, wfix_bytes(s->g, s->prec, p));
     if (e == cudaSuccess) e = cudaMalloc(&s->d_gmix, (size_t)3 * p * eb);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_gacc, (size_t)2 * p * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&s->d_gpart, (size_t)2 * s->ntiles * sizeof(double2));
@@ -684,18 +812,19 @@ qaoa_status gradient_async(qaoa_state s, int p, const double* gamma, const doubl
         CoeffArgs ca;
         std::memset(&ca, 0, sizeof(ca));
         ca.levels = levels;
-        ca.E1 = s->g.m + 1;
+        ca.E1 = table_entries(s->g);
         ca.n = s->n;
         ca.fold_factors = 0;
         ca.gre = 1;
         ca.gim = 0;
+        fill_coeff_weights(ca, s->g, s->prec, s->d_gwfix, 2 + k0);
         for (int k = 0; k < levels; ++k) {
             ca.gamma[k] = gamma[k0 + k];
             ca.beta[k] = beta[k0 + k];
         }
-        ca.phase = reinterpret_cast<C2*>(s->d_gtab) + (size_t)k0 * (s->g.m + 1);
+        ca.phase = reinterpret_cast<C2*>(s->d_gtab) + (size_t)k0 * table_entries(s->g);
         ca.mix = reinterpret_cast<C2*>(s->d_gmix) + (size_t)3 * k0;
-        dim3 grid((unsigned)std::max(1, (ca.E1 + 255) / 256), (unsigned)levels);
+        dim3 grid((unsigned)std::max(1, (std::max(ca.E1, ca.m) + 255) / 256), (unsigned)levels);
         coeff_kernel<real><<<grid, 256, 0, s->stream>>>(ca);
         CUDA_TRY(cudaGetLastError());
         s->launches++;
@@ -707,12 +836,13 @@ qaoa_status gradient_async(qaoa_state s, int p, const double* gamma, const doubl
         std::memset(&j, 0, sizeof(j));
         j.n = s->n;
         j.levels = p;
-        j.E1 = s->g.m + 1;
+        j.E1 = table_entries(s->g);
         for (int v = 0; v < kMaxN; ++v) j.gmask[v] = v < s->n ? s->g.upper[v] : 0;
         j.state = s->buf;
         j.phase = s->d_gtab;
         j.mix = s->d_gmix;
         j.acc = s->d_gacc;
+        set_small_weights(j, s->g, s->prec, s->d_gwfix);
         auto kfn = small_grad_kernel<real>;
         qaoa_status ast = ensure_attributes<real>();
         if (ast != QAOA_OK) return ast;
@@ -726,7 +856,7 @@ qaoa_status gradient_async(qaoa_state s, int p, const double* gamma, const doubl
         } catch (const std::exception& ex) {
             return fail(QAOA_ERR_UNSUPPORTED, ex.what());
         }
-        auto kfn = grad_kernel<real, Q, R>;
+        auto kfn = s->g.weighted ? grad_kernel<real, Q, R, true> : grad_kernel<real, Q, R, false>;
         const size_t smem = (size_t)(1u << Q) * sizeof(C2);
         qaoa_status ast = ensure_attributes<real>();
         if (ast != QAOA_OK) return ast;
@@ -739,6 +869,8 @@ qaoa_status gradient_async(qaoa_state s, int p, const double* gamma, const doubl
             a.phase = s->d_gtab;
             a.mix = s->d_gmix;
             a.partials = s->d_gpart;
+            if (s->g.weighted && !fill_weighted(a, s->g, s->prec, s->d_gwfix, a.ops, a.nops))
+                return fail(QAOA_ERR_UNSUPPORTED, "too many phase levels in one adjoint pass");
             int lev[2] = {-1, -1};
             for (const Op& op : ps.ops)
                 if (op.kind == OP_RXD || op.kind == OP_GRADG) lev[(op.arg >> 16) & 1] = op.arg & 0xffff;
@@ -814,7 +946,8 @@ qaoa_status qaoa_state_init(const qaoa_graph* g, qaoa_prec prec, void* dev_buf, 
         s->ntiles = 1ull << (hg.n - s->tc.Q);
     }
     const size_t eb = elem_bytes(prec);
-    cudaError_t e = cudaMalloc(&s->d_phase, (size_t)kLayerChunk * (hg.m + 1) * eb);
+    cudaError_t e = cudaMalloc(&s->d_phase, (size_t)kLayerChunk * table_entries(hg) * eb);
+    if (e == cudaSuccess && hg.weighted) e = cudaMalloc(&s->d_wfix, wfix_bytes(hg, prec, kLayerChunk));
     if (e == cudaSuccess) e = cudaMalloc(&s->d_mix, (size_t)3 * kLayerChunk * eb);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_partials, (size_t)s->ntiles * sizeof(double2));
     if (e == cudaSuccess) e = cudaMalloc(&s->d_result, sizeof(double2));
@@ -826,6 +959,13 @@ qaoa_status qaoa_state_init(const qaoa_graph* g, qaoa_prec prec, void* dev_buf, 
     }
     s->lazy = true;
     s->exp_valid = false;
+    if (hg.weighted) {  // endpoint and value rows, read by <C> of a state with no level applied
+        st = prec == QAOA_C64 ? write_weight_rows<float>(s) : write_weight_rows<double>(s);
+        if (st != QAOA_OK) {
+            release(s);
+            return st;
+        }
+    }
     *out = s;
     return QAOA_OK;
 }
@@ -908,8 +1048,28 @@ qaoa_status qaoa_cut_table(const qaoa_graph* g, uint16_t* host_out) {
     HostGraph hg;
     qaoa_status st = encode_graph(g, hg);
     if (st != QAOA_OK) return st;
+    if (hg.weighted) return fail(QAOA_ERR_INVALID, "weighted graph: use qaoa_cut_table_f64");
     if (hg.n > 30) return fail(QAOA_ERR_INVALID, "cut table limited to n <= 30");
     return cut_table_impl<float>(hg, QAOA_C64, -1, 0, host_out);
+}
+
+qaoa_status qaoa_cut_table_f64(const qaoa_graph* g, qaoa_prec prec, int32_t group, int32_t layout, double* host_out) {
+    if (!host_out) return fail(QAOA_ERR_INVALID, "host_out is NULL");
+    if (prec != QAOA_C64 && prec != QAOA_C128) return fail(QAOA_ERR_INVALID, "unknown precision");
+    HostGraph hg;
+    qaoa_status st = encode_graph(g, hg);
+    if (st != QAOA_OK) return st;
+    if (hg.n > 28) return fail(QAOA_ERR_INVALID, "cut table limited to n <= 28");
+    if (!hg.weighted) {  // the cut counts, widened
+        std::vector<uint16_t> c((size_t)1 << hg.n);
+        st = prec == QAOA_C64 ? cut_table_impl<float>(hg, prec, group, layout, c.data())
+                              : cut_table_impl<double>(hg, prec, group, layout, c.data());
+        if (st == QAOA_OK)
+            for (size_t z = 0; z < c.size(); ++z) host_out[z] = c[z];
+        return st;
+    }
+    return prec == QAOA_C64 ? cut_table_impl<float>(hg, prec, group, layout, nullptr, host_out)
+                            : cut_table_impl<double>(hg, prec, group, layout, nullptr, host_out);
 }
 
 qaoa_status qaoa_cut_table_geometry(const qaoa_graph* g, qaoa_prec prec, int32_t group, int32_t layout,
@@ -920,6 +1080,7 @@ qaoa_status qaoa_cut_table_geometry(const qaoa_graph* g, qaoa_prec prec, int32_t
     HostGraph hg;
     qaoa_status st = encode_graph(g, hg);
     if (st != QAOA_OK) return st;
+    if (hg.weighted) return fail(QAOA_ERR_INVALID, "weighted graph: use qaoa_cut_table_f64");
     if (hg.n > 30) return fail(QAOA_ERR_INVALID, "cut table limited to n <= 30");
     return prec == QAOA_C64 ? cut_table_impl<float>(hg, prec, group, layout, host_out)
                             : cut_table_impl<double>(hg, prec, group, layout, host_out);

@@ -23,6 +23,16 @@
 // 2^R-entry table of the register bits' internal edges.  K and e_u cost one popcount per
 // vertex per CTA, base and s_j about Q + R popcounts per thread, and each amplitude two
 // integer adds.
+//
+// Edge-weighted graphs (Algorithm 2: C(z) = sum_e w_e (z_u xor z_v) with real w_e) use the same
+// split for any function F(z) = sum_e f_e (z_u xor z_v) with integer f_e, in wrapping B-bit
+// arithmetic (B = 32 for complex64, 64 for complex128), so every partial sum is exact modulo
+// 2^B.  Two kinds of f are used.  For the cost phase of level k, f_e = gamma_k w_e / (2 pi) in
+// units of 2^-B turns, reduced modulo one turn: since z_u xor z_v is 0 or 1, the sum is
+// gamma_k C(z) / (2 pi) modulo one turn up to the rounding of the m per-edge angles, and each
+// amplitude takes one sincospi of it.  For <C> and the adjoint's C psi, f_e = w_e 2^S, with S
+// chosen so that sum |w_e| 2^S < 2^(B-2).  Register-bit pairs enter through R(R-1)/2 pair terms
+// P_jk (z_j z_k coefficients) instead of the 2^R-entry table.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -64,6 +74,16 @@ struct TileArgs {
     uint32_t locAdj[Q];     // all tile-internal neighbours of local bit u
     uint64_t outAdj[Q];     // neighbours of local bit u outside the tile (global positions)
     uint8_t crtab[3][32];   // C_R(x) per register layout
+    // edge-weighted graphs (pass kernels instantiated with kW)
+    const void* wfix;              // rows of m fixed-point words: [0] endpoints u | v << 8,
+                                   // [1] value weights, [2 + k] angles of level k
+    double vscale;                 // value = (signed) sum * vscale
+    int32_t m, wn, wnslots;        // edges; tile-internal edges in wloc; local slots in use
+    uint32_t wloc[kMaxLocEdges];   // tile-internal edge: e | a << 10 | b << 14 (local bits a < b)
+    int16_t wrow[kWSlots];         // wfix row of local slot s (slot 0: the value row)
+    int8_t wslot[kLayerChunk];     // local slot holding level k's angles
+    uint8_t gl2loc[kMaxN];         // local bit of index bit v, 0xff outside the tile
+    double* cutout_w;              // [2^n] weighted cut values (OP_CUTVAL)
     Op ops[kMaxOps];
     void* state;
     void* state2;        // adjoint sweep: lambda
@@ -83,10 +103,22 @@ struct SmallJob {
     const void* mix;
     double2* partials;  // one entry
     uint16_t* cutout;
+    // edge-weighted graphs: wfix rows as in TileArgs (levels at rows 2 + k), NULL for unit weights
+    const void* wfix;
+    int32_t m;
+    double vscale;
+    double* cutout_w;
 };
 
 struct CoeffArgs {
     int32_t levels, E1;
+    // edge-weighted graphs: also writes the fixed-point rows of wfix (endpoints and value weights
+    // always, level k's angles at row wrow0 + k); E1 is then 1 (the table holds only the factor)
+    int32_t weighted, m, wrow0;
+    double vmul;  // 2^S of the value weights
+    void* wfix;
+    double w[kMaxEdges];
+    uint16_t uv[kMaxEdges];  // u | v << 8
     int32_t n;                  // qubits: each level's mixer carries its factor f to the power n
     int32_t fold_factors;       // 1: multiply the phase tables by the mixers' factors (tile passes)
     int32_t fold[kLayerChunk];  // 1: the tile passes apply level k as -i X RX(2 beta - pi)
@@ -153,6 +185,93 @@ __device__ __forceinline__ int cut_count_full(const uint64_t* gm, int n, uint64_
     return c;
 }
 
+// ---------------------------------------------------------------------------------- weighted sums
+
+// Fixed-point word of the weighted sums: 32 bits for complex64, 64 bits for complex128.
+template <typename real>
+struct WAcc;
+template <>
+struct WAcc<float> {
+    using type = uint32_t;
+    using stype = int32_t;
+};
+template <>
+struct WAcc<double> {
+    using type = uint64_t;
+    using stype = int64_t;
+};
+
+// exp(-i 2 pi th / 2^B) times g, with th read as a signed fraction of a turn (|angle| <= pi).
+__device__ __forceinline__ float2 phase_of(uint32_t th, float2 g) {
+    float sn, cs;
+    sincospif((float)(int32_t)th * 0x1p-31f, &sn, &cs);
+    return make_float2(g.x * cs + g.y * sn, g.y * cs - g.x * sn);
+}
+__device__ __forceinline__ double2 phase_of(uint64_t th, double2 g) {
+    double sn, cs;
+    sincospi((double)(int64_t)th * 0x1p-63, &sn, &cs);
+    return make_double2(g.x * cs + g.y * sn, g.y * cs - g.x * sn);
+}
+
+template <typename WA>
+__device__ __forceinline__ WA warp_sum_wrap(WA v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ void smem_add(uint32_t* p, uint32_t v) { atomicAdd(p, v); }
+__device__ __forceinline__ void smem_add(uint64_t* p, uint64_t v) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
+}
+
+// F_s(z) = sum_e W[row][e] (z_u xor z_v) of one z over every edge (small states).
+template <typename WA>
+__device__ __forceinline__ WA wsum_full(const WA* __restrict__ W, int m, int row, uint64_t z) {
+    WA acc = 0;
+    const WA* f = W + (size_t)row * m;
+    for (int e = 0; e < m; ++e) {
+        const uint32_t uv = (uint32_t)__ldg(W + e);
+        if (((z >> (uv & 255u)) ^ (z >> ((uv >> 8) & 255u))) & 1ull) acc += __ldg(f + e);
+    }
+    return acc;
+}
+
+// Per-CTA terms of the weighted split for every local slot s of the pass:
+//   sK[s] = F_s(o|0),   sE[s][u] = sum over edges (u, v), v outside the tile, of f_e (1 - 2 o_v).
+// Wrapping sums, so the result does not depend on the order of the atomics.
+template <typename WA, int Q>
+__device__ void weighted_cta_setup(const TileArgs<Q>& a, uint64_t zb, WA* sK, WA (*sE)[Q], uint32_t tid,
+                                   uint32_t nthreads) {
+    for (uint32_t i = tid; i < (uint32_t)(kWSlots * (Q + 1)); i += nthreads) {
+        if (i < (uint32_t)kWSlots) sK[i] = 0;
+        else sE[(i - kWSlots) / Q][(i - kWSlots) % Q] = 0;
+    }
+    __syncthreads();
+    const WA* W = reinterpret_cast<const WA*>(a.wfix);
+    WA kacc[kWSlots] = {};
+    for (int e = (int)tid; e < a.m; e += (int)nthreads) {
+        const uint32_t uv = (uint32_t)__ldg(W + e);
+        const int u = uv & 255u, v = (uv >> 8) & 255u;
+        const uint32_t bu = (uint32_t)(zb >> u) & 1u, bv = (uint32_t)(zb >> v) & 1u;
+        const int lu = a.gl2loc[u], lv = a.gl2loc[v];
+#pragma unroll
+        for (int sl = 0; sl < kWSlots; ++sl) {
+            if (sl >= a.wnslots) break;
+            const WA f = __ldg(W + (size_t)a.wrow[sl] * a.m + e);
+            if (bu ^ bv) kacc[sl] += f;
+            if (lu != 0xff && lv == 0xff) smem_add(&sE[sl][lu], bv ? (WA)(0 - f) : f);
+            if (lv != 0xff && lu == 0xff) smem_add(&sE[sl][lv], bu ? (WA)(0 - f) : f);
+        }
+    }
+#pragma unroll
+    for (int sl = 0; sl < kWSlots; ++sl) {
+        const WA r = warp_sum_wrap(kacc[sl]);
+        if ((tid & 31u) == 0 && sl < a.wnslots) smem_add(&sK[sl], r);
+    }
+    __syncthreads();
+}
+
 // ---------------------------------------------------------------------------------- tile pass
 
 template <typename real, int Q, int R>
@@ -217,7 +336,91 @@ struct Tile {
         int K;
         const TileArgs<Q>* a;
         int* sE;
+        const void* wK;  // weighted: per-slot F_s(o|0) (shared memory)
+        const void* wE;  // weighted: per-slot e_u terms, [slot][Q] (shared memory)
     };
+
+    using WA = typename WAcc<real>::type;
+    using SWA = typename WAcc<real>::stype;
+    static constexpr int NP = R * (R - 1) / 2;
+
+    template <int N>
+    static __device__ __forceinline__ void add_at(WA (&s)[N], int idx, WA v) {
+#pragma unroll
+        for (int j = 0; j < N; ++j)
+            if (j == idx) s[j] += v;
+    }
+    static __device__ __forceinline__ void add_pair(WA (&P)[NP], int ja, int jb, WA v) {
+        int q = 0;
+#pragma unroll
+        for (int j = 0; j < R; ++j)
+#pragma unroll
+            for (int k = j + 1; k < R; ++k) {
+                if (j == ja && k == jb) P[q] += v;
+                ++q;
+            }
+    }
+
+    // Weighted split of local slot ls in layout L: F = base(tau) + sum_{j in x} s_j
+    // + sum_{j < k in x} P_jk.  The tile-internal edges are classified by where their ends sit:
+    // two thread bits (into base), a register and a thread bit (a slope), two register bits (two
+    // slopes and a pair term).
+    template <int L>
+    static __device__ __forceinline__ WA wsetup(const Ctx& c, uint32_t tid, int ls, WA (&s)[R], WA (&P)[NP]) {
+        const TileArgs<Q>& a = *c.a;
+        const uint32_t tau = tbits(L, tid);
+        const WA* sE = reinterpret_cast<const WA*>(c.wE) + ls * Q;
+        WA base = reinterpret_cast<const WA*>(c.wK)[ls];
+#pragma unroll
+        for (int u = 0; u < Q; ++u)
+            if ((tau >> u) & 1u) base += sE[u];
+#pragma unroll
+        for (int j = 0; j < R; ++j) s[j] = sE[rlo(L) + j];
+#pragma unroll
+        for (int q = 0; q < NP; ++q) P[q] = 0;
+        const WA* __restrict__ W = reinterpret_cast<const WA*>(a.wfix) + (size_t)a.wrow[ls] * a.m;
+        for (int i = 0; i < a.wn; ++i) {
+            const uint32_t ent = a.wloc[i];
+            const WA f = __ldg(W + (ent & 1023u));
+            const int ua = (ent >> 10) & 15, ub = (ent >> 14) & 15;
+            const int ja = ua - rlo(L), jb = ub - rlo(L);
+            const bool ra = (unsigned)ja < (unsigned)R, rb = (unsigned)jb < (unsigned)R;
+            const uint32_t ta = (tau >> ua) & 1u, tb = (tau >> ub) & 1u;
+            if (ra && rb) {
+                add_at(s, ja, f);
+                add_at(s, jb, f);
+                add_pair(P, ja, jb, (WA)(0 - 2 * f));
+            } else if (ra) {
+                if (tb) base += f;
+                add_at(s, ja, tb ? (WA)(0 - f) : f);
+            } else if (rb) {
+                if (ta) base += f;
+                add_at(s, jb, ta ? (WA)(0 - f) : f);
+            } else if (ta ^ tb) {
+                base += f;
+            }
+        }
+        return base;
+    }
+
+    template <int x>
+    static __device__ __forceinline__ WA wat(WA base, const WA (&s)[R], const WA (&P)[NP]) {
+        WA v = base;
+#pragma unroll
+        for (int j = 0; j < R; ++j)
+            if ((x >> j) & 1) v += s[j];
+        int q = 0;
+#pragma unroll
+        for (int j = 0; j < R; ++j)
+#pragma unroll
+            for (int k = j + 1; k < R; ++k) {
+                if (((x >> j) & 1) && ((x >> k) & 1)) v += P[q];
+                ++q;
+            }
+        return v;
+    }
+
+    static __device__ __forceinline__ real wval(WA v, double scale) { return (real)((double)(SWA)v * scale); }
 
     // Element offset of the thread's register-index-0 amplitude in layout L (thread bits only).
     template <int L>
@@ -350,9 +553,23 @@ struct Tile {
         return cidx;
     }
 
-    template <int L>
+    template <int L, bool kW = false>
     static __device__ __forceinline__ void phase(C2 (&v)[NE], const Ctx& c, uint32_t tid, int level) {
         const TileArgs<Q>& a = *c.a;
+        if constexpr (kW) {  // the table holds one entry per level: the folded factor
+            WA s[R], P[NP];
+            const WA base = wsetup<L>(c, tid, a.wslot[level], s, P);
+            const C2 g = __ldg(reinterpret_cast<const C2*>(a.phase) + level);
+            for_x<NE>([&](auto X) {
+                constexpr int x = decltype(X)::value;
+                const C2 f = phase_of(wat<x>(base, s, P), g);
+                if constexpr (kSwapOdd && odd_parity(x))
+                    v[x] = make_c2(v[x].x * f.x + v[x].y * f.y, v[x].y * f.x - v[x].x * f.y);
+                else
+                    v[x] = cmul(v[x], f);
+            });
+            return;
+        }
         int s[R];
         const int base = cut_setup<L>(c, tid, s);
         const C2* __restrict__ T = reinterpret_cast<const C2*>(a.phase) + (size_t)level * a.E1;
@@ -371,10 +588,24 @@ struct Tile {
         });
     }
 
-    template <int L>
+    template <int L, bool kW = false>
     static __device__ __forceinline__ void expect(const C2 (&v)[NE], const Ctx& c, uint32_t tid,
                                                   double& accC, double& accN) {
         const TileArgs<Q>& a = *c.a;
+        if constexpr (kW) {
+            WA s[R], P[NP];
+            const WA base = wsetup<L>(c, tid, 0, s, P);
+            real sc = 0, sn = 0;
+            for_x<NE>([&](auto X) {
+                constexpr int x = decltype(X)::value;
+                const real p = v[x].x * v[x].x + v[x].y * v[x].y;
+                sn += p;
+                sc += p * wval(wat<x>(base, s, P), a.vscale);
+            });
+            accC += (double)sc;
+            accN += (double)sn;
+            return;
+        }
         int s[R];
         const int base = cut_setup<L>(c, tid, s);
         real sc = 0, sn = 0;
@@ -392,9 +623,23 @@ struct Tile {
         accN += (double)sn;
     }
 
-    template <int L>
+    template <int L, bool kW = false>
     static __device__ __forceinline__ void cutval(const Ctx& c, uint32_t tid) {
         const TileArgs<Q>& a = *c.a;
+        if constexpr (kW) {
+            WA s[R], P[NP];
+            const WA base = wsetup<L>(c, tid, 0, s, P);
+            double* __restrict__ g = a.cutout_w + c.zb + toff<L>(a, tid);
+            for_x<NE>([&](auto X) {
+                constexpr int x = decltype(X)::value;
+                int64_t o = 0;
+#pragma unroll
+                for (int j = 0; j < R; ++j)
+                    if ((x >> j) & 1) o += a.rstride[L][j];
+                g[o] = (double)(SWA)wat<x>(base, s, P) * a.vscale;
+            });
+            return;
+        }
         int s[R];
         const int base = cut_setup<L>(c, tid, s);
         uint16_t* __restrict__ g = a.cutout + c.zb + toff<L>(a, tid);
@@ -415,9 +660,19 @@ struct Tile {
     // ------------------------------------------------------------ adjoint sweep (psi v, lambda w)
 
     // lambda <- C psi
-    template <int L>
+    template <int L, bool kW = false>
     static __device__ __forceinline__ void lambda_init(const C2 (&v)[NE], C2 (&w)[NE], const Ctx& c, uint32_t tid) {
         const TileArgs<Q>& a = *c.a;
+        if constexpr (kW) {
+            WA s[R], P[NP];
+            const WA base = wsetup<L>(c, tid, 0, s, P);
+            for_x<NE>([&](auto X) {
+                constexpr int x = decltype(X)::value;
+                const real cc = wval(wat<x>(base, s, P), a.vscale);
+                w[x] = make_c2(cc * v[x].x, cc * v[x].y);
+            });
+            return;
+        }
         int s[R];
         const int base = cut_setup<L>(c, tid, s);
         for_x<NE>([&](auto X) {
@@ -470,9 +725,20 @@ struct Tile {
     }
 
     // sum_z C(z) Im(conj(lambda_z) psi_z) over the thread's amplitudes
-    template <int L>
+    template <int L, bool kW = false>
     static __device__ __forceinline__ real grad_gamma(const C2 (&v)[NE], const C2 (&w)[NE], const Ctx& c, uint32_t tid) {
         const TileArgs<Q>& a = *c.a;
+        if constexpr (kW) {
+            WA s[R], P[NP];
+            const WA base = wsetup<L>(c, tid, 0, s, P);
+            real acc = 0;
+            for_x<NE>([&](auto X) {
+                constexpr int x = decltype(X)::value;
+                acc += wval(wat<x>(base, s, P), a.vscale) *
+                       (re_of<x>(w[x]) * im_of<x>(v[x]) - im_of<x>(w[x]) * re_of<x>(v[x]));
+            });
+            return acc;
+        }
         int s[R];
         const int base = cut_setup<L>(c, tid, s);
         real acc = 0;
@@ -488,9 +754,23 @@ struct Tile {
     }
 
     // exp(+i gamma C(z)) on both states (conjugate phase table entries)
-    template <int L>
+    template <int L, bool kW = false>
     static __device__ __forceinline__ void phase_dual(C2 (&v)[NE], C2 (&w)[NE], const Ctx& c, uint32_t tid, int level) {
         const TileArgs<Q>& a = *c.a;
+        if constexpr (kW) {
+            WA s[R], P[NP];
+            const WA base = wsetup<L>(c, tid, a.wslot[level], s, P);
+            const C2 g = __ldg(reinterpret_cast<const C2*>(a.phase) + level);
+            for_x<NE>([&](auto X) {
+                constexpr int x = decltype(X)::value;
+                const C2 f = phase_of(wat<x>(base, s, P), g);
+                const real pr = re_of<x>(v[x]), pi = im_of<x>(v[x]);
+                v[x] = mk<x>(pr * f.x + pi * f.y, pi * f.x - pr * f.y);
+                const real lr = re_of<x>(w[x]), li = im_of<x>(w[x]);
+                w[x] = mk<x>(lr * f.x + li * f.y, li * f.x - lr * f.y);
+            });
+            return;
+        }
         int s[R];
         const int base = cut_setup<L>(c, tid, s);
         const C2* __restrict__ T = reinterpret_cast<const C2*>(a.phase) + (size_t)level * a.E1;
@@ -557,14 +837,17 @@ struct Tile {
 #define QAOA_TILE_MIN_BLOCKS 2  // resident CTAs per SM the register budget is sized for
 #endif
 
-template <typename real, int Q, int R>
+template <typename real, int Q, int R, bool kW>
 __global__ void __launch_bounds__(1 << (Q - R), QAOA_TILE_MIN_BLOCKS) tile_kernel(const __grid_constant__ TileArgs<Q> a) {
     using T = Tile<real, Q, R>;
     using C2 = typename T::C2;
+    using WA = typename T::WA;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int sE[Q];
     __shared__ int sK;
     __shared__ double sred[2][T::NT / 32];
+    __shared__ WA sKw[kW ? kWSlots : 1];
+    __shared__ WA sEw[kW ? kWSlots : 1][Q];
 
     unsigned char* tile = smem_raw;
     const uint32_t tid = threadIdx.x;
@@ -572,7 +855,9 @@ __global__ void __launch_bounds__(1 << (Q - R), QAOA_TILE_MIN_BLOCKS) tile_kerne
     uint64_t zb = 0;  // outer index bits of tile t: runs of tile-id bits deposited in place
     for (int r = 0; r < a.nruns; ++r) zb |= ((t >> a.run_src[r]) & ((1ull << a.run_len[r]) - 1ull)) << a.run_dst[r];
 
-    if (a.need_cut) {
+    if constexpr (kW) {
+        if (a.need_cut) weighted_cta_setup<WA, Q>(a, zb, sKw, sEw, tid, T::NT);
+    } else if (a.need_cut) {
         if (tid < 32) {
             int acc = 0;
             for (int v = (int)tid; v < a.n; v += 32) {
@@ -588,9 +873,11 @@ __global__ void __launch_bounds__(1 << (Q - R), QAOA_TILE_MIN_BLOCKS) tile_kerne
 
     typename T::Ctx c;
     c.zb = zb;
-    c.K = a.need_cut ? sK : 0;
+    c.K = (!kW && a.need_cut) ? sK : 0;
     c.a = &a;
     c.sE = sE;
+    c.wK = sKw;
+    c.wE = sEw;
 
     C2 v[T::NE];
     int L = 0;
@@ -630,20 +917,20 @@ __global__ void __launch_bounds__(1 << (Q - R), QAOA_TILE_MIN_BLOCKS) tile_kerne
                 T::rx(v, op.mask, reinterpret_cast<const C2*>(a.mix)[3 * op.arg + 1].x);
                 break;
             case OP_PHASE:
-                if (L == 0) T::template phase<0>(v, c, tid, op.arg);
-                else if (L == 1) T::template phase<1>(v, c, tid, op.arg);
-                else T::template phase<2>(v, c, tid, op.arg);
+                if (L == 0) T::template phase<0, kW>(v, c, tid, op.arg);
+                else if (L == 1) T::template phase<1, kW>(v, c, tid, op.arg);
+                else T::template phase<2, kW>(v, c, tid, op.arg);
                 break;
             case OP_EXPECT:
                 did_expect = true;
-                if (L == 0) T::template expect<0>(v, c, tid, accC, accN);
-                else if (L == 1) T::template expect<1>(v, c, tid, accC, accN);
-                else T::template expect<2>(v, c, tid, accC, accN);
+                if (L == 0) T::template expect<0, kW>(v, c, tid, accC, accN);
+                else if (L == 1) T::template expect<1, kW>(v, c, tid, accC, accN);
+                else T::template expect<2, kW>(v, c, tid, accC, accN);
                 break;
             case OP_CUTVAL:
-                if (L == 0) T::template cutval<0>(c, tid);
-                else if (L == 1) T::template cutval<1>(c, tid);
-                else T::template cutval<2>(c, tid);
+                if (L == 0) T::template cutval<0, kW>(c, tid);
+                else if (L == 1) T::template cutval<1, kW>(c, tid);
+                else T::template cutval<2, kW>(c, tid);
                 break;
             case OP_STORE:
                 if (L == 0) T::template store<0>(v, c, tid);
@@ -679,21 +966,27 @@ __global__ void __launch_bounds__(1 << (Q - R), QAOA_TILE_MIN_BLOCKS) tile_kerne
 // One pass of the adjoint sweep over psi (a.state) and lambda (a.state2), same tiling as
 // tile_kernel.  Per CTA it writes, for accumulator slots 0 and 1, (sum of RXD pair terms,
 // sum of GRADG terms) to partials[2 t + slot].
-template <typename real, int Q, int R>
+template <typename real, int Q, int R, bool kW>
 __global__ void __launch_bounds__(1 << (Q - R), 1) grad_kernel(const __grid_constant__ TileArgs<Q> a) {
     using T = Tile<real, Q, R>;
     using C2 = typename T::C2;
+    using WA = typename T::WA;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int sE[Q];
     __shared__ int sK;
     __shared__ double sred[4][T::NT / 32];
+    __shared__ WA sKw[kW ? kWSlots : 1];
+    __shared__ WA sEw[kW ? kWSlots : 1][Q];
 
     unsigned char* tile = smem_raw;
     const uint32_t tid = threadIdx.x;
     const uint64_t t = blockIdx.x;
     uint64_t zb = 0;
     for (int r = 0; r < a.nruns; ++r) zb |= ((t >> a.run_src[r]) & ((1ull << a.run_len[r]) - 1ull)) << a.run_dst[r];
-    if (tid < 32) {
+    if constexpr (kW) {
+        weighted_cta_setup<WA, Q>(a, zb, sKw, sEw, tid, T::NT);
+        if (tid == 0) sK = 0;
+    } else if (tid < 32) {
         int acc = 0;
         for (int v = (int)tid; v < a.n; v += 32) {
             const uint64_t bI = 0ull - ((zb >> v) & 1ull);
@@ -706,9 +999,11 @@ __global__ void __launch_bounds__(1 << (Q - R), 1) grad_kernel(const __grid_cons
     __syncthreads();
     typename T::Ctx c;
     c.zb = zb;
-    c.K = sK;
+    c.K = kW ? 0 : sK;
     c.a = &a;
     c.sE = sE;
+    c.wK = sKw;
+    c.wE = sEw;
 
     C2 v[T::NE], w[T::NE];
     int L = 0;
@@ -731,7 +1026,9 @@ __global__ void __launch_bounds__(1 << (Q - R), 1) grad_kernel(const __grid_cons
                 if (!lam_init) QAOA_BY_LAYOUT(load_from, w, c, tid, a.state2);
                 break;
             case OP_LAMBDA:
-                QAOA_BY_LAYOUT(lambda_init, v, w, c, tid);
+                if (L == 0) T::template lambda_init<0, kW>(v, w, c, tid);
+                else if (L == 1) T::template lambda_init<1, kW>(v, w, c, tid);
+                else T::template lambda_init<2, kW>(v, w, c, tid);
                 break;
             case OP_XCHG: {
                 const int Lold = L;
@@ -757,14 +1054,16 @@ __global__ void __launch_bounds__(1 << (Q - R), 1) grad_kernel(const __grid_cons
             case OP_GRADG: {
                 const int slot = op.arg >> 16;
                 real g = 0;
-                if (L == 0) g = T::template grad_gamma<0>(v, w, c, tid);
-                else if (L == 1) g = T::template grad_gamma<1>(v, w, c, tid);
-                else g = T::template grad_gamma<2>(v, w, c, tid);
+                if (L == 0) g = T::template grad_gamma<0, kW>(v, w, c, tid);
+                else if (L == 1) g = T::template grad_gamma<1, kW>(v, w, c, tid);
+                else g = T::template grad_gamma<2, kW>(v, w, c, tid);
                 acc[2 * slot + 1] += (double)g;
                 break;
             }
             case OP_PHASED:
-                QAOA_BY_LAYOUT(phase_dual, v, w, c, tid, op.arg);
+                if (L == 0) T::template phase_dual<0, kW>(v, w, c, tid, op.arg);
+                else if (L == 1) T::template phase_dual<1, kW>(v, w, c, tid, op.arg);
+                else T::template phase_dual<2, kW>(v, w, c, tid, op.arg);
                 break;
             case OP_STORE:
                 L = op.layout;
@@ -832,6 +1131,9 @@ struct SmallGradJob {
     const void* phase;   // plain tables [level][E1]
     const void* mix;     // [3 * level]: (cos b, sin b)
     double* acc;         // [2 * levels]: pair sums, gamma sums
+    const void* wfix;    // edge-weighted graphs: rows as in TileArgs (level k at row 2 + k), else NULL
+    int32_t m;
+    double vscale;
 };
 
 template <typename real>
@@ -844,13 +1146,20 @@ __global__ void __launch_bounds__(kSmallThreadsGrad) small_grad_kernel(const __g
     C2* lm = ps + dim;
     __shared__ uint64_t gm[kMaxN];
     __shared__ double sred[kSmallThreadsGrad / 32];
+    using WA = typename WAcc<real>::type;
+    using SWA = typename WAcc<real>::stype;
+    const WA* W = reinterpret_cast<const WA*>(j.wfix);
+    // C(z): the cut count, or the weighted sum of the value row
+    auto cval = [&](uint32_t z) -> double {
+        return W ? (double)(SWA)wsum_full(W, j.m, 1, z) * j.vscale : (double)cut_count_full(gm, n, z);
+    };
     const uint32_t tid = threadIdx.x;
     if (tid < (uint32_t)n) gm[tid] = j.gmask[tid];
     __syncthreads();
     const C2* src = reinterpret_cast<const C2*>(j.state);
     for (uint32_t z = tid; z < dim; z += kSmallThreadsGrad) {
         const C2 q = src[z];
-        const real cc = (real)cut_count_full(gm, n, z);
+        const real cc = (real)cval(z);
         ps[z] = q;
         lm[z] = make_c2(cc * q.x, cc * q.y);
     }
@@ -890,14 +1199,14 @@ __global__ void __launch_bounds__(kSmallThreadsGrad) small_grad_kernel(const __g
         double pg = 0.0;
         for (uint32_t z = tid; z < dim; z += kSmallThreadsGrad) {
             const C2 p = ps[z], l = lm[z];
-            pg += (double)cut_count_full(gm, n, z) * (double)(l.x * p.y - l.y * p.x);
+            pg += cval(z) * (double)(l.x * p.y - l.y * p.x);
         }
         const double sg = block_sum(pg);
         if (tid == 0) j.acc[j.levels + k] = sg;
         if (k > 0) {
             const C2* Tk = reinterpret_cast<const C2*>(j.phase) + (size_t)k * j.E1;
             for (uint32_t z = tid; z < dim; z += kSmallThreadsGrad) {
-                const C2 f = Tk[cut_count_full(gm, n, z)];
+                const C2 f = W ? phase_of(wsum_full(W, j.m, 2 + k, z), Tk[0]) : Tk[cut_count_full(gm, n, z)];
                 const C2 fc = make_c2(f.x, -f.y);
                 ps[z] = cmul(ps[z], fc);
                 lm[z] = cmul(lm[z], fc);
@@ -917,6 +1226,9 @@ __device__ __forceinline__ void small_body(const SmallJob& j) {
     C2* st = reinterpret_cast<C2*>(smem_raw);
     __shared__ uint64_t gm[kMaxN];
     __shared__ double sred[2][kSmallThreads / 32];
+    using WA = typename WAcc<real>::type;
+    using SWA = typename WAcc<real>::stype;
+    const WA* W = reinterpret_cast<const WA*>(j.wfix);  // NULL: unit weights
     const int n = j.n;
     const uint32_t dim = 1u << n;
     const uint32_t tid = threadIdx.x;
@@ -929,7 +1241,10 @@ __device__ __forceinline__ void small_body(const SmallJob& j) {
     const C2* mix = reinterpret_cast<const C2*>(j.mix);
     for (int k = 0; k < j.levels; ++k) {
         const C2* T = reinterpret_cast<const C2*>(j.phase) + (size_t)k * j.E1;
-        for (uint32_t z = tid; z < dim; z += kSmallThreads) st[z] = cmul(st[z], __ldg(T + cut_count_full(gm, n, z)));
+        if (W)
+            for (uint32_t z = tid; z < dim; z += kSmallThreads) st[z] = cmul(st[z], phase_of(wsum_full(W, j.m, 2 + k, z), T[0]));
+        else
+            for (uint32_t z = tid; z < dim; z += kSmallThreads) st[z] = cmul(st[z], __ldg(T + cut_count_full(gm, n, z)));
         const C2 cs = mix[3 * k];
         for (int q = 0; q < n; ++q) {
             __syncthreads();
@@ -942,15 +1257,19 @@ __device__ __forceinline__ void small_body(const SmallJob& j) {
         __syncthreads();
     }
 
-    if (j.cutval)
-        for (uint32_t z = tid; z < dim; z += kSmallThreads) j.cutout[z] = (uint16_t)cut_count_full(gm, n, z);
+    if (j.cutval) {
+        if (W)
+            for (uint32_t z = tid; z < dim; z += kSmallThreads) j.cutout_w[z] = (double)(SWA)wsum_full(W, j.m, 1, z) * j.vscale;
+        else
+            for (uint32_t z = tid; z < dim; z += kSmallThreads) j.cutout[z] = (uint16_t)cut_count_full(gm, n, z);
+    }
 
     if (j.expect) {
         double sc = 0.0, sn = 0.0;
         for (uint32_t z = tid; z < dim; z += kSmallThreads) {
             const double p = (double)st[z].x * (double)st[z].x + (double)st[z].y * (double)st[z].y;
             sn += p;
-            sc += p * (double)cut_count_full(gm, n, z);
+            sc += p * (W ? (double)(SWA)wsum_full(W, j.m, 1, z) * j.vscale : (double)cut_count_full(gm, n, z));
         }
         sc = warp_sum_double(sc);
         sn = warp_sum_double(sn);
@@ -998,6 +1317,31 @@ __device__ __forceinline__ double mixer_factor(double beta, int fold) {
     return fold ? s : co;
 }
 
+// Fixed-point rows of an edge-weighted graph (see the weighted split above).  Row 0: endpoints;
+// row 1: value weights round(w_e 2^S) as signed B-bit words; row wrow0 + k: level k's angles
+// gamma_k w_e / (2 pi) modulo one turn, in units of 2^-B turns.  All in FP64 before rounding.
+template <typename real>
+__device__ void coeff_weighted_rows(const CoeffArgs& a, int k) {
+    using WA = typename WAcc<real>::type;
+    using SWA = typename WAcc<real>::stype;
+    constexpr double kTurn = sizeof(WA) == 4 ? 4294967296.0 : 18446744073709551616.0;
+    WA* W = reinterpret_cast<WA*>(a.wfix);
+    const double inv2pi = 0.15915494309189533577;  // 1 / (2 pi)
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < a.m; e += gridDim.x * blockDim.x) {
+        if (k == 0) {
+            W[e] = (WA)a.uv[e];
+            W[a.m + e] = (WA)(SWA)llrint(a.w[e] * a.vmul);
+        }
+        if (k < a.levels) {
+            double t = a.gamma[k] * a.w[e] * inv2pi;
+            t -= floor(t);                      // [0, 1) turns, exact
+            double u = rint(t * kTurn);         // t * 2^B has at most 53 significant bits
+            if (u >= kTurn) u = 0.0;            // one full turn
+            W[(size_t)(a.wrow0 + k) * a.m + e] = (WA)(unsigned long long)u;
+        }
+    }
+}
+
 template <typename real>
 __global__ void coeff_kernel(const __grid_constant__ CoeffArgs a) {
     using C2 = typename C2T<real>::type;
@@ -1009,6 +1353,8 @@ __global__ void coeff_kernel(const __grid_constant__ CoeffArgs a) {
         if (k > 0) mult *= pow(mixer_factor(a.beta[k - 1], a.fold[k - 1]), (double)a.n);
         if (last) mult *= pow(mixer_factor(a.beta[k], a.fold[k]), (double)a.n);
     }
+    if (a.weighted) coeff_weighted_rows<real>(a, k);
+    if (k >= a.levels) return;  // levels == 0: only the endpoint and value rows
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < a.E1; c += gridDim.x * blockDim.x) {
         double s, co;
         sincos(a.gamma[k] * (double)c, &s, &co);

@@ -34,6 +34,9 @@ namespace qaoa {
 constexpr int kMaxN = 34;
 constexpr int kMaxOps = 48;
 constexpr int kLayerChunk = 64;  // levels per coefficient table upload
+constexpr int kMaxEdges = kMaxN * (kMaxN - 1) / 2;
+constexpr int kMaxLocEdges = 13 * 12 / 2;  // edges among the Q <= 13 local bits of a tile
+constexpr int kWSlots = 4;                 // weighted sums per pass: the value and up to 3 levels
 
 enum OpKind : uint8_t {
     OP_NONE = 0,

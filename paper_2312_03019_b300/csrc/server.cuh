@@ -80,11 +80,12 @@ struct SReq {
 
 // Device block of a request that runs alone (offsets from the block start).
 struct Layout {
-    size_t state, work, phase, mix, partials, result, gtab, gmix, gacc, gpart, total;
+    size_t state, work, phase, mix, partials, result, gtab, gmix, gacc, gpart, wfix, gwfix, total;
 };
 
-Layout single_layout(int n, int m, int p, int prec, bool grad, uint64_t ntiles) {
-    const size_t eb = elem_bytes(prec), E1 = (size_t)m + 1, dim = (size_t)1 << n;
+Layout single_layout(const HostGraph& g, int p, int prec, bool grad, uint64_t ntiles) {
+    const int n = g.n;
+    const size_t eb = elem_bytes(prec), E1 = (size_t)table_entries(g), dim = (size_t)1 << n;
     Layout L{};
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -98,11 +99,13 @@ Layout single_layout(int n, int m, int p, int prec, bool grad, uint64_t ntiles) 
     L.mix = take((size_t)3 * p * eb);
     L.partials = take(ntiles * sizeof(double2));
     L.result = take(sizeof(double2));
+    if (g.weighted) L.wfix = take(wfix_bytes(g, prec, p));
     if (grad) {
         L.gtab = take((size_t)p * E1 * eb);
         L.gmix = take((size_t)3 * p * eb);
         L.gacc = take((size_t)2 * p * sizeof(double));
         L.gpart = take((size_t)2 * ntiles * sizeof(double2));
+        if (g.weighted) L.gwfix = take(wfix_bytes(g, prec, p));
     }
     L.total = o;
     return L;
@@ -204,7 +207,7 @@ void bump(qaoa_server_s* sv, int64_t qaoa_server_stats::*field, int64_t k = 1) {
 }
 
 bool serve_small(const qaoa_server_s* sv, const SReq& r) {
-    return !r.grad && is_small(r.g.n, sv->cfg.prec);
+    return !r.grad && !r.g.weighted && is_small(r.g.n, sv->cfg.prec);
 }
 
 cudaEvent_t take_event(qaoa_server_s* sv) {
@@ -302,12 +305,14 @@ qaoa_status dispatch_single(qaoa_server_s* sv, SReq&& r, size_t off, const Layou
     st->d_mix = base + L.mix;
     st->d_partials = reinterpret_cast<double2*>(base + L.partials);
     st->d_result = reinterpret_cast<double2*>(base + L.result);
+    if (r.g.weighted) st->d_wfix = base + L.wfix;
     if (r.grad) {
         st->grad_levels = r.p;
         st->d_gtab = base + L.gtab;
         st->d_gmix = base + L.gmix;
         st->d_gacc = reinterpret_cast<double*>(base + L.gacc);
         st->d_gpart = reinterpret_cast<double2*>(base + L.gpart);
+        if (r.g.weighted) st->d_gwfix = base + L.gwfix;
     }
     run.st = st;
     double* host = sv->pin_single + (size_t)slot * (2 + 2 * QAOA_SERVE_MAX_P);
@@ -337,6 +342,7 @@ qaoa_status dispatch_single(qaoa_server_s* sv, SReq&& r, size_t off, const Layou
         st->d_gtab = st->d_gmix = nullptr;
         st->d_gacc = nullptr;
         st->d_gpart = nullptr;
+        st->d_wfix = st->d_gwfix = nullptr;
         delete st;
         return s;
     }
@@ -489,6 +495,7 @@ bool scheduler_turn(qaoa_server_s* sv) {
         st->d_gtab = st->d_gmix = nullptr;
         st->d_gacc = nullptr;
         st->d_gpart = nullptr;
+        st->d_wfix = st->d_gwfix = nullptr;
         delete st;
         sv->inflight--;
         sv->running[i] = std::move(sv->running.back());
@@ -551,7 +558,7 @@ bool scheduler_turn(qaoa_server_s* sv) {
             if (sv->free_single.empty()) break;
             const uint64_t ntiles = r.g.n > tile_config_for(sv->cfg.prec).Q
                                         ? (1ull << (r.g.n - tile_config_for(sv->cfg.prec).Q)) : 1ull;
-            const Layout L = single_layout(r.g.n, r.g.m, r.p, sv->cfg.prec, r.grad, ntiles);
+            const Layout L = single_layout(r.g, r.p, sv->cfg.prec, r.grad, ntiles);
             size_t off = 0;
             if (!sv->arena.alloc(L.total, off)) break;
             const int slot = sv->free_single.back();
@@ -699,8 +706,8 @@ qaoa_status qaoa_submit(qaoa_server sv, const qaoa_request* r, uint64_t* ticket)
     q.grad = r->want_grad != 0;
     const TileConfig tc = tile_config_for(sv->cfg.prec);
     const uint64_t ntiles = q.g.n > tc.Q ? (1ull << (q.g.n - tc.Q)) : 1ull;
-    const size_t need = (!q.grad && is_small(q.g.n, sv->cfg.prec)) ? small_bytes(q.g.m, q.p, sv->cfg.prec)
-                                                                  : single_layout(q.g.n, q.g.m, q.p, sv->cfg.prec, q.grad, ntiles).total;
+    const size_t need = (!q.grad && !q.g.weighted && is_small(q.g.n, sv->cfg.prec)) ? small_bytes(q.g.m, q.p, sv->cfg.prec)
+                                                                  : single_layout(q.g, q.p, sv->cfg.prec, q.grad, ntiles).total;
     if (need > sv->arena.size) return fail(QAOA_ERR_OOM, "request needs more device memory than the server's arena");
     std::lock_guard<std::mutex> lock(sv->mu);
     if ((int)sv->queue.size() >= sv->cfg.queue_capacity) {

@@ -1,0 +1,226 @@
+"""Edge-weighted graphs (Algorithm 2: C(z) = sum_e w_e (z_u xor z_v), real w_e) on the GPU
+against the CPU oracle.
+
+The kernels evaluate two fixed-point sums per amplitude (B = 32 bits for complex64, 64 for
+complex128, exact modulo 2^B): the phase angle from per-edge angles gamma w_e / (2 pi) rounded to
+2^-B turns, and the value C(z) from the weights rounded to 2^-S, S the largest power with
+sum |w_e| 2^S <= 2^(B-2).  Tolerances follow from that:
+  cut values: at most m 2^-(S+1) from the exact sum (bit-exact for integer weights);
+  complex128: <C> within 1e-12 relative, state within 1e-12 in the 2-norm;
+  complex64: <C> within 1e-5 sum |w|, fidelity >= 1 - 1e-5.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2312_03019_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2312_03019_b300 import build
+    build.build()
+    from paper_2312_03019_b300 import binding
+    return binding
+
+
+def weighted(g, seed, lo=0.1, hi=2.0):
+    return I.random_weights(g, seed=seed, lo=lo, hi=hi)
+
+
+def integer_weighted(g, seed):
+    w = I.random_weights(g, seed=seed, lo=1.0, hi=6.0)
+    return I.Graph(n=g.n, edges=w.edges, weights=np.floor(w.weights), name=g.name + "+int")
+
+
+def value_tol(g, prec):
+    tot = float(np.sum(np.abs(g.weights)))
+    bits = 32 if prec == "c64" else 64
+    s = bits - 2 - math.ceil(math.log2(tot))
+    return g.m * 2.0 ** -(s + 1) + 1e-12 * tot
+
+
+def oracle_weighted_cuts(g):
+    """C(z) from Algorithm 2's totRotation, C = (W - totRotation) / 2, cross-checked against the
+    oracle's plain edge loop."""
+    import oracle
+    W = float(np.sum(g.weights))
+    out = np.empty(1 << g.n)
+    for z in range(1 << g.n):
+        out[z] = oracle.cut_value(g, z)
+    for z in range(0, 1 << g.n, max(1, (1 << g.n) // 64)):
+        assert abs((W - oracle.alg2_tot_rotation(g, z)) / 2 - out[z]) <= 1e-12 * max(1.0, W)
+    return out
+
+
+GRAPHS = [
+    lambda n: weighted(I.regular3(n, n) if n % 2 == 0 else I.gnp(n, 0.3, n), 1),
+    lambda n: weighted(I.gnp(n, 0.5, 2 * n), 2, lo=-1.0, hi=1.0),       # signed weights
+    lambda n: weighted(I.complete(min(n, 12)), 3, lo=10.0, hi=100.0),   # large gamma w: many turns
+]
+
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+@pytest.mark.parametrize("n", [6, 11, 14, 16])
+def test_weighted_cut_values_every_geometry(B, prec, n):
+    for mk in GRAPHS:
+        g = mk(n)
+        ref = oracle_weighted_cuts(g)
+        tol = value_tol(g, prec)
+        got = B.qaoa_cut_table_f64(g, prec)  # the path the size uses by default
+        assert np.max(np.abs(got - ref)) <= tol, (g.name, prec)
+        plan = B.qaoa_plan_describe(g.n, prec, 1)
+        if not plan:  # whole state in one CTA: no tile geometries
+            continue
+        groups = plan[3]
+        for grp in range(groups):
+            for layout in range(3):
+                got = B.qaoa_cut_table_f64(g, prec, grp, layout)
+                assert np.max(np.abs(got - ref)) <= tol, (g.name, prec, grp, layout)
+
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+@pytest.mark.parametrize("n", [9, 15])
+def test_integer_weights_bit_exact(B, prec, n):
+    g = integer_weighted(I.gnp(n, 0.4, 11), 4)
+    ref = oracle_weighted_cuts(g)
+    got = B.qaoa_cut_table_f64(g, prec)
+    assert np.array_equal(got, ref)
+
+
+def run(B, g, gamma, beta, prec):
+    s = B.QAOAState(g, prec)
+    s.apply_layers(gamma, beta)
+    c, nrm = s.expectation()
+    psi = s.amplitudes().astype(np.complex128)
+    s.close()
+    return c, nrm, psi
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("n,p,mk", [
+    (2, 2, lambda: weighted(I._canonical(2, [(0, 1)], "edge"), 5)),
+    (8, 3, lambda: weighted(I.complete(8), 6, lo=-2.0, hi=2.0)),
+    (10, 2, lambda: weighted(I.regular3(10, 0), 7)),
+    (13, 3, lambda: weighted(I.gnp(13, 0.4, 8), 8)),
+    (14, 2, lambda: weighted(I.regular3(14, 1), 9, lo=5.0, hi=50.0)),
+    (16, 4, lambda: weighted(I.gnp(16, 0.3, 9), 10)),
+    (18, 3, lambda: weighted(I.regular3(18, 2), 11)),
+    (20, 2, lambda: weighted(I.gnp(20, 0.25, 10), 12, lo=-1.0, hi=3.0)),
+])
+def test_weighted_state_parity(B, prec, n, p, mk):
+    import oracle
+    g = mk()
+    gamma, beta = I.angles(p, seed=n + 40)
+    ref = oracle.qaoa_state(g, gamma, beta)
+    ref_c, _ = oracle.expectation(g, ref)
+    c, nrm, psi = run(B, g, gamma, beta, prec)
+    if prec == "c128":
+        assert abs(c - ref_c) <= 1e-12 * max(1.0, abs(ref_c))
+        assert abs(nrm - 1.0) < 1e-12
+        assert np.linalg.norm(psi - ref) <= 1e-12
+    else:
+        assert abs(c - ref_c) <= 1e-5 * float(np.sum(np.abs(g.weights)))
+        assert abs(nrm - 1.0) < 1e-5
+        assert abs(np.vdot(ref, psi)) ** 2 >= 1 - 1e-5
+
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+def test_weights_all_one_take_the_unit_path(B, prec):
+    g = I.gnp(17, 0.4, 3)
+    g1 = I.Graph(n=g.n, edges=g.edges, weights=np.ones(g.m), name=g.name + "+ones")
+    gamma, beta = I.angles(3, 5)
+    c0, _, psi0 = run(B, g, gamma, beta, prec)
+    c1, _, psi1 = run(B, g1, gamma, beta, prec)
+    assert c0 == c1 and np.array_equal(psi0, psi1)
+
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+def test_weighted_zero_levels_expectation(B, prec):
+    """|+>^n: <C> = W / 2 exactly up to the value rounding, through the lazy initial state."""
+    g = weighted(I.regular3(16, 4), 13)
+    s = B.QAOAState(g, prec)
+    c, nrm = s.expectation()
+    s.close()
+    assert abs(c - float(np.sum(g.weights)) / 2) <= value_tol(g, prec) + (1e-6 if prec == "c64" else 1e-12) * float(np.sum(g.weights))
+    assert abs(nrm - 1.0) <= (1e-6 if prec == "c64" else 1e-13)
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("n,p,mk", [
+    (6, 3, lambda: weighted(I.complete(6), 20, lo=-1.0, hi=2.0)),
+    (12, 2, lambda: weighted(I.gnp(12, 0.5, 21), 21)),
+    (14, 3, lambda: weighted(I.regular3(14, 22), 22)),
+    (16, 2, lambda: weighted(I.gnp(16, 0.3, 23), 23, lo=2.0, hi=20.0)),
+])
+def test_weighted_gradient_matches_oracle_adjoint(B, prec, n, p, mk):
+    import oracle
+    import torch
+    g = mk()
+    gamma, beta = I.angles(p, seed=n + 70)
+    ref_c, ref_dg, ref_db = oracle.adjoint_gradient(g, gamma, beta)
+    s = B.QAOAState(g, prec)
+    work = torch.empty(s.nbytes, dtype=torch.uint8, device="cuda")
+    c, dg, db = B.qaoa_gradient(s.handle, gamma, beta, work.data_ptr(), s.nbytes)
+    s.close()
+    W = float(np.sum(np.abs(g.weights)))
+    scale = max(1.0, np.max(np.abs(np.concatenate([ref_dg, ref_db]))))
+    if prec == "c128":
+        assert abs(c - ref_c) <= 1e-12 * max(1.0, abs(ref_c))
+        assert np.max(np.abs(dg - ref_dg)) <= 1e-10 * scale
+        assert np.max(np.abs(db - ref_db)) <= 1e-10 * scale
+    else:
+        assert abs(c - ref_c) <= 1e-5 * W
+        assert np.max(np.abs(dg - ref_dg)) <= 1e-4 * W * max(1.0, W / g.m)
+        assert np.max(np.abs(db - ref_db)) <= 1e-4 * W
+
+
+def test_weighted_requests_through_the_server(B):
+    reqs = [(weighted(I.gnp(n, 0.4, n), n), *I.angles(2, n), n % 2 == 0) for n in (9, 14, 18)]
+    sv = B.qaoa_server_create(1 << 30, "c64", max_inflight=8, max_batch=8, streams=2)
+    tickets = [B.qaoa_submit(sv, g, ga, be, grad) for g, ga, be, grad in reqs]
+    got = {}
+    import time
+    t0 = time.time()
+    while len(got) < len(tickets) and time.time() - t0 < 60:
+        for t in tickets:
+            if t not in got:
+                r = B.qaoa_poll(sv, t)
+                if r is not None:
+                    got[t] = r
+        time.sleep(0.001)
+    stats = B.qaoa_server_stats_read(sv)
+    B.qaoa_server_destroy(sv)
+    assert stats["batched_requests"] == 0  # weighted requests always run alone
+    import torch
+    for (g, ga, be, grad), t in zip(reqs, tickets):
+        r = got[t]
+        assert r["status"] == 0
+        s = B.QAOAState(g, "c64")
+        if grad:
+            work = torch.empty(s.nbytes, dtype=torch.uint8, device="cuda")
+            c, dg, db = B.qaoa_gradient(s.handle, ga, be, work.data_ptr(), s.nbytes)
+            assert np.array_equal(r["d_gamma"], dg) and np.array_equal(r["d_beta"], db)
+        else:
+            s.apply_layers(ga, be)
+            c, _ = s.expectation()
+        s.close()
+        assert r["expectation"] == c
+
+
+def test_weighted_rejections(B):
+    g = I.gnp(10, 0.5, 1)
+    bad = I.Graph(n=g.n, edges=g.edges, weights=np.full(g.m, np.nan))
+    with pytest.raises(B.QAOAError):
+        B.QAOAState(bad, "c64")
+    huge = I.Graph(n=g.n, edges=g.edges, weights=np.full(g.m, 1e13))
+    with pytest.raises(B.QAOAError):
+        B.QAOAState(huge, "c64")
+    with pytest.raises(B.QAOAError):  # the uint16 table is for cut counts only
+        B.qaoa_cut_table(weighted(g, 1))
