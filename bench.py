@@ -175,6 +175,25 @@ def cpu_baseline_block(args, g_target):
                        f"by 2^n x gate count ({gates_per_level(gs)} -> {gates_per_level(g_target)} gates/level)")}
 
 
+def paper_method_block(g_target, n_s: int = 24):
+    """The paper's own CPU method (Opt_u: launch control, Algorithm 2 + 3 cost layer, mixer gate
+    by gate, OpenMP) timed for one level at n_s on the same graph family, scaled to the target
+    size by 2^n x n (its per-level work: n popcounts per amplitude and n mixer passes)."""
+    import baseline
+    gs = I.regular3(n_s, 0)
+    ga, be = I.angles(1, 0)
+    baseline.run(gs, ga, be)  # warm-up (page faults, thread start)
+    t0 = time.perf_counter()
+    baseline.run(gs, ga, be)
+    t = time.perf_counter() - t0
+    scale = (2.0 ** (g_target.n - n_s)) * g_target.n / n_s
+    return {"value": 1.0 / (t * scale), "unit": UNIT, "cores": baseline.threads(), "kind": "paper method (Opt_u)",
+            "sample": (f"one level of Opt_u (launch control + Algorithm 2/3 + gate-by-gate mixer, OpenMP) on "
+                       f"3-regular n={n_s} took {t:.3f} s (includes the launch-control fill); scaled to "
+                       f"n={g_target.n} by 2^n x n"),
+            "measured_layers_per_s_at_sample": 1.0 / t}
+
+
 # --------------------------------------------------------------------------------- reference arm
 
 def run_reference(args):
@@ -334,6 +353,7 @@ def run_ours(args):
         del st
         torch.cuda.empty_cache()
         rec["cpu_baseline"] = cpu_baseline_block(args, g)
+        rec["cpu_paper_method"] = paper_method_block(g)
     if rank == 0:
         print(json.dumps(rec), flush=True)
     if world > 1:
