@@ -9,12 +9,14 @@ from __future__ import annotations
 import os
 import subprocess
 import sys
+import tempfile
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libqaoa_b300.so")
-SOURCES = ["capi.cu", "plan.cpp"]
-HEADERS = ["kernels.cuh", "plan.h", "server.cuh", os.path.join("..", "..", "include", "qaoa.h")]
+# translation units, compiled in parallel and linked into one shared object
+SOURCES = ["capi.cu", "tile_c64.cu", "recipes_c64.cu", "tile_c128.cu", "grad_kernels.cu", "plan.cpp"]
+HEADERS = ["kernels.cuh", "plan.h", "server.cuh", "instances.h", os.path.join("..", "..", "include", "qaoa.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -34,17 +36,33 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not (force or verbose or _stale()):
         return LIB
     nvcc = os.environ.get("NVCC", "nvcc")
-    cmd = [nvcc, "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC,-O2", "-shared",
-           "-o", LIB + ".tmp"] + [os.path.join(CSRC, s) for s in SOURCES]
+    # kernel template instances live in their own units: their host stubs need external linkage
+    flags = ["-O3", "-std=c++17", *ARCH, "-lineinfo", "-static-global-template-stub=false", "-Xcompiler",
+             "-fPIC,-O2"]
     if verbose:
-        cmd += ["-Xptxas", "-v"]
-    cmd += os.environ.get("QAOA_NVCC_EXTRA", "").split()
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        sys.stderr.write(r.stdout + r.stderr)
-        raise RuntimeError("nvcc failed building libqaoa_b300.so")
-    if verbose:
-        sys.stderr.write(r.stderr)
+        flags += ["-Xptxas", "-v"]
+    flags += os.environ.get("QAOA_NVCC_EXTRA", "").split()
+    with tempfile.TemporaryDirectory(prefix="qaoa_build_") as tmp:
+        objs, procs = [], []
+        for src in SOURCES:
+            obj = os.path.join(tmp, src + ".o")
+            objs.append(obj)
+            procs.append((src, subprocess.Popen([nvcc, *flags, "-c", os.path.join(CSRC, src), "-o", obj],
+                                                stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)))
+        failed = False
+        for src, pr in procs:
+            out, _ = pr.communicate()
+            if pr.returncode != 0:
+                failed = True
+                sys.stderr.write(out)
+            elif verbose:
+                sys.stderr.write(out)
+        if failed:
+            raise RuntimeError("nvcc failed building libqaoa_b300.so")
+        r = subprocess.run([nvcc, *ARCH, "-shared", "-o", LIB + ".tmp", *objs], capture_output=True, text=True)
+        if r.returncode != 0:
+            sys.stderr.write(r.stdout + r.stderr)
+            raise RuntimeError("nvcc failed linking libqaoa_b300.so")
     os.replace(LIB + ".tmp", LIB)
     return LIB
 

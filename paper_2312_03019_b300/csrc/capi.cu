@@ -21,6 +21,7 @@
 
 #include "../../include/qaoa.h"
 #include "kernels.cuh"
+#include "instances.h"
 #include "plan.h"
 
 using namespace qaoa;
@@ -280,6 +281,7 @@ struct qaoa_state_s {
     bool lazy = true;
     bool exp_valid = false;
     bool compl_ = false;  // buffer index z holds the amplitude of ~z (pending X on every qubit)
+    bool pform_ = false;  // complex64 parity form: odd-parity indices hold (im, re)
     // profiling
     bool prof = false;
     std::vector<EventPair> events;
@@ -304,6 +306,38 @@ EventPair* next_event(qaoa_state s, int kind) {
 // Dynamic shared-memory limits of the kernels, set once per process (first use, or by
 // prepare_kernels before any stream capture).
 template <typename real>
+using TileFn = void (*)(TileArgs<PrecTraits<real>::Q>);
+
+// The straight-line instantiation of recipe r (unit weights).
+template <typename real>
+TileFn<real> recipe_kernel(int r) {
+    constexpr int Q = PrecTraits<real>::Q, R = PrecTraits<real>::R;
+    switch (r) {
+        case 0: return tile_kernel<real, Q, R, false, kRecipe0.code, kRecipe0.nops>;
+        case 1: return tile_kernel<real, Q, R, false, kRecipe1.code, kRecipe1.nops>;
+        case 2: return tile_kernel<real, Q, R, false, kRecipe2.code, kRecipe2.nops>;
+        case 3: return tile_kernel<real, Q, R, false, kRecipe3.code, kRecipe3.nops>;
+        default: return tile_kernel<real, Q, R, false, kRecipe4.code, kRecipe4.nops>;
+    }
+}
+
+// The pass kernel for a program: its recipe instantiation when one matches, else the
+// interpreting one.
+template <typename real>
+TileFn<real> pick_tile_kernel(const TileArgs<PrecTraits<real>::Q>& a, bool weighted) {
+    constexpr int Q = PrecTraits<real>::Q, R = PrecTraits<real>::R;
+    if (weighted) return tile_kernel<real, Q, R, true>;
+    if (a.nops <= 10) {
+        uint64_t code = 0;
+        for (int i = 0; i < a.nops; ++i) code |= recipe_step(i, a.ops[i].kind, a.ops[i].layout);
+        const Recipe rs[kRecipes] = {kRecipe0, kRecipe1, kRecipe2, kRecipe3, kRecipe4};
+        for (int r = 0; r < kRecipes; ++r)
+            if (rs[r].nops == a.nops && rs[r].code == code) return recipe_kernel<real>(r);
+    }
+    return tile_kernel<real, Q, R, false>;
+}
+
+template <typename real>
 qaoa_status ensure_attributes() {
     static bool done = false;
     if (done) return QAOA_OK;
@@ -313,6 +347,9 @@ qaoa_status ensure_attributes() {
                                   (int)((1u << Q) * sizeof(C2))));
     CUDA_TRY(cudaFuncSetAttribute(tile_kernel<real, Q, R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)((1u << Q) * sizeof(C2))));
+    for (int r = 0; r < kRecipes; ++r)
+        CUDA_TRY(cudaFuncSetAttribute(recipe_kernel<real>(r), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)((1u << Q) * sizeof(C2))));
     CUDA_TRY(cudaFuncSetAttribute(grad_kernel<real, Q, R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)((1u << Q) * sizeof(C2))));
     CUDA_TRY(cudaFuncSetAttribute(grad_kernel<real, Q, R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -334,7 +371,7 @@ template <typename real>
 qaoa_status launch_tile(qaoa_state s, TileArgs<PrecTraits<real>::Q>& a, int kind) {
     constexpr int Q = PrecTraits<real>::Q, R = PrecTraits<real>::R;
     using C2 = typename C2T<real>::type;
-    auto kfn = s->g.weighted ? tile_kernel<real, Q, R, true> : tile_kernel<real, Q, R, false>;
+    auto kfn = pick_tile_kernel<real>(a, s->g.weighted);
     const size_t smem = (size_t)(1u << Q) * sizeof(C2);
     qaoa_status ast = ensure_attributes<real>();
     if (ast != QAOA_OK) return ast;
@@ -397,6 +434,9 @@ qaoa_status run_plan(qaoa_state s, const Plan& plan) {
 }
 
 template <typename real>
+qaoa_status set_parity_form(qaoa_state s, bool parity);
+
+template <typename real>
 qaoa_status apply_chunk(qaoa_state s, int levels, const double* gamma, const double* beta, bool expect) {
     CoeffArgs ca;
     std::memset(&ca, 0, sizeof(ca));
@@ -446,9 +486,12 @@ qaoa_status apply_chunk(qaoa_state s, int levels, const double* gamma, const dou
         qaoa_status st = launch_small<real>(s, j);
         if (st != QAOA_OK) return st;
     } else {
-        Plan plan = plan_levels(s->n, s->tc, levels, s->lazy, expect);
-        qaoa_status st = run_plan<real>(s, plan);
+        qaoa_status st = set_parity_form<real>(s, true);  // the passes read and write the parity form
         if (st != QAOA_OK) return st;
+        Plan plan = plan_levels(s->n, s->tc, levels, s->lazy, expect);
+        st = run_plan<real>(s, plan);
+        if (st != QAOA_OK) return st;
+        s->pform_ = std::is_same<real, float>::value;
     }
     s->lazy = false;
     if (expect) {
@@ -483,13 +526,27 @@ qaoa_status materialize(qaoa_state s) {
         s->launches++;
         s->lazy = false;
         s->compl_ = false;  // |+>^n is its own complement
+        s->pform_ = false;
     }
-    if (s->compl_) {
-        complement_kernel<real><<<148 * 8, 256, 0, s->stream>>>(s->buf, s->dim);
+    if (s->compl_ || s->pform_) {
+        complement_kernel<real><<<148 * 8, 256, 0, s->stream>>>(s->buf, s->dim, s->compl_ ? 1 : 0, s->pform_ ? 1 : 0);
         CUDA_TRY(cudaGetLastError());
         s->launches++;
         s->compl_ = false;
+        s->pform_ = false;
     }
+    return QAOA_OK;
+}
+
+// Puts (parity = true) or takes (false) the state buffer into / out of the complex64 parity form
+// the forward tile passes keep it in between passes.
+template <typename real>
+qaoa_status set_parity_form(qaoa_state s, bool parity) {
+    if (!std::is_same<real, float>::value || s->lazy || s->pform_ == parity) return QAOA_OK;
+    complement_kernel<real><<<148 * 8, 256, 0, s->stream>>>(s->buf, s->dim, 0, 1);
+    CUDA_TRY(cudaGetLastError());
+    s->launches++;
+    s->pform_ = parity;
     return QAOA_OK;
 }
 
@@ -789,6 +846,7 @@ qaoa_status forward_async(qaoa_state s, int p, const double* gamma, const double
     s->lazy = true;
     s->exp_valid = false;
     s->compl_ = false;
+    s->pform_ = false;
     qaoa_status st = QAOA_OK;
     for (int k0 = 0; k0 < p && st == QAOA_OK; k0 += kLayerChunk) {
         const int levels = std::min(kLayerChunk, p - k0);
@@ -804,6 +862,7 @@ qaoa_status forward_async(qaoa_state s, int p, const double* gamma, const double
 template <typename real>
 qaoa_status gradient_async(qaoa_state s, int p, const double* gamma, const double* beta, void* work) {
     qaoa_status st = forward_async<real>(s, p, gamma, beta);
+    if (st == QAOA_OK) st = set_parity_form<real>(s, false);  // the sweep reads the plain form
     if (st != QAOA_OK) return st;
     using C2 = typename C2T<real>::type;
     // plain per-level tables (no folded factors) for the sweep
@@ -885,6 +944,7 @@ qaoa_status gradient_async(qaoa_state s, int p, const double* gamma, const doubl
     s->lazy = true;
     s->exp_valid = false;
     s->compl_ = false;
+    s->pform_ = false;
     return QAOA_OK;
 }
 
@@ -975,6 +1035,7 @@ qaoa_status qaoa_state_reset(qaoa_state s) {
     s->lazy = true;
     s->exp_valid = false;
     s->compl_ = false;
+    s->pform_ = false;
     return QAOA_OK;
 }
 

@@ -1,0 +1,47 @@
+// instances.h -- the heavy kernel template instantiations (the pass kernels and the adjoint-sweep
+// kernels), each compiled in a translation unit of its own (tile_c64.cu, tile_c128.cu,
+// grad_kernels.cu) so that the library builds in parallel.  capi.cu includes this file after
+// kernels.cuh with QAOA_INSTANCE = "extern template" (declarations); each instance unit defines
+// QAOA_OWN_* for the set it owns and instantiates that set with QAOA_INSTANCE = "template".
+// Building this way needs -static-global-template-stub=false (external kernel stubs).
+#pragma once
+
+#ifndef QAOA_INSTANCE
+#define QAOA_INSTANCE extern template
+#endif
+
+#define QAOA_TILE_INSTANCES(real, Q, R)                                                                  \
+    namespace qaoa {                                                                                      \
+    QAOA_INSTANCE __global__ void tile_kernel<real, Q, R, false, 0, 0>(const __grid_constant__ TileArgs<Q>);                \
+    QAOA_INSTANCE __global__ void tile_kernel<real, Q, R, true, 0, 0>(const __grid_constant__ TileArgs<Q>);                 \
+    }
+
+#define QAOA_RECIPE_INSTANCES(real, Q, R)                                                                \
+    namespace qaoa {                                                                                      \
+    QAOA_INSTANCE __global__ void tile_kernel<real, Q, R, false, kRecipe0.code, kRecipe0.nops>(const __grid_constant__ TileArgs<Q>); \
+    QAOA_INSTANCE __global__ void tile_kernel<real, Q, R, false, kRecipe1.code, kRecipe1.nops>(const __grid_constant__ TileArgs<Q>); \
+    QAOA_INSTANCE __global__ void tile_kernel<real, Q, R, false, kRecipe2.code, kRecipe2.nops>(const __grid_constant__ TileArgs<Q>); \
+    QAOA_INSTANCE __global__ void tile_kernel<real, Q, R, false, kRecipe3.code, kRecipe3.nops>(const __grid_constant__ TileArgs<Q>); \
+    QAOA_INSTANCE __global__ void tile_kernel<real, Q, R, false, kRecipe4.code, kRecipe4.nops>(const __grid_constant__ TileArgs<Q>); \
+    }
+
+#define QAOA_GRAD_INSTANCES(real, Q, R)                                              \
+    namespace qaoa {                                                                  \
+    QAOA_INSTANCE __global__ void grad_kernel<real, Q, R, false>(const __grid_constant__ TileArgs<Q>);  \
+    QAOA_INSTANCE __global__ void grad_kernel<real, Q, R, true>(const __grid_constant__ TileArgs<Q>);   \
+    }
+
+#if !defined(QAOA_OWN_TILE_C64)
+QAOA_TILE_INSTANCES(float, 13, 5)
+#endif
+#if !defined(QAOA_OWN_RECIPE_C64)
+QAOA_RECIPE_INSTANCES(float, 13, 5)
+#endif
+#if !defined(QAOA_OWN_TILE_C128)
+QAOA_TILE_INSTANCES(double, 12, 4)
+QAOA_RECIPE_INSTANCES(double, 12, 4)
+#endif
+#if !defined(QAOA_OWN_GRAD)
+QAOA_GRAD_INSTANCES(float, 13, 5)
+QAOA_GRAD_INSTANCES(double, 12, 4)
+#endif

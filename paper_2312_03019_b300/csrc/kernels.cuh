@@ -138,16 +138,9 @@ __device__ __forceinline__ C2 cmul(C2 a, C2 b) {
     return make_c2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// d = a * b + c on two float lanes at once (one packed FMA instruction on sm_100 and later).
-__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
-    float2 d;
-    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
-        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
-        "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
-        : "=f"(d.x), "=f"(d.y)
-        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
-    return d;
-}
+// d = a * b + c on two float lanes at once (one packed FMA instruction on sm_100 and later;
+// CUDA's builtin, which keeps each float2 in an aligned register pair).
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
 __host__ __device__ constexpr bool odd_parity(int x) {
     int p = 0;
@@ -274,21 +267,28 @@ __device__ void weighted_cta_setup(const TileArgs<Q>& a, uint64_t zb, WA* sK, WA
 
 // ---------------------------------------------------------------------------------- tile pass
 
-template <typename real, int Q, int R>
+template <typename real, int Q, int R, bool kGP = false>
 struct Tile {
     using C2 = typename C2T<real>::type;
     static constexpr int NT = 1 << (Q - R);
     static constexpr int NE = 1 << R;
     static constexpr bool kPair = sizeof(C2) == 8;  // two amplitudes per 16-byte vector
 
-    // complex64 register representation: register slot x holds (re, im) when x has an even
-    // number of set bits and (im, re) when odd.  Every butterfly then pairs one slot of each
-    // kind and becomes two packed FMAs (see rx_bits); the swap is undone wherever amplitudes
-    // leave registers (HBM, shared memory) and re-applied when they come back.
+    // complex64 amplitude forms: an amplitude is held either as (re, im) or as (im, re), such
+    // that every butterfly pairs one of each and becomes two packed FMAs (see rx_bits).
+    //   kGP = false (adjoint sweep): the form follows the register index, (im, re) when slot x
+    //     has an odd number of set bits; it is converted wherever amplitudes leave registers.
+    //   kGP = true (forward passes): the form follows the amplitude's global index z, (im, re)
+    //     when z has odd parity, in registers, shared memory and HBM alike, so loads, stores and
+    //     exchanges move raw values.  Slot x of a thread then holds (im, re) when
+    //     parity(x) xor P = 1 with P = parity(tile outer bits) xor parity(tid) (every layout
+    //     places the thread index bits by a bit permutation, so P is the same in all of them);
+    //     a thread with P = 1 runs the same butterflies with t -> -t (sg = -1).  The state buffer
+    //     is then in "parity form" between passes and is converted when it is read out.
     static constexpr bool kSwapOdd = kPair;
     template <int x>
     static __device__ __forceinline__ C2 to_reg(C2 z) {
-        if constexpr (kSwapOdd && odd_parity(x)) return make_c2(z.y, z.x);
+        if constexpr (kSwapOdd && !kGP && odd_parity(x)) return make_c2(z.y, z.x);
         else return z;
     }
     template <int x>
@@ -338,7 +338,22 @@ struct Tile {
         int* sE;
         const void* wK;  // weighted: per-slot F_s(o|0) (shared memory)
         const void* wE;  // weighted: per-slot e_u terms, [slot][Q] (shared memory)
+        real sg;         // kGP: +1, or -1 when the thread's even-parity slots hold (im, re)
     };
+
+    // f applied to the amplitude in slot x: f itself on a (re, im) slot, conj(f) on an (im, re)
+    // slot (the complex product of the raw pair with conj(f) is the swapped product).
+    template <int x>
+    static __device__ __forceinline__ C2 apply_phase(C2 vx, C2 f, real sg) {
+        if constexpr (kSwapOdd && kGP) {
+            const real fy = (odd_parity(x) ? -sg : sg) * f.y;
+            return cmul(vx, make_c2(f.x, fy));
+        } else if constexpr (kSwapOdd && odd_parity(x)) {
+            return make_c2(vx.x * f.x + vx.y * f.y, vx.y * f.x - vx.x * f.y);
+        } else {
+            return cmul(vx, f);
+        }
+    }
 
     using WA = typename WAcc<real>::type;
     using SWA = typename WAcc<real>::stype;
@@ -562,11 +577,7 @@ struct Tile {
             const C2 g = __ldg(reinterpret_cast<const C2*>(a.phase) + level);
             for_x<NE>([&](auto X) {
                 constexpr int x = decltype(X)::value;
-                const C2 f = phase_of(wat<x>(base, s, P), g);
-                if constexpr (kSwapOdd && odd_parity(x))
-                    v[x] = make_c2(v[x].x * f.x + v[x].y * f.y, v[x].y * f.x - v[x].x * f.y);
-                else
-                    v[x] = cmul(v[x], f);
+                v[x] = apply_phase<x>(v[x], phase_of(wat<x>(base, s, P), g), c.sg);
             });
             return;
         }
@@ -580,11 +591,7 @@ struct Tile {
             for (int j = 0; j < R; ++j)
                 if ((x >> j) & 1) cidx += s[j];
             // the count is always in [0, |E|]; the unsigned clamp keeps every table read in bounds
-            const C2 f = __ldg(T + min((unsigned)cidx, (unsigned)(a.E1 - 1)));
-            if constexpr (kSwapOdd && odd_parity(x))  // slot holds (im, re)
-                v[x] = make_c2(v[x].x * f.x + v[x].y * f.y, v[x].y * f.x - v[x].x * f.y);
-            else
-                v[x] = cmul(v[x], f);
+            v[x] = apply_phase<x>(v[x], __ldg(T + min((unsigned)cidx, (unsigned)(a.E1 - 1))), c.sg);
         });
     }
 
@@ -833,13 +840,59 @@ struct Tile {
 
 };
 
+// Pass recipes: the op kinds of a pass program and the layouts its LOAD / SYNTH / XCHG ops
+// switch to, 6 bits per op (kind | layout << 4).  A recipe instantiation of tile_kernel runs
+// that program as straight-line code (levels and masks stay runtime arguments), so the register
+// allocator carries the amplitudes across op boundaries and the op dispatch disappears; passes
+// whose program matches no compiled recipe run the interpreting instantiation (kNops = 0).
+__host__ __device__ constexpr int recipe_kind(uint64_t r, int i) { return (int)((r >> (6 * i)) & 15u); }
+__host__ __device__ constexpr bool sets_layout(int kind) {
+    return kind == OP_LOAD || kind == OP_SYNTH || kind == OP_XCHG;
+}
+// register layout in effect after op i
+__host__ __device__ constexpr int recipe_layout(uint64_t r, int i) {
+    int L = 0;
+    for (int k = 0; k <= i; ++k)
+        if (sets_layout(recipe_kind(r, k))) L = (int)((r >> (6 * k + 4)) & 3u);
+    return L;
+}
+__host__ __device__ constexpr uint64_t recipe_step(int i, int kind, int layout) {
+    return (uint64_t)(kind | (sets_layout(kind) ? layout : 0) << 4) << (6 * i);
+}
+
+struct Recipe {
+    uint64_t code;
+    int nops;
+};
+// The pass programs of the tiled plans with three or more groups (complex64 n >= 23, complex128
+// n >= 20): first pass, group-0 pass, fused boundary pass, last pass, and complex128's
+// two-exchange high-group pass.
+constexpr Recipe kRecipe0{recipe_step(0, OP_SYNTH, 1) | recipe_step(1, OP_PHASE, 0) | recipe_step(2, OP_RX, 0) |
+                              recipe_step(3, OP_XCHG, 0) | recipe_step(4, OP_RX, 0) | recipe_step(5, OP_STORE, 0),
+                          6};
+constexpr Recipe kRecipe1{recipe_step(0, OP_LOAD, 1) | recipe_step(1, OP_RX, 0) | recipe_step(2, OP_XCHG, 2) |
+                              recipe_step(3, OP_RX, 0) | recipe_step(4, OP_XCHG, 0) | recipe_step(5, OP_RX, 0) |
+                              recipe_step(6, OP_STORE, 0),
+                          7};
+constexpr Recipe kRecipe2{recipe_step(0, OP_LOAD, 0) | recipe_step(1, OP_RX, 0) | recipe_step(2, OP_XCHG, 1) |
+                              recipe_step(3, OP_RX, 0) | recipe_step(4, OP_PHASE, 0) | recipe_step(5, OP_RX, 0) |
+                              recipe_step(6, OP_XCHG, 0) | recipe_step(7, OP_RX, 0) | recipe_step(8, OP_STORE, 0),
+                          9};
+constexpr Recipe kRecipe3{recipe_step(0, OP_LOAD, 1) | recipe_step(1, OP_RX, 0) | recipe_step(2, OP_XCHG, 0) |
+                              recipe_step(3, OP_RX, 0) | recipe_step(4, OP_EXPECT, 0) | recipe_step(5, OP_STORE, 0),
+                          6};
+constexpr Recipe kRecipe4{recipe_step(0, OP_LOAD, 1) | recipe_step(1, OP_RX, 0) | recipe_step(2, OP_XCHG, 0) |
+                              recipe_step(3, OP_RX, 0) | recipe_step(4, OP_STORE, 0),
+                          5};
+constexpr int kRecipes = 5;
+
 #ifndef QAOA_TILE_MIN_BLOCKS
 #define QAOA_TILE_MIN_BLOCKS 2  // resident CTAs per SM the register budget is sized for
 #endif
 
-template <typename real, int Q, int R, bool kW>
+template <typename real, int Q, int R, bool kW, uint64_t kRecipe = 0, int kNops = 0>
 __global__ void __launch_bounds__(1 << (Q - R), QAOA_TILE_MIN_BLOCKS) tile_kernel(const __grid_constant__ TileArgs<Q> a) {
-    using T = Tile<real, Q, R>;
+    using T = Tile<real, Q, R, true>;
     using C2 = typename T::C2;
     using WA = typename T::WA;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -878,20 +931,59 @@ __global__ void __launch_bounds__(1 << (Q - R), QAOA_TILE_MIN_BLOCKS) tile_kerne
     c.sE = sE;
     c.wK = sKw;
     c.wE = sEw;
+    const bool podd = ((__popcll(zb) + __popc(tid)) & 1) != 0;  // P of the parity form
+    c.sg = (T::kSwapOdd && podd) ? (real)-1 : (real)1;
 
     C2 v[T::NE];
     int L = 0;
     double accC = 0.0, accN = 0.0;
     bool did_expect = false;
 
-    for (int i = 0; i < a.nops; ++i) {
-        const Op op = a.ops[i];
-        switch (op.kind) {
-            case OP_SYNTH: {
+    if constexpr (kNops > 0) {
+        const C2* mix = reinterpret_cast<const C2*>(a.mix);
+        T::template for_x<kNops>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            constexpr int kind = recipe_kind(kRecipe, i);
+            constexpr int Lc = recipe_layout(kRecipe, i);
+            constexpr int Lp = i == 0 ? 0 : recipe_layout(kRecipe, i - 1);
+            if constexpr (kind == OP_SYNTH) {
                 const real amp = (real)a.init_amp;
                 T::template for_x<T::NE>([&](auto X) {
                     constexpr int x = decltype(X)::value;
-                    v[x] = T::template to_reg<x>(make_c2(amp, (real)0));
+                    const bool sw = T::kSwapOdd && (odd_parity(x) != podd);
+                    v[x] = make_c2(sw ? (real)0 : amp, sw ? amp : (real)0);
+                });
+            } else if constexpr (kind == OP_LOAD) {
+                T::template load<Lc>(v, c, tid);
+            } else if constexpr (kind == OP_XCHG) {
+                __syncthreads();
+                T::template to_smem<Lp>(v, tile, tid);
+                __syncthreads();
+                T::template from_smem<Lc>(v, tile, tid);
+            } else if constexpr (kind == OP_RX) {
+                const Op op = a.ops[i];
+                T::rx(v, op.mask, c.sg * mix[3 * op.arg + 1].x);
+            } else if constexpr (kind == OP_PHASE) {
+                T::template phase<Lc, kW>(v, c, tid, a.ops[i].arg);
+            } else if constexpr (kind == OP_EXPECT) {
+                did_expect = true;
+                T::template expect<Lc, kW>(v, c, tid, accC, accN);
+            } else if constexpr (kind == OP_CUTVAL) {
+                T::template cutval<Lc, kW>(c, tid);
+            } else if constexpr (kind == OP_STORE) {
+                T::template store<Lc>(v, c, tid);
+            }
+        });
+    }
+    for (int i = 0; kNops == 0 && i < a.nops; ++i) {
+        const Op op = a.ops[i];
+        switch (op.kind) {
+            case OP_SYNTH: {  // |+>^n in the parity form: (amp, 0), or (0, amp) where swapped
+                const real amp = (real)a.init_amp;
+                T::template for_x<T::NE>([&](auto X) {
+                    constexpr int x = decltype(X)::value;
+                    const bool sw = T::kSwapOdd && (odd_parity(x) != podd);
+                    v[x] = make_c2(sw ? (real)0 : amp, sw ? amp : (real)0);
                 });
                 L = op.layout;
                 break;
@@ -914,7 +1006,7 @@ __global__ void __launch_bounds__(1 << (Q - R), QAOA_TILE_MIN_BLOCKS) tile_kerne
                 else T::template from_smem<2>(v, tile, tid);
                 break;
             case OP_RX:
-                T::rx(v, op.mask, reinterpret_cast<const C2*>(a.mix)[3 * op.arg + 1].x);
+                T::rx(v, op.mask, c.sg * reinterpret_cast<const C2*>(a.mix)[3 * op.arg + 1].x);
                 break;
             case OP_PHASE:
                 if (L == 0) T::template phase<0, kW>(v, c, tid, op.arg);
@@ -1004,6 +1096,7 @@ __global__ void __launch_bounds__(1 << (Q - R), 1) grad_kernel(const __grid_cons
     c.sE = sE;
     c.wK = sKw;
     c.wE = sEw;
+    c.sg = (real)1;
 
     C2 v[T::NE], w[T::NE];
     int L = 0;
@@ -1093,7 +1186,7 @@ __global__ void __launch_bounds__(1 << (Q - R), 1) grad_kernel(const __grid_cons
 // Adds, in a fixed order, the per-tile adjoint partials of one pass to the per-level sums:
 // slot s of the pass belongs to level lev[s] (-1: unused); acc[level] gets the pair terms
 // (d/d beta) and acc[p + level] the gamma terms.
-__global__ void __launch_bounds__(1024) grad_reduce_kernel(const double2* __restrict__ partials, uint64_t tiles,
+static __global__ void __launch_bounds__(1024) grad_reduce_kernel(const double2* __restrict__ partials, uint64_t tiles,
                                                            int lev0, int lev1, int p, double* __restrict__ acc) {
     __shared__ double sm[4][1024];
     double r[4] = {0.0, 0.0, 0.0, 0.0};
@@ -1413,21 +1506,34 @@ __global__ void coeff_batch_kernel(const CoeffJob* __restrict__ jobs) {
     }
 }
 
-// Reverses the index order of a state in place (psi_z <-> psi_{~z}), one swap per thread.
+// Resolves the pending transforms of a state in place, one index pair (i, dim - 1 - i) per
+// step: with `parity`, the (re, im) halves of every amplitude at an odd-parity index are swapped
+// (the parity form of the forward passes; the swap is its own inverse, so the same kernel also
+// enters the form); with `complement`, psi_z <-> psi_{~z}.
 template <typename real>
-__global__ void complement_kernel(void* state, uint64_t dim) {
+__global__ void complement_kernel(void* state, uint64_t dim, int complement, int parity) {
     using C2 = typename C2T<real>::type;
     C2* s = reinterpret_cast<C2*>(state);
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < dim / 2; i += (uint64_t)gridDim.x * blockDim.x) {
-        const C2 a = s[i], b = s[dim - 1 - i];
-        s[i] = b;
-        s[dim - 1 - i] = a;
+        const uint64_t j = dim - 1 - i;
+        C2 a = s[i], b = s[j];
+        if (parity) {
+            if (__popcll(i) & 1) a = make_c2(a.y, a.x);
+            if (__popcll(j) & 1) b = make_c2(b.y, b.x);
+        }
+        if (complement) {
+            s[i] = b;
+            s[j] = a;
+        } else {
+            s[i] = a;
+            s[j] = b;
+        }
     }
 }
 
 // ---------------------------------------------------------------------------------- reductions / fill
 
-__global__ void __launch_bounds__(1024) finalize_kernel(const double2* __restrict__ partials, uint64_t count,
+static __global__ void __launch_bounds__(1024) finalize_kernel(const double2* __restrict__ partials, uint64_t count,
                                                         double2* __restrict__ out) {
     __shared__ double sc[1024], sn[1024];
     double a = 0.0, b = 0.0;

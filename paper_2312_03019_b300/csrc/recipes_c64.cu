@@ -1,0 +1,9 @@
+// recipes_c64.cu -- complex64 pass kernels specialised to the compiled pass recipes, one
+// translation unit.
+#include "kernels.cuh"
+
+#define QAOA_OWN_RECIPE_C64
+#include "instances.h"
+#undef QAOA_INSTANCE
+#define QAOA_INSTANCE template
+QAOA_RECIPE_INSTANCES(float, 13, 5)

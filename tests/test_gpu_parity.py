@@ -181,6 +181,33 @@ def test_split_calls_equal_one_call(B, prec, n):
 
 
 @pytest.mark.parametrize("prec", ["c64", "c128"])
+@pytest.mark.parametrize("n", [16, 21])
+def test_read_out_between_calls(B, prec, n):
+    """Reading the state between calls (copy out, the torch view, which resolve the pending
+    complement and the complex64 parity form) and continuing gives the oracle's state; so does
+    a caller's write through the view."""
+    import oracle
+    import torch
+    g = I.regular3(n, 9) if n % 2 == 0 else I.gnp(n, 0.3, 9)
+    gamma, beta = I.angles(4, 11)
+    beta[1] = 1.3  # |tan beta| > 1: a pending complement
+    s = B.QAOAState(g, prec)
+    s.apply_layers(gamma[:1], beta[:1])
+    mid = s.amplitudes()
+    assert np.linalg.norm(mid - oracle.qaoa_state(g, gamma[:1], beta[:1])) <= (1e-12 if prec == "c128" else 1e-5)
+    s.apply_layers(gamma[1:2], beta[1:2])
+    view = s.as_tensor()  # canonical in place
+    view.mul_(1.0)
+    torch.cuda.synchronize()
+    s.apply_layers(gamma[2:], beta[2:])
+    c, _ = s.expectation()
+    psi = s.amplitudes().astype(np.complex128)
+    s.close()
+    ref = oracle.qaoa_state(g, gamma, beta)
+    (check_c128 if prec == "c128" else check_c64)(g, c, 1.0, psi, ref)
+
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
 @pytest.mark.parametrize("n", [6, 16])
 def test_initial_state_and_zero_levels(B, prec, n):
     g = I.gnp(n, 0.5, 1)
