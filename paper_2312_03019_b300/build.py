@@ -1,15 +1,15 @@
 """Builds the in-tree CUDA library ``libqaoa_b300.so`` for sm_103a with nvcc.
 
-``python -m paper_2312_03019_b300.build [--verbose]``; the shared object lands next to this
-file, so it travels with the source tree.  ``--verbose`` adds ``-Xptxas -v`` (registers,
-spills, shared memory per kernel).
+``python -m paper_2312_03019_b300.build [--force] [--verbose]``; the shared object lands next to
+this file, so it travels with the source tree.  Units compile in parallel into ``_build/``
+(git-ignored) and only stale ones are recompiled; ``--force`` recompiles all, ``--verbose``
+recompiles all with ``-Xptxas -v`` (registers, spills, shared memory per kernel).
 """
 from __future__ import annotations
 
 import os
 import subprocess
 import sys
-import tempfile
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
@@ -32,6 +32,16 @@ def _stale() -> bool:
     return False
 
 
+def _dep_time() -> float:
+    """Newest modification time among the headers and this script (they affect every unit)."""
+    t = os.path.getmtime(os.path.abspath(__file__))
+    for h in HEADERS:
+        p = os.path.join(CSRC, h)
+        if os.path.exists(p):
+            t = max(t, os.path.getmtime(p))
+    return t
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     if not (force or verbose or _stale()):
         return LIB
@@ -41,32 +51,42 @@ def build(force: bool = False, verbose: bool = False) -> str:
              "-fPIC,-O2"]
     if verbose:
         flags += ["-Xptxas", "-v"]
-    flags += os.environ.get("QAOA_NVCC_EXTRA", "").split()
-    with tempfile.TemporaryDirectory(prefix="qaoa_build_") as tmp:
-        objs, procs = [], []
-        for src in SOURCES:
-            obj = os.path.join(tmp, src + ".o")
-            objs.append(obj)
-            procs.append((src, subprocess.Popen([nvcc, *flags, "-c", os.path.join(CSRC, src), "-o", obj],
-                                                stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)))
-        failed = False
-        for src, pr in procs:
-            out, _ = pr.communicate()
-            if pr.returncode != 0:
-                failed = True
-                sys.stderr.write(out)
-            elif verbose:
-                sys.stderr.write(out)
-        if failed:
-            raise RuntimeError("nvcc failed building libqaoa_b300.so")
-        r = subprocess.run([nvcc, *ARCH, "-shared", "-o", LIB + ".tmp", *objs], capture_output=True, text=True)
-        if r.returncode != 0:
-            sys.stderr.write(r.stdout + r.stderr)
-            raise RuntimeError("nvcc failed linking libqaoa_b300.so")
+    extra = os.environ.get("QAOA_NVCC_EXTRA", "").split()
+    flags += extra
+    # objects are kept (per flag set) so that a change to one unit recompiles only that unit
+    objdir = os.path.join(HERE, "_build", "extra" if extra else "default")
+    os.makedirs(objdir, exist_ok=True)
+    dep_t = _dep_time()
+    objs, procs = [], []
+    for src in SOURCES:
+        srcp = os.path.join(CSRC, src)
+        obj = os.path.join(objdir, src + ".o")
+        objs.append(obj)
+        fresh = os.path.exists(obj) and os.path.getmtime(obj) >= max(dep_t, os.path.getmtime(srcp))
+        if fresh and not (force or verbose or extra):
+            continue
+        procs.append((obj, subprocess.Popen([nvcc, *flags, "-c", srcp, "-o", obj + ".tmp"],
+                                            stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)))
+    failed = False
+    for obj, pr in procs:
+        out, _ = pr.communicate()
+        if pr.returncode != 0:
+            failed = True
+            sys.stderr.write(out)
+            continue
+        os.replace(obj + ".tmp", obj)
+        if verbose:
+            sys.stderr.write(out)
+    if failed:
+        raise RuntimeError("nvcc failed building libqaoa_b300.so")
+    r = subprocess.run([nvcc, *ARCH, "-shared", "-o", LIB + ".tmp", *objs], capture_output=True, text=True)
+    if r.returncode != 0:
+        sys.stderr.write(r.stdout + r.stderr)
+        raise RuntimeError("nvcc failed linking libqaoa_b300.so")
     os.replace(LIB + ".tmp", LIB)
     return LIB
 
 
 if __name__ == "__main__":
-    build(force=True, verbose="--verbose" in sys.argv)
+    build(force="--force" in sys.argv, verbose="--verbose" in sys.argv)
     print(LIB)

@@ -17,28 +17,53 @@ TileConfig tile_config_for(int prec) {
     return TileConfig{12, 4, 4, 17};
 }
 
+// Groups for n qubits.  Group 0 holds a contiguous run [0, r) of the lowest bits (its tiles are
+// rows of 2^r amplitudes) and the other groups hold at most Q - cmin bits each (their tiles keep
+// >= cmin contiguous row bits).  The bits at or above the 2 MiB page boundary are dealt evenly
+// over all groups, group 0 included (it gives up its top low bits for them, keeping r >= 8):
+// a tile then touches 2^(its group's share) pages, and that count, not the row length, limits the
+// copy rate of the scattered tiles of large states.  The remaining high groups' page bits are
+// dealt round robin from the top and the mid bits (between the low run and the page boundary)
+// go to the smallest group each.
 std::vector<Group> make_groups(int n, const TileConfig& tc) {
     std::vector<Group> g(1);
-    for (int b = 0; b < std::min(n, tc.Q); ++b) g[0].bits.push_back(b);
-    const int rest = n - tc.Q;
-    if (rest > 0) {
-        const int cap = tc.Q - tc.cmin;
-        const int ng = (rest + cap - 1) / cap;
-        g.resize(1 + ng);
-        int i = 0;
-        for (int b = n - 1; b >= tc.Q; --b, ++i) g[1 + i % ng].bits.push_back(b);
-        for (int k = 1; k <= ng; ++k) std::sort(g[k].bits.begin(), g[k].bits.end());
+    if (n <= tc.Q) {
+        for (int b = 0; b < n; ++b) g[0].bits.push_back(b);
+        return g;
     }
+    const int cap = tc.Q - tc.cmin;
+    const int ng = (n - tc.Q + cap - 1) / cap;  // high groups
+    g.resize(1 + ng);
+    const int pb = std::max(tc.page_bit, tc.Q);
+    const int np = std::max(0, n - pb);  // bits [pb, n)
+    const int k0 = std::min(np / (ng + 1), tc.Q - kMinLowRun);
+    const int r = tc.Q - k0;
+    for (int b = 0; b < r; ++b) g[0].bits.push_back(b);
+    for (int b = pb; b < pb + k0; ++b) g[0].bits.push_back(b);
+    int i = 0;
+    for (int b = n - 1; b >= pb + k0; --b, ++i) g[1 + i % ng].bits.push_back(b);
+    for (int b = r; b < std::min(pb, n); ++b) {
+        int best = 1;
+        for (int k = 2; k <= ng; ++k)
+            if (g[k].size() < g[best].size()) best = k;
+        g[best].bits.push_back(b);
+    }
+    for (auto& x : g) std::sort(x.bits.begin(), x.bits.end());
     return g;
 }
 
+// Tile of a group: rows of 2^c' contiguous amplitudes plus the group's remaining bits.  Group 0
+// (which holds bit 0) has c' = the length of its run of low bits and applies RX to every tile
+// bit; another group has c' = Q - size and applies RX to its own bits only.
 Geometry group_geometry(const Group& g, const TileConfig& tc) {
     Geometry geo;
     const bool low = !g.bits.empty() && g.bits[0] == 0;
-    geo.cprime = low ? tc.Q : tc.Q - g.size();
+    int run = 0;
+    if (low)
+        while (run < g.size() && g.bits[run] == run) ++run;
+    geo.cprime = low ? run : tc.Q - g.size();
     for (int u = 0; u < geo.cprime; ++u) geo.gpos[u] = u;
-    if (!low)
-        for (int j = 0; j < g.size(); ++j) geo.gpos[geo.cprime + j] = g.bits[j];
+    for (int j = low ? run : 0, u = geo.cprime; j < g.size(); ++j, ++u) geo.gpos[u] = g.bits[j];
     return geo;
 }
 
@@ -51,8 +76,8 @@ Geometry low_geometry(const TileConfig& tc) {
 
 uint32_t group_target_mask(const Group& g, const TileConfig& tc) {
     const uint32_t all = (1u << tc.Q) - 1u;
+    if (!g.bits.empty() && g.bits[0] == 0) return all;  // group 0: every tile bit
     const Geometry geo = group_geometry(g, tc);
-    if (geo.cprime == tc.Q) return all;
     return all & ~((1u << geo.cprime) - 1u);
 }
 

@@ -37,6 +37,7 @@ constexpr int kLayerChunk = 64;  // levels per coefficient table upload
 constexpr int kMaxEdges = kMaxN * (kMaxN - 1) / 2;
 constexpr int kMaxLocEdges = 13 * 12 / 2;  // edges among the Q <= 13 local bits of a tile
 constexpr int kWSlots = 4;                 // weighted sums per pass: the value and up to 3 levels
+constexpr int kMinLowRun = 8;              // contiguous low bits group 0 keeps (2 KiB rows complex64)
 
 enum OpKind : uint8_t {
     OP_NONE = 0,
@@ -109,14 +110,14 @@ struct Plan {
     std::vector<Pass> passes;
 };
 
-// Mixer groups for n >= Q qubits: group 0 = bits [0, Q); the bits of [Q, n) are dealt from the
-// top down, round robin, into balanced groups of at most Q - cmin bits.  Dealing spreads the
-// bits above page_bit evenly, so no tile's rows fall into more distinct 2 MiB pages than
-// necessary (rows of a tile whose group bits all lie above page_bit sit in 2^|G| different
-// pages, which measurably slows the pass down).
+// Mixer groups for n >= Q qubits: group 0 = a run [0, r) of low bits (r >= kMinLowRun) plus its
+// share of the bits at or above page_bit; the other groups hold at most Q - cmin bits each.  The
+// bits at or above page_bit are spread evenly over all groups, so no tile's rows fall into more
+// distinct 2 MiB pages than necessary (a tile with k group bits above page_bit touches 2^k
+// pages, which measurably slows the pass down once 2^k reaches the hundreds).
 std::vector<Group> make_groups(int n, const TileConfig& tc);
 Geometry group_geometry(const Group& g, const TileConfig& tc);
-// Geometry of group 0 (the contiguous tile of bits [0, Q)); allocates nothing.
+// Geometry of the contiguous tile of bits [0, Q); allocates nothing.
 Geometry low_geometry(const TileConfig& tc);
 uint32_t group_target_mask(const Group& g, const TileConfig& tc);
 
@@ -130,7 +131,7 @@ Plan plan_levels(int n, const TileConfig& tc, int levels, bool synth_first, bool
 // The last pass stores nothing.
 Plan plan_backward(int n, const TileConfig& tc, int levels);
 
-// Single pass over group 0 that only evaluates (no store): expectation or cut values.
+// Single pass over one group's tiles that only evaluates (no store): expectation or cut values.
 Plan plan_readonly(int n, const TileConfig& tc, bool synth, uint8_t kind, int group = 0,
                    int layout = 0);
 

@@ -99,18 +99,25 @@ def test_plan_applies_each_rx_once_per_level(lib, prec, n, p):
         pytest.skip("small-state kernel")
     d = lib.qaoa_plan_describe(n, prec, p)
     Q, R, cmin, groups, passes = _parse_plan(d)
-    # groups partition [0, n); group 0 is [0, Q); high groups leave >= cmin row bits and hold
-    # balanced numbers of bits, and of bits above the 2 MiB page boundary
+    # groups partition [0, n); group 0 is a run [0, r) with r >= 8 plus bits at or above the
+    # 2 MiB page boundary; high groups leave >= cmin row bits; the page-boundary bits are spread
+    # evenly over all groups (group 0's share capped by r >= 8)
     cover = []
     for bits in groups:
         cover += bits
     assert sorted(cover) == list(range(n))
-    assert groups[0] == list(range(Q))
+    page_bit = 18 if prec == "c64" else 17
+    g0 = groups[0]
+    r = 0
+    while r < len(g0) and g0[r] == r:
+        r += 1
+    assert len(g0) == Q and r >= 8 and all(b >= page_bit for b in g0[r:])
     sizes = [len(b) for b in groups[1:]]
     assert all(sz <= Q - cmin for sz in sizes) and max(sizes) - min(sizes) <= 1
-    page_bit = 18 if prec == "c64" else 17
-    high = [sum(1 for b in bits if b >= page_bit) for bits in groups[1:]]
-    assert max(high) - min(high) <= 1
+    high = [sum(1 for b in bits if b >= page_bit) for bits in groups]
+    assert max(high[1:]) - min(high[1:]) <= 1
+    assert high[0] == min(Q - 8, max(0, n - max(page_bit, Q)) // len(groups))
+    assert max(high) - min(high) <= 1 or high[0] == Q - 8
     g = len(groups)
     assert len(passes) == p * (g - 1) + 1
 
@@ -121,9 +128,13 @@ def test_plan_applies_each_rx_once_per_level(lib, prec, n, p):
     events = []  # sequence of ("rx", level) / ("phase", level)
     for pi, (grp, ops) in enumerate(passes):
         bits = groups[grp]
-        cprime = Q if grp == 0 else Q - len(bits)
-        gpos = list(range(Q)) if grp == 0 else list(range(cprime)) + bits
-        target = (1 << Q) - 1 if grp == 0 else ((1 << Q) - 1) & ~((1 << cprime) - 1)
+        if grp == 0:  # rows of the low run, then group 0's page-boundary bits
+            gpos = list(bits)
+            target = (1 << Q) - 1
+        else:
+            cprime = Q - len(bits)
+            gpos = list(range(cprime)) + bits
+            target = ((1 << Q) - 1) & ~((1 << cprime) - 1)
         kind0, lay0, _ = ops[0]
         assert kind0 == (2 if pi == 0 else 1)  # synthesise |+> only in the first pass
         assert lay0 in (0, 1)
