@@ -32,9 +32,13 @@ from paper_2312_03019_b300 import inputs as I  # noqa: E402
 
 METRIC = "QAOA layers/s"
 UNIT = "layers/s"
-# DRAM bytes (read + write) per launch of the dominant pass kernel from an ncu capture of the
-# same kernel build; None when the kernel changed since it was captured.
-NCU_TRAFFIC_BYTES_PER_LAUNCH = None
+# DRAM bytes (read + write) per launch of the read+write pass kernel from an ncu capture of the
+# same kernel build (None when the kernel changed since it was captured), for 2^n amplitudes.
+# Captured at n = 28 (the full-size state is too large for a multi-metric capture): 4.2320 GB
+# per launch (2.1476 GB read + 2.0844 GB written, the same for the group-0, fused and last
+# passes), against 4.2950 GB algorithmic; a pass reads and writes every amplitude once, so the
+# traffic scales with 2^n.
+NCU_TRAFFIC_BYTES_PER_AMPLITUDE = 4.2320e9 / 2 ** 28
 
 
 def parse_args():
@@ -46,7 +50,9 @@ def parse_args():
     ap.add_argument("--n", type=int, default=33)
     ap.add_argument("--p", type=int, default=8)
     ap.add_argument("--prec", choices=["c64", "c128"], default="c64")
-    ap.add_argument("--cpu-sample-n", type=int, default=24)
+    ap.add_argument("--cpu-sample-n", type=int, default=26)
+    ap.add_argument("--cpu-sample-seconds", type=float, default=10.0,
+                    help="the CPU baseline times oracle levels at --cpu-sample-n until this much time has passed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--weighted", action="store_true",
@@ -158,19 +164,24 @@ def gates_per_level(g):
     return 3 * g.m + 1 + g.n  # CNOT-RZ-CNOT per edge, global phase, one RX per qubit
 
 
-def oracle_layers_per_s(n_target: int, m_target_graph, n_s: int):
-    """Oracle layers/s at n_target extrapolated from one timed level at n_s: every gate streams
-    the whole state, so time scales with 2^n times the gate count."""
+def oracle_layers_per_s(n_target: int, m_target_graph, n_s: int, min_seconds: float):
+    """Oracle layers/s at n_target extrapolated from levels timed at n_s (as many as fit in
+    about min_seconds, at most 8): every gate streams the whole state, so time scales with 2^n
+    times the gate count."""
     import oracle
-    t, gs = oracle_level_seconds(n_s)
+    levels, total, gs = 0, 0.0, None
+    while levels < 8 and (levels == 0 or total < min_seconds):
+        t, gs = oracle_level_seconds(n_s)
+        levels += 1
+        total += t
     scale = (2.0 ** (n_target - n_s)) * gates_per_level(m_target_graph) / gates_per_level(gs)
-    return 1.0 / (t * scale), t, gs, oracle.threads()
+    return levels / (total * scale), total, levels, gs, oracle.threads()
 
 
 def cpu_baseline_block(args, g_target):
-    v, t, gs, cores = oracle_layers_per_s(g_target.n, g_target, args.cpu_sample_n)
+    v, t, levels, gs, cores = oracle_layers_per_s(g_target.n, g_target, args.cpu_sample_n, args.cpu_sample_seconds)
     return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": (f"one oracle level (gate-level complex128, Algorithm 1) on the same graph family at "
+            "sample": (f"{levels} oracle levels (gate-level complex128, Algorithm 1) on the same graph family at "
                        f"n={gs.n} (|E|={gs.m}) took {t:.2f} s on {cores} threads; scaled to n={g_target.n} "
                        f"by 2^n x gate count ({gates_per_level(gs)} -> {gates_per_level(g_target)} gates/level)")}
 
@@ -327,7 +338,9 @@ def run_ours(args):
         bytes_per_launch = 2.0 * elem * (1 << g.n)
         achieved = bytes_per_launch / per_launch_s / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": NCU_TRAFFIC_BYTES_PER_LAUNCH, "peak_kind": f"{peak_kind} copy bandwidth",
+                "traffic": (NCU_TRAFFIC_BYTES_PER_AMPLITUDE * (1 << g.n)
+                            if NCU_TRAFFIC_BYTES_PER_AMPLITUDE and args.prec == "c64" and g.weights is None else None),
+                "peak_kind": f"{peak_kind} copy bandwidth",
                 "kernel": "tile_kernel (read+write state pass)",
                 "bytes_per_launch": bytes_per_launch, "launch_ms": per_launch_s * 1e3,
                 "launches": prof["pass_launches"]}
