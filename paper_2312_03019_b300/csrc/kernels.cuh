@@ -890,8 +890,22 @@ constexpr int kRecipes = 5;
 #define QAOA_TILE_MIN_BLOCKS 2  // resident CTAs per SM the register budget is sized for
 #endif
 
+// Resident CTAs per SM a pass kernel's register budget is sized for.  Two (128 registers a
+// thread) by default; three (85) for the complex64 recipes that measured faster with 24 warps
+// per SM despite a few spilled registers (first, group-0 and last pass; the fused boundary pass,
+// with two RX sets and the phase live at once, is faster at two).
+template <typename real>
+__host__ __device__ constexpr int tile_min_blocks(uint64_t recipe, int nops) {
+    if (sizeof(real) == 4 && nops > 0 &&
+        ((recipe == kRecipe0.code && nops == kRecipe0.nops) || (recipe == kRecipe1.code && nops == kRecipe1.nops) ||
+         (recipe == kRecipe3.code && nops == kRecipe3.nops)))
+        return 3;
+    return QAOA_TILE_MIN_BLOCKS;
+}
+
 template <typename real, int Q, int R, bool kW, uint64_t kRecipe = 0, int kNops = 0>
-__global__ void __launch_bounds__(1 << (Q - R), QAOA_TILE_MIN_BLOCKS) tile_kernel(const __grid_constant__ TileArgs<Q> a) {
+__global__ void __launch_bounds__(1 << (Q - R), tile_min_blocks<real>(kRecipe, kNops))
+    tile_kernel(const __grid_constant__ TileArgs<Q> a) {
     using T = Tile<real, Q, R, true>;
     using C2 = typename T::C2;
     using WA = typename T::WA;
