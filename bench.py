@@ -9,6 +9,7 @@ levels, complex64 state of 2^33 amplitudes (64 GiB), larger than L2, so no L2 fl
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--n 33] [--p 8]
   python bench.py --serve      # request-serving mode (qaoa_submit / qaoa_poll), its own JSON line
+  python bench.py --grad       # adjoint-gradient mode (qaoa_gradient), its own JSON line
 
 Prints ONE JSON line on rank 0.  `--impl reference` times the CPU oracle (gate-level complex128
 simulator, the paper's Algorithm 1) on a bounded sample of the same workload on the host cores.
@@ -57,6 +58,8 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--weighted", action="store_true",
                     help="edge weights U[0.1, 2] on the same graph (Algorithm 2 path), for context")
+    ap.add_argument("--grad", action="store_true",
+                    help="gradient mode: d<C>/d(gamma, beta) by qaoa_gradient on G(24, 0.5), p = 10")
     ap.add_argument("--serve", action="store_true",
                     help="serving mode: an open-loop Poisson request stream through qaoa_submit/qaoa_poll")
     ap.add_argument("--serve-requests", type=int, default=4096)
@@ -424,6 +427,59 @@ def serve_stream(B, reqs, cfg):
             "stats": stats}, done
 
 
+def run_grad(args):
+    """Adjoint gradients per second on G(24, 0.5), seed 0, p = 10 (20 parameters), complex64,
+    through qaoa_gradient (forward levels, lambda = C psi, reverse sweep; host-synchronous per
+    call), beside the forward evaluation of the same circuit and the 4p forward evaluations
+    central differences would need."""
+    import torch
+
+    if not torch.cuda.is_available():
+        raise SystemExit("the gradient benchmark needs a CUDA device")
+    from paper_2312_03019_b300 import build as bld
+    bld.build()
+    from paper_2312_03019_b300 import binding as B
+
+    g, gamma, beta = I.workload_gnp24_p10()
+    s = B.QAOAState(g, args.prec)
+    work = torch.empty(s.nbytes, dtype=torch.uint8, device="cuda")
+    warm, K = max(3, args.warmup), max(args.steps, 10)
+
+    def grad():
+        return B.qaoa_gradient(s.handle, gamma, beta, work.data_ptr(), s.nbytes)
+
+    def forward():
+        s.reset()
+        s.apply_layers(gamma, beta)
+        return s.expectation()
+
+    for _ in range(warm):
+        grad()
+        forward()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        c, dg, db = grad()
+    t_grad = (time.perf_counter() - t0) / K
+    t0 = time.perf_counter()
+    for _ in range(K):
+        forward()
+    t_fwd = (time.perf_counter() - t0) / K
+    p = len(gamma)
+    rec = {"metric": "QAOA adjoint gradients/s", "value": 1.0 / t_grad, "unit": "gradients/s", "higher_is_better": True,
+           "n_gpus": 1, "steps": K, "warmup": warm, "mode": "grad", "dtype": "f32" if args.prec == "c64" else "f64",
+           "data": "synthetic",
+           "config": {"workload": f"G(24, 0.5) seed 0, |E|={g.m}, p={p} seeded levels ({2 * p} parameters), "
+                                  f"{'complex64' if args.prec == 'c64' else 'complex128'}, host-timed calls"},
+           "ms_per_gradient": t_grad * 1e3, "ms_per_forward": t_fwd * 1e3,
+           "gradient_over_forward": t_grad / t_fwd,
+           "speedup_vs_central_differences": 4 * p * t_fwd / t_grad,
+           "expectation": c}
+    s.close()
+    print(json.dumps(rec), flush=True)
+    return 0
+
+
 def run_serve(args):
     import torch
 
@@ -458,6 +514,8 @@ def main():
     args = parse_args()
     if args.serve:
         return run_serve(args)
+    if args.grad:
+        return run_grad(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
