@@ -309,20 +309,28 @@ template <typename real>
 using TileFn = void (*)(TileArgs<PrecTraits<real>::Q>);
 
 // The straight-line instantiation of recipe r (unit weights).
+template <typename real, int r>
+constexpr TileFn<real> recipe_fn() {
+    return tile_kernel<real, PrecTraits<real>::Q, PrecTraits<real>::R, false, recipe_def(r).code, recipe_def(r).nops,
+                       recipe_masks<real>(r)>;
+}
+
 template <typename real>
 TileFn<real> recipe_kernel(int r) {
-    constexpr int Q = PrecTraits<real>::Q, R = PrecTraits<real>::R;
     switch (r) {
-        case 0: return tile_kernel<real, Q, R, false, kRecipe0.code, kRecipe0.nops>;
-        case 1: return tile_kernel<real, Q, R, false, kRecipe1.code, kRecipe1.nops>;
-        case 2: return tile_kernel<real, Q, R, false, kRecipe2.code, kRecipe2.nops>;
-        case 3: return tile_kernel<real, Q, R, false, kRecipe3.code, kRecipe3.nops>;
-        default: return tile_kernel<real, Q, R, false, kRecipe4.code, kRecipe4.nops>;
+        case 0: return recipe_fn<real, 0>();
+        case 1: return recipe_fn<real, 1>();
+        case 2: return recipe_fn<real, 2>();
+        case 3: return recipe_fn<real, 3>();
+        case 4: return recipe_fn<real, 4>();
+        case 5: return recipe_fn<real, 5>();
+        case 6: return recipe_fn<real, 6>();
+        default: return recipe_fn<real, 7>();
     }
 }
 
-// The pass kernel for a program: its recipe instantiation when one matches, else the
-// interpreting one.
+// The pass kernel for a program: a recipe instantiation when one matches (those with compiled-in
+// masks first, and only when the program's masks are exactly those), else the interpreting one.
 template <typename real>
 TileFn<real> pick_tile_kernel(const TileArgs<PrecTraits<real>::Q>& a, bool weighted) {
     constexpr int Q = PrecTraits<real>::Q, R = PrecTraits<real>::R;
@@ -330,9 +338,17 @@ TileFn<real> pick_tile_kernel(const TileArgs<PrecTraits<real>::Q>& a, bool weigh
     if (a.nops <= 10) {
         uint64_t code = 0;
         for (int i = 0; i < a.nops; ++i) code |= recipe_step(i, a.ops[i].kind, a.ops[i].layout);
-        const Recipe rs[kRecipes] = {kRecipe0, kRecipe1, kRecipe2, kRecipe3, kRecipe4};
-        for (int r = 0; r < kRecipes; ++r)
-            if (rs[r].nops == a.nops && rs[r].code == code) return recipe_kernel<real>(r);
+        const int order[] = {1, 5, 7, 0, 2, 3, 4};  // the full-mask fused pass (6) spills: not used
+        for (int r : order) {
+            const Recipe d = recipe_def(r);
+            if (d.nops != a.nops || d.code != code) continue;
+            bool masks_ok = true;
+            for (int i = 0; i < a.nops; ++i) {
+                const uint32_t fm = (uint32_t)((recipe_masks<real>(r) >> (6 * i)) & 63u);
+                if ((fm & 32u) && a.ops[i].mask != (fm & 31u)) masks_ok = false;
+            }
+            if (masks_ok) return recipe_kernel<real>(r);
+        }
     }
     return tile_kernel<real, Q, R, false>;
 }

@@ -16,13 +16,20 @@
     QAOA_INSTANCE __global__ void tile_kernel<real, Q, R, true, 0, 0>(const __grid_constant__ TileArgs<Q>);                 \
     }
 
-#define QAOA_RECIPE_INSTANCES(real, Q, R)                                                                \
-    namespace qaoa {                                                                                      \
-    QAOA_INSTANCE __global__ void tile_kernel<real, Q, R, false, kRecipe0.code, kRecipe0.nops>(const __grid_constant__ TileArgs<Q>); \
-    QAOA_INSTANCE __global__ void tile_kernel<real, Q, R, false, kRecipe1.code, kRecipe1.nops>(const __grid_constant__ TileArgs<Q>); \
-    QAOA_INSTANCE __global__ void tile_kernel<real, Q, R, false, kRecipe2.code, kRecipe2.nops>(const __grid_constant__ TileArgs<Q>); \
-    QAOA_INSTANCE __global__ void tile_kernel<real, Q, R, false, kRecipe3.code, kRecipe3.nops>(const __grid_constant__ TileArgs<Q>); \
-    QAOA_INSTANCE __global__ void tile_kernel<real, Q, R, false, kRecipe4.code, kRecipe4.nops>(const __grid_constant__ TileArgs<Q>); \
+#define QAOA_RECIPE_ONE(real, Q, R, r)                                                                    \
+    QAOA_INSTANCE __global__ void tile_kernel<real, Q, R, false, recipe_def(r).code, recipe_def(r).nops,     \
+                                              recipe_masks<real>(r)>(const __grid_constant__ TileArgs<Q>);
+
+#define QAOA_RECIPE_INSTANCES(real, Q, R)                                                                 \
+    namespace qaoa {                                                                                       \
+    QAOA_RECIPE_ONE(real, Q, R, 0)                                                                         \
+    QAOA_RECIPE_ONE(real, Q, R, 1)                                                                         \
+    QAOA_RECIPE_ONE(real, Q, R, 2)                                                                         \
+    QAOA_RECIPE_ONE(real, Q, R, 3)                                                                         \
+    QAOA_RECIPE_ONE(real, Q, R, 4)                                                                         \
+    QAOA_RECIPE_ONE(real, Q, R, 5)                                                                         \
+    QAOA_RECIPE_ONE(real, Q, R, 6)                                                                         \
+    QAOA_RECIPE_ONE(real, Q, R, 7)                                                                         \
     }
 
 #define QAOA_GRAD_INSTANCES(real, Q, R)                                              \

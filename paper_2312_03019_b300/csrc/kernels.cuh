@@ -833,6 +833,39 @@ struct Tile {
         }
     }
 
+    // RX on the register bits of a compile-time mask only (no butterflies for the other bits)
+    template <uint32_t kMask>
+    static __device__ __forceinline__ void rx_fixed(C2 (&v)[NE], real t) {
+        for_x<R>([&](auto J) {
+            constexpr int j = decltype(J)::value;
+            if constexpr ((kMask >> j) & 1u) {
+                const real T = t, nT = -t;
+                for_x<NE>([&](auto X) {
+                    constexpr int x = decltype(X)::value;
+                    if constexpr (!(x & (1 << j))) {
+                        constexpr int y = x | (1 << j);
+                        if constexpr (kSwapOdd) {
+                            const C2 cp = make_c2(T, nT), cm = make_c2(nT, T);
+                            if constexpr (!odd_parity(x)) {
+                                const C2 n0 = v[x], s0 = v[y];
+                                v[x] = ffma2(cp, s0, n0);
+                                v[y] = ffma2(cm, n0, s0);
+                            } else {
+                                const C2 n0 = v[y], s0 = v[x];
+                                v[y] = ffma2(cp, s0, n0);
+                                v[x] = ffma2(cm, n0, s0);
+                            }
+                        } else {
+                            const C2 p = v[x], q = v[y];
+                            v[x] = make_c2(fma(T, q.y, p.x), fma(nT, q.x, p.y));
+                            v[y] = make_c2(fma(T, p.y, q.x), fma(nT, p.x, q.y));
+                        }
+                    }
+                });
+            }
+        });
+    }
+
     static __device__ __forceinline__ void rx(C2 (&v)[NE], uint32_t mask, real t) {
         if (mask == (1u << R) - 1u) rx_bits<true>(v, mask, t);
         else rx_bits<false>(v, mask, t);
@@ -864,27 +897,55 @@ struct Recipe {
     uint64_t code;
     int nops;
 };
+// Compiled-in RX masks of a recipe, 6 bits per op (bit 5 set: the op's register mask is bits
+// 0..4; clear: the mask is a runtime argument).
+__host__ __device__ constexpr uint64_t fixed_mask(int i, uint32_t m) { return (uint64_t)(32u | m) << (6 * i); }
 // The pass programs of the tiled plans with three or more groups (complex64 n >= 23, complex128
-// n >= 20): first pass, group-0 pass, fused boundary pass, last pass, and complex128's
+// n >= 20): 0 first pass, 1 group-0 pass, 2 fused boundary pass, 3 last pass, 4 complex128's
 // two-exchange high-group pass.
-constexpr Recipe kRecipe0{recipe_step(0, OP_SYNTH, 1) | recipe_step(1, OP_PHASE, 0) | recipe_step(2, OP_RX, 0) |
-                              recipe_step(3, OP_XCHG, 0) | recipe_step(4, OP_RX, 0) | recipe_step(5, OP_STORE, 0),
-                          6};
-constexpr Recipe kRecipe1{recipe_step(0, OP_LOAD, 1) | recipe_step(1, OP_RX, 0) | recipe_step(2, OP_XCHG, 2) |
-                              recipe_step(3, OP_RX, 0) | recipe_step(4, OP_XCHG, 0) | recipe_step(5, OP_RX, 0) |
-                              recipe_step(6, OP_STORE, 0),
-                          7};
-constexpr Recipe kRecipe2{recipe_step(0, OP_LOAD, 0) | recipe_step(1, OP_RX, 0) | recipe_step(2, OP_XCHG, 1) |
-                              recipe_step(3, OP_RX, 0) | recipe_step(4, OP_PHASE, 0) | recipe_step(5, OP_RX, 0) |
-                              recipe_step(6, OP_XCHG, 0) | recipe_step(7, OP_RX, 0) | recipe_step(8, OP_STORE, 0),
-                          9};
-constexpr Recipe kRecipe3{recipe_step(0, OP_LOAD, 1) | recipe_step(1, OP_RX, 0) | recipe_step(2, OP_XCHG, 0) |
-                              recipe_step(3, OP_RX, 0) | recipe_step(4, OP_EXPECT, 0) | recipe_step(5, OP_STORE, 0),
-                          6};
-constexpr Recipe kRecipe4{recipe_step(0, OP_LOAD, 1) | recipe_step(1, OP_RX, 0) | recipe_step(2, OP_XCHG, 0) |
-                              recipe_step(3, OP_RX, 0) | recipe_step(4, OP_STORE, 0),
-                          5};
-constexpr int kRecipes = 5;
+__host__ __device__ constexpr Recipe base_recipe(int r) {
+    return r == 0 ? Recipe{recipe_step(0, OP_SYNTH, 1) | recipe_step(1, OP_PHASE, 0) | recipe_step(2, OP_RX, 0) |
+                               recipe_step(3, OP_XCHG, 0) | recipe_step(4, OP_RX, 0) | recipe_step(5, OP_STORE, 0),
+                           6}
+         : r == 1 ? Recipe{recipe_step(0, OP_LOAD, 1) | recipe_step(1, OP_RX, 0) | recipe_step(2, OP_XCHG, 2) |
+                               recipe_step(3, OP_RX, 0) | recipe_step(4, OP_XCHG, 0) | recipe_step(5, OP_RX, 0) |
+                               recipe_step(6, OP_STORE, 0),
+                           7}
+         : r == 2 ? Recipe{recipe_step(0, OP_LOAD, 0) | recipe_step(1, OP_RX, 0) | recipe_step(2, OP_XCHG, 1) |
+                               recipe_step(3, OP_RX, 0) | recipe_step(4, OP_PHASE, 0) | recipe_step(5, OP_RX, 0) |
+                               recipe_step(6, OP_XCHG, 0) | recipe_step(7, OP_RX, 0) | recipe_step(8, OP_STORE, 0),
+                           9}
+         : r == 3 ? Recipe{recipe_step(0, OP_LOAD, 1) | recipe_step(1, OP_RX, 0) | recipe_step(2, OP_XCHG, 0) |
+                               recipe_step(3, OP_RX, 0) | recipe_step(4, OP_EXPECT, 0) | recipe_step(5, OP_STORE, 0),
+                           6}
+                  : Recipe{recipe_step(0, OP_LOAD, 1) | recipe_step(1, OP_RX, 0) | recipe_step(2, OP_XCHG, 0) |
+                               recipe_step(3, OP_RX, 0) | recipe_step(4, OP_STORE, 0),
+                           5};
+}
+constexpr Recipe kRecipe0 = base_recipe(0), kRecipe1 = base_recipe(1), kRecipe2 = base_recipe(2),
+                 kRecipe3 = base_recipe(3), kRecipe4 = base_recipe(4);
+// Instantiations 5..7 are recipes 0, 2 and 3 again with every RX mask compiled in as full (the
+// high-group passes of 10-bit complex64 / 8-bit complex128 groups, as at n = 33); the host
+// tries them before the runtime-mask versions.
+constexpr int kRecipes = 8;
+__host__ __device__ constexpr Recipe recipe_def(int r) { return base_recipe(r == 5 ? 0 : r == 6 ? 2 : r == 7 ? 3 : r); }
+// Compiled-in masks.  The group-0 pass (recipe 1) always covers its Q bits with the same masks:
+// complex64 (R = 5) layouts 1, 2, 0 take local bits 3..7, 0..2 (the layout-2 op skips bits 3, 4,
+// done already), 8..12; complex128 (R = 4) takes 4..7, 0..3, 8..11.  Masks compiled in remove
+// the butterflies of skipped bits and the per-bit selects, which measurably cost register moves.
+template <typename real>
+__host__ __device__ constexpr uint64_t recipe_masks(int r) {
+    const uint32_t full = sizeof(real) == 4 ? 31u : 15u;
+    if (r == 1)
+        return sizeof(real) == 4 ? (fixed_mask(1, 31) | fixed_mask(3, 7) | fixed_mask(5, 31))
+                                 : (fixed_mask(1, 15) | fixed_mask(3, 15) | fixed_mask(5, 15));
+    if (r < 5) return 0;
+    const Recipe d = recipe_def(r);
+    uint64_t m = 0;
+    for (int i = 0; i < d.nops; ++i)
+        if (recipe_kind(d.code, i) == OP_RX) m |= fixed_mask(i, full);
+    return m;
+}
 
 #ifndef QAOA_TILE_MIN_BLOCKS
 #define QAOA_TILE_MIN_BLOCKS 2  // resident CTAs per SM the register budget is sized for
@@ -896,14 +957,14 @@ constexpr int kRecipes = 5;
 // with two RX sets and the phase live at once, is faster at two).
 template <typename real>
 __host__ __device__ constexpr int tile_min_blocks(uint64_t recipe, int nops) {
-    if (sizeof(real) == 4 && nops > 0 &&
-        ((recipe == kRecipe0.code && nops == kRecipe0.nops) || (recipe == kRecipe1.code && nops == kRecipe1.nops) ||
-         (recipe == kRecipe3.code && nops == kRecipe3.nops)))
-        return 3;
+    // (the first-pass, group-0 and last-pass programs, with runtime or compiled-in masks)
+    if (sizeof(real) == 4 && nops > 0)
+        for (int r : {0, 1, 3})
+            if (recipe == base_recipe(r).code && nops == base_recipe(r).nops) return 3;
     return QAOA_TILE_MIN_BLOCKS;
 }
 
-template <typename real, int Q, int R, bool kW, uint64_t kRecipe = 0, int kNops = 0>
+template <typename real, int Q, int R, bool kW, uint64_t kRecipe = 0, int kNops = 0, uint64_t kMasks = 0>
 __global__ void __launch_bounds__(1 << (Q - R), tile_min_blocks<real>(kRecipe, kNops))
     tile_kernel(const __grid_constant__ TileArgs<Q> a) {
     using T = Tile<real, Q, R, true>;
@@ -976,7 +1037,11 @@ __global__ void __launch_bounds__(1 << (Q - R), tile_min_blocks<real>(kRecipe, k
                 T::template from_smem<Lc>(v, tile, tid);
             } else if constexpr (kind == OP_RX) {
                 const Op op = a.ops[i];
-                T::rx(v, op.mask, c.sg * mix[3 * op.arg + 1].x);
+                constexpr uint32_t fm = (uint32_t)((kMasks >> (6 * i)) & 63u);
+                if constexpr ((fm & 32u) != 0)
+                    T::template rx_fixed<(fm & 31u)>(v, c.sg * mix[3 * op.arg + 1].x);
+                else
+                    T::rx(v, op.mask, c.sg * mix[3 * op.arg + 1].x);
             } else if constexpr (kind == OP_PHASE) {
                 T::template phase<Lc, kW>(v, c, tid, a.ops[i].arg);
             } else if constexpr (kind == OP_EXPECT) {
