@@ -244,6 +244,25 @@ def run_reference(args):
     return 0
 
 
+# --------------------------------------------------------------------------------- replicas
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The largest of every rank's x (the slowest replica's time): an all-reduce MAX over the
+    process group (NCCL on the GPUs, gloo in the CPU tests), x itself on a single process."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(units_per_rank: float, seconds_max: float, world: int) -> float:
+    """Whole-job rate of `world` independent replicas: every rank's units over the slowest time."""
+    return world * units_per_rank / seconds_max
+
+
 # --------------------------------------------------------------------------------- our arm
 
 def run_ours(args):
@@ -302,11 +321,8 @@ def run_ours(args):
     prof = B.qaoa_profile_read(st.handle)
     B.qaoa_profile_enable(st.handle, False)
 
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * args.steps * args.p / (ms_max / 1e3)
+    ms_max = max_over_ranks(ms, world, dev)
+    value = replica_rate(args.steps * args.p, ms_max / 1e3, world)
 
     # end to end through the public API with host inputs and a host result
     e2e = None
@@ -326,10 +342,7 @@ def run_ours(args):
             B.qaoa_state_free(h)
         torch.cuda.synchronize(dev)
         el = time.perf_counter() - t0
-        te = torch.tensor([el], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * args.steps * args.p / float(te.item()), "unit": UNIT,
+        e2e = {"value": replica_rate(args.steps * args.p, max_over_ranks(el, world, dev), world), "unit": UNIT,
                "h2d_bytes_per_step": int(8 * g.m + 16 * args.p), "d2h_bytes_per_step": 16,
                "note": "graph and angles go host to device as kernel parameters; <C> and norm come back"}
 
