@@ -309,10 +309,27 @@ template <typename real>
 using TileFn = void (*)(TileArgs<PrecTraits<real>::Q>);
 
 // The straight-line instantiation of recipe r (unit weights).
-template <typename real, int r>
+template <typename real, int r, bool kW = false>
 constexpr TileFn<real> recipe_fn() {
-    return tile_kernel<real, PrecTraits<real>::Q, PrecTraits<real>::R, false, recipe_def(r).code, recipe_def(r).nops,
+    return tile_kernel<real, PrecTraits<real>::Q, PrecTraits<real>::R, kW, recipe_def(r).code, recipe_def(r).nops,
                        recipe_masks<real>(r)>;
+}
+
+// The weighted (complex64) instantiation of recipe r, or NULL where none is compiled.
+template <typename real>
+TileFn<real> recipe_kernel_w(int r) {
+    if constexpr (std::is_same<real, float>::value) {
+        switch (r) {
+            case 0: return recipe_fn<real, 0, true>();
+            case 1: return recipe_fn<real, 1, true>();
+            case 2: return recipe_fn<real, 2, true>();
+            case 3: return recipe_fn<real, 3, true>();
+            case 5: return recipe_fn<real, 5, true>();
+            case 7: return recipe_fn<real, 7, true>();
+            default: return nullptr;
+        }
+    }
+    return nullptr;
 }
 
 template <typename real>
@@ -334,7 +351,6 @@ TileFn<real> recipe_kernel(int r) {
 template <typename real>
 TileFn<real> pick_tile_kernel(const TileArgs<PrecTraits<real>::Q>& a, bool weighted) {
     constexpr int Q = PrecTraits<real>::Q, R = PrecTraits<real>::R;
-    if (weighted) return tile_kernel<real, Q, R, true>;
     if (a.nops <= 10) {
         uint64_t code = 0;
         for (int i = 0; i < a.nops; ++i) code |= recipe_step(i, a.ops[i].kind, a.ops[i].layout);
@@ -347,10 +363,12 @@ TileFn<real> pick_tile_kernel(const TileArgs<PrecTraits<real>::Q>& a, bool weigh
                 const uint32_t fm = (uint32_t)((recipe_masks<real>(r) >> (6 * i)) & 63u);
                 if ((fm & 32u) && a.ops[i].mask != (fm & 31u)) masks_ok = false;
             }
-            if (masks_ok) return recipe_kernel<real>(r);
+            if (!masks_ok) continue;
+            if (!weighted) return recipe_kernel<real>(r);
+            if (TileFn<real> f = recipe_kernel_w<real>(r)) return f;
         }
     }
-    return tile_kernel<real, Q, R, false>;
+    return weighted ? tile_kernel<real, Q, R, true> : tile_kernel<real, Q, R, false>;
 }
 
 template <typename real>
@@ -363,9 +381,12 @@ qaoa_status ensure_attributes() {
                                   (int)((1u << Q) * sizeof(C2))));
     CUDA_TRY(cudaFuncSetAttribute(tile_kernel<real, Q, R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)((1u << Q) * sizeof(C2))));
-    for (int r = 0; r < kRecipes; ++r)
+    for (int r = 0; r < kRecipes; ++r) {
         CUDA_TRY(cudaFuncSetAttribute(recipe_kernel<real>(r), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)((1u << Q) * sizeof(C2))));
+        if (TileFn<real> f = recipe_kernel_w<real>(r))
+            CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)((1u << Q) * sizeof(C2))));
+    }
     CUDA_TRY(cudaFuncSetAttribute(grad_kernel<real, Q, R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)((1u << Q) * sizeof(C2))));
     CUDA_TRY(cudaFuncSetAttribute(grad_kernel<real, Q, R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -16,9 +16,21 @@
     QAOA_INSTANCE __global__ void tile_kernel<real, Q, R, true, 0, 0>(const __grid_constant__ TileArgs<Q>);                 \
     }
 
-#define QAOA_RECIPE_ONE(real, Q, R, r)                                                                    \
-    QAOA_INSTANCE __global__ void tile_kernel<real, Q, R, false, recipe_def(r).code, recipe_def(r).nops,     \
+#define QAOA_RECIPE_ONE(real, Q, R, r) QAOA_RECIPE_W(real, Q, R, r, false)
+#define QAOA_RECIPE_W(real, Q, R, r, w)                                                                   \
+    QAOA_INSTANCE __global__ void tile_kernel<real, Q, R, w, recipe_def(r).code, recipe_def(r).nops,         \
                                               recipe_masks<real>(r)>(const __grid_constant__ TileArgs<Q>);
+
+// edge-weighted complex64 passes (recipes 0..3 and their full-mask forms)
+#define QAOA_RECIPE_W_INSTANCES(real, Q, R)                                                               \
+    namespace qaoa {                                                                                       \
+    QAOA_RECIPE_W(real, Q, R, 0, true)                                                                     \
+    QAOA_RECIPE_W(real, Q, R, 1, true)                                                                     \
+    QAOA_RECIPE_W(real, Q, R, 2, true)                                                                     \
+    QAOA_RECIPE_W(real, Q, R, 3, true)                                                                     \
+    QAOA_RECIPE_W(real, Q, R, 5, true)                                                                     \
+    QAOA_RECIPE_W(real, Q, R, 7, true)                                                                     \
+    }
 
 #define QAOA_RECIPE_INSTANCES(real, Q, R)                                                                 \
     namespace qaoa {                                                                                       \
@@ -43,6 +55,9 @@ QAOA_TILE_INSTANCES(float, 13, 5)
 #endif
 #if !defined(QAOA_OWN_RECIPE_C64)
 QAOA_RECIPE_INSTANCES(float, 13, 5)
+#endif
+#if !defined(QAOA_OWN_RECIPE_W_C64)
+QAOA_RECIPE_W_INSTANCES(float, 13, 5)
 #endif
 #if !defined(QAOA_OWN_TILE_C128)
 QAOA_TILE_INSTANCES(double, 12, 4)

@@ -955,8 +955,9 @@ __host__ __device__ constexpr uint64_t recipe_masks(int r) {
 // thread) by default; three (85) for the complex64 recipes that measured faster with 24 warps
 // per SM despite a few spilled registers (first, group-0 and last pass; the fused boundary pass,
 // with two RX sets and the phase live at once, is faster at two).
-template <typename real>
+template <typename real, bool kW = false>
 __host__ __device__ constexpr int tile_min_blocks(uint64_t recipe, int nops) {
+    if (kW) return QAOA_TILE_MIN_BLOCKS;  // the weighted split needs more registers
     // (the first-pass, group-0 and last-pass programs, with runtime or compiled-in masks)
     if (sizeof(real) == 4 && nops > 0)
         for (int r : {0, 1, 3})
@@ -965,7 +966,7 @@ __host__ __device__ constexpr int tile_min_blocks(uint64_t recipe, int nops) {
 }
 
 template <typename real, int Q, int R, bool kW, uint64_t kRecipe = 0, int kNops = 0, uint64_t kMasks = 0>
-__global__ void __launch_bounds__(1 << (Q - R), tile_min_blocks<real>(kRecipe, kNops))
+__global__ void __launch_bounds__(1 << (Q - R), tile_min_blocks<real, kW>(kRecipe, kNops))
     tile_kernel(const __grid_constant__ TileArgs<Q> a) {
     using T = Tile<real, Q, R, true>;
     using C2 = typename T::C2;
