@@ -245,6 +245,20 @@ struct PrecTraits<double> {
     static constexpr int Q = 12, R = 4;
 };
 
+// Tiles of the adjoint sweep: Q = 12, R = 4 in both precisions (the sweep holds psi and lambda,
+// two 16-amplitude register sets per thread, so two CTAs fit per SM in complex64).
+template <typename real>
+struct GradTraits {
+    static constexpr int Q = 12, R = 4;
+};
+
+TileConfig grad_tile_config(int prec) {
+    if (prec == QAOA_C64) return TileConfig{12, 4, 3, 18};  // 64-byte rows, 2 MiB pages of complex64
+    return tile_config_for(prec);
+}
+
+uint64_t grad_tiles(int n) { return n > 12 ? 1ull << (n - 12) : 1ull; }
+
 struct EventPair {
     cudaEvent_t a = nullptr, b = nullptr;
     int kind = 0;  // 1 read+write pass, 2 synthesising pass
@@ -387,10 +401,11 @@ qaoa_status ensure_attributes() {
         if (TileFn<real> f = recipe_kernel_w<real>(r))
             CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)((1u << Q) * sizeof(C2))));
     }
-    CUDA_TRY(cudaFuncSetAttribute(grad_kernel<real, Q, R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)((1u << Q) * sizeof(C2))));
-    CUDA_TRY(cudaFuncSetAttribute(grad_kernel<real, Q, R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)((1u << Q) * sizeof(C2))));
+    constexpr int GQ = GradTraits<real>::Q, GR = GradTraits<real>::R;
+    CUDA_TRY(cudaFuncSetAttribute(grad_kernel<real, GQ, GR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)((1u << GQ) * sizeof(C2))));
+    CUDA_TRY(cudaFuncSetAttribute(grad_kernel<real, GQ, GR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)((1u << GQ) * sizeof(C2))));
     CUDA_TRY(cudaFuncSetAttribute(small_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024));
     CUDA_TRY(cudaFuncSetAttribute(small_batch_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024));
     CUDA_TRY(cudaFuncSetAttribute(small_grad_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -434,10 +449,12 @@ qaoa_status launch_small(qaoa_state s, const SmallJob& j) {
     return QAOA_OK;
 }
 
-template <typename real>
-void fill_program(TileArgs<PrecTraits<real>::Q>& a, qaoa_state s, const Pass& ps) {
-    const Geometry geo = group_geometry(s->groups[ps.group], s->tc);
-    fill_geometry(a, s->g, geo, s->tc);
+// Pass arguments for the tile geometry of `groups[ps.group]` under tile configuration tc.
+template <int Qt>
+void fill_program_with(TileArgs<Qt>& a, qaoa_state s, const Pass& ps, const std::vector<Group>& groups,
+                       const TileConfig& tc) {
+    const Geometry geo = group_geometry(groups[ps.group], tc);
+    fill_geometry(a, s->g, geo, tc);
     a.nops = (int)ps.ops.size();
     a.need_cut = 0;
     for (size_t i = 0; i < ps.ops.size(); ++i) {
@@ -453,6 +470,11 @@ void fill_program(TileArgs<PrecTraits<real>::Q>& a, qaoa_state s, const Pass& ps
     a.partials = s->d_partials;
     a.cutout = nullptr;
     if (s->g.weighted) fill_weighted(a, s->g, s->prec, s->d_wfix, a.ops, a.nops);
+}
+
+template <typename real>
+void fill_program(TileArgs<PrecTraits<real>::Q>& a, qaoa_state s, const Pass& ps) {
+    fill_program_with(a, s, ps, s->groups, s->tc);
 }
 
 template <typename real>
@@ -868,7 +890,7 @@ qaoa_status grad_workspace(qaoa_state s, int p) {
     if (e == cudaSuccess && s->g.weighted) e = cudaMalloc(&s->d_gwfix, wfix_bytes(s->g, s->prec, p));
     if (e == cudaSuccess) e = cudaMalloc(&s->d_gmix, (size_t)3 * p * eb);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_gacc, (size_t)2 * p * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_gpart, (size_t)2 * s->ntiles * sizeof(double2));
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_gpart, (size_t)2 * grad_tiles(s->n) * sizeof(double2));
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(QAOA_ERR_OOM, std::string("gradient workspace allocation failed: ") + cudaGetErrorString(e));
@@ -926,7 +948,7 @@ qaoa_status gradient_async(qaoa_state s, int p, const double* gamma, const doubl
         s->launches++;
     }
     CUDA_TRY(cudaMemsetAsync(s->d_gacc, 0, (size_t)2 * p * sizeof(double), s->stream));
-    constexpr int Q = PrecTraits<real>::Q, R = PrecTraits<real>::R;
+    constexpr int Q = GradTraits<real>::Q, R = GradTraits<real>::R;
     if (s->n <= Q) {
         SmallGradJob j;
         std::memset(&j, 0, sizeof(j));
@@ -947,11 +969,13 @@ qaoa_status gradient_async(qaoa_state s, int p, const double* gamma, const doubl
         s->launches++;
     } else {
         Plan plan;
+        const TileConfig gtc = grad_tile_config(s->prec);
         try {
-            plan = plan_backward(s->n, s->tc, p);
+            plan = plan_backward(s->n, gtc, p);
         } catch (const std::exception& ex) {
             return fail(QAOA_ERR_UNSUPPORTED, ex.what());
         }
+        const uint64_t gt = grad_tiles(s->n);
         auto kfn = s->g.weighted ? grad_kernel<real, Q, R, true> : grad_kernel<real, Q, R, false>;
         const size_t smem = (size_t)(1u << Q) * sizeof(C2);
         qaoa_status ast = ensure_attributes<real>();
@@ -959,7 +983,7 @@ qaoa_status gradient_async(qaoa_state s, int p, const double* gamma, const doubl
         TileArgs<Q> a;
         for (const Pass& ps : plan.passes) {
             std::memset(&a, 0, sizeof(a));
-            fill_program<real>(a, s, ps);
+            fill_program_with(a, s, ps, plan.groups, gtc);
             a.need_cut = 1;
             a.state2 = work;
             a.phase = s->d_gtab;
@@ -970,9 +994,9 @@ qaoa_status gradient_async(qaoa_state s, int p, const double* gamma, const doubl
             int lev[2] = {-1, -1};
             for (const Op& op : ps.ops)
                 if (op.kind == OP_RXD || op.kind == OP_GRADG) lev[(op.arg >> 16) & 1] = op.arg & 0xffff;
-            kfn<<<(unsigned)s->ntiles, 1u << (Q - R), smem, s->stream>>>(a);
+            kfn<<<(unsigned)gt, 1u << (Q - R), smem, s->stream>>>(a);
             CUDA_TRY(cudaGetLastError());
-            grad_reduce_kernel<<<1, 1024, 0, s->stream>>>(s->d_gpart, s->ntiles, lev[0], lev[1], p, s->d_gacc);
+            grad_reduce_kernel<<<1, 1024, 0, s->stream>>>(s->d_gpart, gt, lev[0], lev[1], p, s->d_gacc);
             CUDA_TRY(cudaGetLastError());
             s->launches += 2;
         }

@@ -6,5 +6,5 @@
 #include "instances.h"
 #undef QAOA_INSTANCE
 #define QAOA_INSTANCE template
-QAOA_GRAD_INSTANCES(float, 13, 5)
+QAOA_GRAD_INSTANCES(float, 12, 4)
 QAOA_GRAD_INSTANCES(double, 12, 4)

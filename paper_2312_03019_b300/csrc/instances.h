@@ -64,6 +64,6 @@ QAOA_TILE_INSTANCES(double, 12, 4)
 QAOA_RECIPE_INSTANCES(double, 12, 4)
 #endif
 #if !defined(QAOA_OWN_GRAD)
-QAOA_GRAD_INSTANCES(float, 13, 5)
+QAOA_GRAD_INSTANCES(float, 12, 4)
 QAOA_GRAD_INSTANCES(double, 12, 4)
 #endif

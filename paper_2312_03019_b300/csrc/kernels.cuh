@@ -1138,8 +1138,9 @@ __global__ void __launch_bounds__(1 << (Q - R), tile_min_blocks<real, kW>(kRecip
 // One pass of the adjoint sweep over psi (a.state) and lambda (a.state2), same tiling as
 // tile_kernel.  Per CTA it writes, for accumulator slots 0 and 1, (sum of RXD pair terms,
 // sum of GRADG terms) to partials[2 t + slot].
+// (complex64 holds both states in 64 registers and runs two CTAs per SM; complex128 needs 128)
 template <typename real, int Q, int R, bool kW>
-__global__ void __launch_bounds__(1 << (Q - R), 1) grad_kernel(const __grid_constant__ TileArgs<Q> a) {
+__global__ void __launch_bounds__(1 << (Q - R), sizeof(real) == 4 ? 2 : 1) grad_kernel(const __grid_constant__ TileArgs<Q> a) {
     using T = Tile<real, Q, R>;
     using C2 = typename T::C2;
     using WA = typename T::WA;

@@ -104,7 +104,7 @@ Layout single_layout(const HostGraph& g, int p, int prec, bool grad, uint64_t nt
         L.gtab = take((size_t)p * E1 * eb);
         L.gmix = take((size_t)3 * p * eb);
         L.gacc = take((size_t)2 * p * sizeof(double));
-        L.gpart = take((size_t)2 * ntiles * sizeof(double2));
+        L.gpart = take((size_t)2 * grad_tiles(n) * sizeof(double2));
         if (g.weighted) L.gwfix = take(wfix_bytes(g, prec, p));
     }
     L.total = o;
