@@ -356,8 +356,7 @@ TileFn<real> recipe_kernel(int r) {
         case 4: return recipe_fn<real, 4>();
         case 5: return recipe_fn<real, 5>();
         case 6: return recipe_fn<real, 6>();
-        case 7: return recipe_fn<real, 7>();
-        default: return recipe_fn<real, 8>();
+        default: return recipe_fn<real, 7>();
     }
 }
 
@@ -369,7 +368,7 @@ TileFn<real> pick_tile_kernel(const TileArgs<PrecTraits<real>::Q>& a, bool weigh
     if (a.nops <= 10) {
         uint64_t code = 0;
         for (int i = 0; i < a.nops; ++i) code |= recipe_step(i, a.ops[i].kind, a.ops[i].layout);
-        const int order[] = {1, 5, 8, 7, 0, 2, 3, 4};  // the full-mask fused pass (6) spills: not used
+        const int order[] = {1, 5, 7, 0, 2, 3, 4};  // the full-mask fused pass (6) spills: not used
         for (int r : order) {
             const Recipe d = recipe_def(r);
             if (d.nops != a.nops || d.code != code) continue;

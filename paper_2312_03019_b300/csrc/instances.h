@@ -42,7 +42,6 @@
     QAOA_RECIPE_ONE(real, Q, R, 5)                                                                         \
     QAOA_RECIPE_ONE(real, Q, R, 6)                                                                         \
     QAOA_RECIPE_ONE(real, Q, R, 7)                                                                         \
-    QAOA_RECIPE_ONE(real, Q, R, 8)                                                                         \
     }
 
 #define QAOA_GRAD_INSTANCES(real, Q, R)                                              \

@@ -927,10 +927,8 @@ constexpr Recipe kRecipe0 = base_recipe(0), kRecipe1 = base_recipe(1), kRecipe2 
 // Instantiations 5..7 are recipes 0, 2 and 3 again with every RX mask compiled in as full (the
 // high-group passes of 10-bit complex64 / 8-bit complex128 groups, as at n = 33); the host
 // tries them before the runtime-mask versions.
-constexpr int kRecipes = 9;
-__host__ __device__ constexpr Recipe recipe_def(int r) {
-    return base_recipe(r == 5 ? 0 : r == 6 || r == 8 ? 2 : r == 7 ? 3 : r);
-}
+constexpr int kRecipes = 8;
+__host__ __device__ constexpr Recipe recipe_def(int r) { return base_recipe(r == 5 ? 0 : r == 6 ? 2 : r == 7 ? 3 : r); }
 // Compiled-in masks.  The group-0 pass (recipe 1) always covers its Q bits with the same masks:
 // complex64 (R = 5) layouts 1, 2, 0 take local bits 3..7, 0..2 (the layout-2 op skips bits 3, 4,
 // done already), 8..12; complex128 (R = 4) takes 4..7, 0..3, 8..11.  Masks compiled in remove
@@ -942,7 +940,6 @@ __host__ __device__ constexpr uint64_t recipe_masks(int r) {
         return sizeof(real) == 4 ? (fixed_mask(1, 31) | fixed_mask(3, 7) | fixed_mask(5, 31))
                                  : (fixed_mask(1, 15) | fixed_mask(3, 15) | fixed_mask(5, 15));
     if (r < 5) return 0;
-    if (r == 8) return fixed_mask(1, full) | fixed_mask(7, full);  // fused pass, layout-0 ops only
     const Recipe d = recipe_def(r);
     uint64_t m = 0;
     for (int i = 0; i < d.nops; ++i)
