@@ -297,6 +297,45 @@ def test_full_size_n33_properties(B):
     torch.cuda.empty_cache()
 
 
+def test_max_size_n34_complex64(B):
+    """The largest state the library takes, n = 34 (exact 3-regular, 51 edges; complex64, 128 GiB,
+    four mixer groups): p = 1 matches the closed-form <C>; beta = 0 gives the cost phases
+    amplitude by amplitude (sampled against the oracle's cut value, the highest index bits
+    included); a p = 3 run keeps the norm and the complement symmetry."""
+    import oracle
+    import torch
+    from tests.test_oracle_pins import p1_closed_form
+    g = I.regular3(34, 0)
+    gamma, beta = I.angles(3, 34)
+    n = g.n
+    amp = 2 ** (-n / 2)
+    rng = np.random.default_rng(34)
+    idx = np.unique(np.concatenate([rng.integers(0, 1 << n, 256), [0, (1 << n) - 1, 1 << 33, (1 << 33) + 7]]))
+    s = B.QAOAState(g, "c64")
+    s.apply_layers([0.4], [0.3])
+    c, nrm = s.expectation()
+    assert abs(c - p1_closed_form(g, 0.4, 0.3)) <= 1e-5 * g.m
+    assert abs(nrm - 1) < 1e-5
+    s.reset()
+    s.apply_layers(gamma, np.zeros(3))
+    t = s.as_tensor()
+    samp = t[torch.tensor(idx, device=t.device)].cpu().numpy().astype(np.complex128)
+    ref = np.array([amp * np.exp(-1j * gamma.sum() * oracle.cut_value(g, int(z))) for z in idx])
+    assert np.max(np.abs(samp - ref)) < 1e-5 * amp
+    del t
+    s.reset()
+    s.apply_layers(gamma, beta)
+    c, nrm = s.expectation()
+    assert abs(nrm - 1) < 1e-4 and 0 <= c <= g.m
+    t = s.as_tensor()
+    a = t[torch.tensor(idx, device=t.device)].cpu().numpy()
+    b = t[torch.tensor(((1 << n) - 1) ^ idx, device=t.device)].cpu().numpy()
+    assert np.max(np.abs(a - b)) < 1e-5 * amp
+    s.close()
+    del t
+    torch.cuda.empty_cache()
+
+
 @pytest.mark.slow
 def test_full_size_n33_c128_closed_form(B):
     """complex128 at n = 33 (128 GiB): p = 1 <C> equals the closed form to 1e-12 relative."""
