@@ -132,6 +132,46 @@ def test_weighted_state_parity(B, prec, n, p, mk):
 
 
 @pytest.mark.parametrize("prec", ["c64", "c128"])
+@pytest.mark.parametrize("n,p", [(24, 2), (25, 3)])
+def test_weighted_state_parity_three_groups(B, prec, n, p):
+    """Sizes with three mixer groups, where the weighted passes run their recipe kernels
+    (complex64) and the interpreting kernel (complex128)."""
+    import oracle
+    g = weighted(I.regular3(n, 3) if n % 2 == 0 else I.gnp(n, 0.2, 3), 31, lo=-0.5, hi=2.0)
+    gamma, beta = I.angles(p, seed=n + 90)
+    ref = oracle.qaoa_state(g, gamma, beta)
+    ref_c, _ = oracle.expectation(g, ref)
+    c, nrm, psi = run(B, g, gamma, beta, prec)
+    if prec == "c128":
+        assert abs(c - ref_c) <= 1e-12 * max(1.0, abs(ref_c))
+        assert np.linalg.norm(psi - ref) <= 1e-12
+    else:
+        assert abs(c - ref_c) <= 1e-5 * float(np.sum(np.abs(g.weights)))
+        assert abs(np.vdot(ref, psi)) ** 2 >= 1 - 1e-5
+
+
+def test_weighted_phase_samples_n30(B):
+    """n = 30, complex64, beta = 0: psi_z = 2^(-n/2) exp(-i sum gamma C(z)) with the weighted
+    cut value, sampled amplitude by amplitude against the oracle."""
+    import oracle
+    import torch
+    g = weighted(I.regular3(30, 4), 32, lo=0.1, hi=3.0)
+    gamma = np.array([0.7, 1.9])
+    n = g.n
+    rng = np.random.default_rng(30)
+    idx = np.unique(np.concatenate([rng.integers(0, 1 << n, 200), [0, (1 << n) - 1]]))
+    s = B.QAOAState(g, "c64")
+    s.apply_layers(gamma, np.zeros(2))
+    t = s.as_tensor()
+    samp = t[torch.tensor(idx, device=t.device)].cpu().numpy().astype(np.complex128)
+    amp = 2 ** (-n / 2)
+    ref = np.array([amp * np.exp(-1j * gamma.sum() * oracle.cut_value(g, int(z))) for z in idx])
+    s.close()
+    del t
+    assert np.max(np.abs(samp - ref)) < 2e-5 * amp
+
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
 def test_weights_all_one_take_the_unit_path(B, prec):
     g = I.gnp(17, 0.4, 3)
     g1 = I.Graph(n=g.n, edges=g.edges, weights=np.ones(g.m), name=g.name + "+ones")
