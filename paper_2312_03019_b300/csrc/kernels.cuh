@@ -2,15 +2,23 @@
 //
 // Kernels:
 //   coeff_kernel   per level k: phase table T_k[c] = exp(-i gamma_k c), c = 0..|E| (FP64
-//                  sincos, rounded to the state precision) and the mixer coefficients: (cos b,
-//                  sin b) and the factored butterfly t, f described at `rx`.
+//                  sincos, rounded to the state precision), the mixer coefficients (cos b,
+//                  sin b) and the factored butterfly t, f described at `rx`, and for
+//                  edge-weighted graphs the fixed-point rows of the weighted split.
 //   tile_kernel    one pass over the state in tiles of 2^Q amplitudes (see plan.h): loads a
 //                  tile (or synthesises |+>^n), runs the pass program (RX butterflies in
 //                  registers, register-layout exchanges through swizzled shared memory, the
 //                  cost phase with the on-the-fly cut count, the <C> reduction) and stores.
-//   small_kernel   a whole state of n <= Q_small qubits in shared memory, all levels in one
-//                  launch; one CTA per state, so many small states share a launch.
+//                  Instantiated once interpreting any program (kNops = 0) and once per compiled
+//                  pass recipe as straight-line code (kRecipe, kNops, kMasks).
+//   grad_kernel    one pass of the adjoint sweep over psi and lambda = C psi (inverse mixer with
+//                  the d/d beta pair sums, the d/d gamma sums, the conjugate phase), with
+//   grad_reduce_kernel  the fixed-order sum of its per-tile partials per level.
+//   small_kernel / small_batch_kernel / small_grad_kernel / coeff_batch_kernel
+//                  a whole state of n <= Q_small qubits in shared memory, all levels in one
+//                  launch: one CTA per state, many states per launch for the server.
 //   finalize_kernel fixed-order FP64 sum of the per-tile partials of <C> and the norm.
+//   complement_kernel resolves the pending complement and the complex64 parity form in place.
 //   fill_kernel    writes |+>^n when a deferred initial state has to be materialised.
 //
 // On-the-fly cut count (bit-exact integer arithmetic, Algorithm 3 re-associated).  For a
