@@ -138,3 +138,39 @@ def test_autograd_function(B):
     assert np.allclose(gamma.grad.numpy(), 2.0 * dg, rtol=0, atol=1e-12)
     assert np.allclose(beta.grad.numpy(), 2.0 * db, rtol=0, atol=1e-12)
     s.close()
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("n", [10, 16])
+def test_gradient_more_levels_than_one_coefficient_chunk(B, prec, n):
+    """p = 70 crosses the 64-level coefficient chunks of the forward run; the adjoint sweep's
+    tables cover all levels (one-CTA sweep at n = 10, tiled sweep at n = 16)."""
+    import oracle
+    g = I.regular3(n, 5)
+    gamma, beta = I.angles(70, n + 200)
+    gamma *= 0.2  # keep <C> away from its extremes, where all derivatives are tiny
+    ref_c, ref_dg, ref_db = oracle.adjoint_gradient(g, gamma, beta)
+    c, dg, db = gpu_gradient(B, g, gamma, beta, prec)
+    scale = max(1.0, np.max(np.abs(np.concatenate([ref_dg, ref_db]))))
+    tol = 1e-10 if prec == "c128" else 2e-4 * g.m
+    assert abs(c - ref_c) <= (1e-12 * abs(ref_c) if prec == "c128" else 1e-4 * g.m)
+    assert np.max(np.abs(dg - ref_dg)) <= tol * scale
+    assert np.max(np.abs(db - ref_db)) <= tol * scale
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_empty_graph_tiled(B, prec):
+    """No edges at n = 20 (tiled passes, a one-entry phase table): <C> = 0, the state is
+    exp(-i n sum beta) |+>^n times 2^(-n/2) per amplitude, every derivative is 0."""
+    g = I.empty(20)
+    gamma, beta = I.angles(3, 7)
+    s = B.QAOAState(g, prec)
+    s.apply_layers(gamma, beta)
+    c, nrm = s.expectation()
+    psi = s.amplitudes().astype(np.complex128)
+    s.close()
+    assert c == 0.0 and abs(nrm - 1) < (1e-12 if prec == "c128" else 1e-5)
+    want = 2 ** (-10) * np.exp(-1j * 20 * beta.sum())
+    assert np.max(np.abs(psi - want)) < (1e-14 if prec == "c128" else 1e-7)
+    c, dg, db = gpu_gradient(B, g, gamma, beta, prec)
+    assert c == 0.0 and np.all(dg == 0) and np.all(db == 0)

@@ -254,6 +254,18 @@ def test_weighted_requests_through_the_server(B):
         assert r["expectation"] == c
 
 
+def test_weighted_more_levels_than_one_coefficient_chunk(B):
+    """p = 70 on a weighted graph: the fixed-point angle rows are rebuilt per 64-level chunk."""
+    import oracle
+    g = weighted(I.regular3(16, 9), 40)
+    gamma, beta = I.angles(70, 41)
+    ref = oracle.qaoa_state(g, gamma, beta)
+    ref_c, _ = oracle.expectation(g, ref)
+    c, nrm, psi = run(B, g, gamma, beta, "c128")
+    assert abs(c - ref_c) <= 1e-12 * max(1.0, abs(ref_c))
+    assert np.linalg.norm(psi - ref) <= 1e-11
+
+
 def test_weighted_rejections(B):
     g = I.gnp(10, 0.5, 1)
     bad = I.Graph(n=g.n, edges=g.edges, weights=np.full(g.m, np.nan))
