@@ -58,6 +58,8 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--weighted", action="store_true",
                     help="edge weights U[0.1, 2] on the same graph (Algorithm 2 path), for context")
+    ap.add_argument("--cpu-report", action="store_true",
+                    help="time the CPU oracle on the host's cores (all threads and one) at the small configurations")
     ap.add_argument("--grad", action="store_true",
                     help="gradient mode: d<C>/d(gamma, beta) by qaoa_gradient on G(24, 0.5), p = 10")
     ap.add_argument("--serve", action="store_true",
@@ -440,6 +442,55 @@ def serve_stream(B, reqs, cfg):
             "stats": stats}, done
 
 
+def run_cpu_report(args):
+    """The oracle (gate-level complex128, Algorithm 1) timed on this host with all threads and
+    with one: 3-regular n=10, p=1 (gamma 0.4, beta 0.3); one level of G(26, 0.5) (one thread:
+    one level at n=20, scaled by 2^n x gate count); the FP64 adjoint gradient of G(14, 0.5),
+    p=10."""
+    import oracle
+    allt = oracle.threads()
+    rows = []
+
+    def timed(fn, reps=1):
+        fn()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        return (time.perf_counter() - t0) / reps
+
+    for threads in (allt, 1):
+        oracle.set_threads(threads)
+        g1, ga1, be1 = I.workload_n10_regular3_p1()
+        t1 = timed(lambda: oracle.expectation(g1, oracle.qaoa_state(g1, ga1, be1)), reps=20)
+        g2, ga2, be2 = I.workload_gnp26_p4()
+        if threads == 1:
+            gs = I.gnp(20, 0.5, 0)
+            ts, _ = oracle_level_seconds_graph(gs, ga2[0], be2[0])
+            t2 = ts * 2.0 ** 6 * gates_per_level(g2) / gates_per_level(gs)
+            how = "one level at n=20 scaled by 2^n x gate count"
+        else:
+            t2, _ = oracle_level_seconds_graph(g2, ga2[0], be2[0])
+            how = "one level measured"
+        g4 = I.gnp(14, 0.5, 0)
+        ga4, be4 = I.angles(10, 0)
+        t4 = timed(lambda: oracle.adjoint_gradient(g4, ga4, be4), reps=3)
+        rows.append({"threads": threads, "n10_p1_ms": t1 * 1e3, "gnp26_level_s": t2, "gnp26_level": how,
+                     "gnp14_p10_adjoint_ms": t4 * 1e3})
+    oracle.set_threads(allt)
+    print(json.dumps({"mode": "cpu-report", "kind": "oracle", "host_threads": allt, "rows": rows}), flush=True)
+    return 0
+
+
+def oracle_level_seconds_graph(g, gamma, beta):
+    """One oracle level (cost layer, gate by gate, and mixer layer) on graph g."""
+    import oracle
+    psi = oracle.initial_state(g.n)
+    t0 = time.perf_counter()
+    psi = oracle.cost_layer(g, gamma, psi)
+    psi = oracle.mixer_layer(g.n, beta, psi)
+    return time.perf_counter() - t0, g
+
+
 def run_grad(args):
     """Adjoint gradients per second on G(24, 0.5), seed 0, p = 10 (20 parameters), complex64,
     through qaoa_gradient (forward levels, lambda = C psi, reverse sweep; host-synchronous per
@@ -529,6 +580,8 @@ def main():
         return run_serve(args)
     if args.grad:
         return run_grad(args)
+    if args.cpu_report:
+        return run_cpu_report(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
