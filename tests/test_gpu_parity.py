@@ -337,6 +337,24 @@ def test_max_size_n34_complex64(B):
 
 
 @pytest.mark.slow
+def test_max_size_n34_complex128_closed_form(B):
+    """The largest complex128 state, n = 34 (256 GiB): p = 1 against the closed form to 1e-12."""
+    import torch
+    from tests.test_oracle_pins import p1_closed_form
+    free, _ = torch.cuda.mem_get_info()
+    if free < B.qaoa_state_bytes(34, "c128") + (2 << 30):
+        pytest.skip("needs 258 GiB of free device memory")
+    g = I.regular3(34, 0)
+    s = B.QAOAState(g, "c128")
+    s.apply_layers([0.4], [0.3])
+    c, nrm = s.expectation()
+    s.close()
+    torch.cuda.empty_cache()
+    assert abs(c - p1_closed_form(g, 0.4, 0.3)) <= 1e-12 * c
+    assert abs(nrm - 1) < 1e-12
+
+
+@pytest.mark.slow
 def test_full_size_n33_c128_closed_form(B):
     """complex128 at n = 33 (128 GiB): p = 1 <C> equals the closed form to 1e-12 relative."""
     import torch
