@@ -385,10 +385,17 @@ TileFn<real> pick_tile_kernel(const TileArgs<PrecTraits<real>::Q>& a, bool weigh
     return weighted ? tile_kernel<real, Q, R, true> : tile_kernel<real, Q, R, false>;
 }
 
+// Dynamic shared-memory limits of every kernel, set once per device (the attribute belongs to
+// the device's instance of the function) and thread-safely (the server's scheduler thread and
+// callers' threads both launch).
 template <typename real>
 qaoa_status ensure_attributes() {
-    static bool done = false;
-    if (done) return QAOA_OK;
+    static std::mutex mu;
+    static std::vector<char> done;
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev < (int)done.size() && done[dev]) return QAOA_OK;
     constexpr int Q = PrecTraits<real>::Q, R = PrecTraits<real>::R;
     using C2 = typename C2T<real>::type;
     CUDA_TRY(cudaFuncSetAttribute(tile_kernel<real, Q, R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -410,7 +417,8 @@ qaoa_status ensure_attributes() {
     CUDA_TRY(cudaFuncSetAttribute(small_batch_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024));
     CUDA_TRY(cudaFuncSetAttribute(small_grad_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)(2 * (1u << Q) * sizeof(C2))));
-    done = true;
+    if ((int)done.size() <= dev) done.resize(dev + 1, 0);
+    done[dev] = 1;
     return QAOA_OK;
 }
 
