@@ -274,10 +274,10 @@ def run_ours(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if world > 1:  # one replica per GPU: bind the group to this rank's device
+        dist.init_process_group("nccl", device_id=dev)
 
     from paper_2312_03019_b300 import build as bld
     bld.build()
@@ -298,7 +298,7 @@ def run_ours(args):
 
     def barrier():
         if world > 1:
-            dist.barrier()
+            dist.barrier(device_ids=[local])
 
     props = torch.cuda.get_device_properties(dev)
     uuid = getattr(props, "uuid", None)
