@@ -290,6 +290,16 @@ class QAOAState:
     def expectation(self):
         return qaoa_expectation(self.handle)
 
+    def gradient(self, gamma, beta):
+        """(<C>, d<C>/d gamma, d<C>/d beta) after len(gamma) levels from |+>^n by the adjoint sweep
+        (qaoa_gradient); the sweep's second state lives in a work buffer kept with this handle.
+        The state is |+>^n again afterwards."""
+        import torch
+
+        if getattr(self, "_work", None) is None:
+            self._work = torch.empty(self.nbytes, dtype=torch.uint8, device=self.buffer.device)
+        return qaoa_gradient(self.handle, gamma, beta, self._work.data_ptr(), self.nbytes)
+
     def amplitudes(self) -> np.ndarray:
         return qaoa_state_copy_out(self.handle, self.n, self.prec)
 
@@ -307,6 +317,7 @@ class QAOAState:
             qaoa_state_free(self.handle)
             self.handle = None
         self.buffer = None
+        self._work = None
 
     def __del__(self):
         try:

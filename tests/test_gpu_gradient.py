@@ -174,3 +174,14 @@ def test_empty_graph_tiled(B, prec):
     assert np.max(np.abs(psi - want)) < (1e-14 if prec == "c128" else 1e-7)
     c, dg, db = gpu_gradient(B, g, gamma, beta, prec)
     assert c == 0.0 and np.all(dg == 0) and np.all(db == 0)
+
+
+def test_state_gradient_method_matches_the_c_call(B):
+    g = I.gnp(16, 0.4, 2)
+    gamma, beta = I.angles(3, 16)
+    c0, dg0, db0 = gpu_gradient(B, g, gamma, beta, "c64")
+    s = B.QAOAState(g, "c64")
+    c1, dg1, db1 = s.gradient(gamma, beta)
+    c2, dg2, db2 = s.gradient(gamma, beta)  # the kept work buffer is reused
+    s.close()
+    assert c0 == c1 == c2 and np.array_equal(dg0, dg1) and np.array_equal(db1, db2)
