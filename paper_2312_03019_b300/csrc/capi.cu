@@ -58,9 +58,9 @@ struct HostGraph {
     std::vector<double> w;                   // weight of edges[e] (weighted graphs)
 };
 
-// Phase-table entries per level: |E| + 1 for the cut count, one (the folded factor) when the
-// phase comes from the weighted sums.
-int table_entries(const HostGraph& g) { return g.weighted ? 1 : g.m + 1; }
+// Phase-table entries per level: |E| + 1 for the cut count; kWTurnSteps rotations of the folded
+// factor when the phase comes from the weighted sums.
+int table_entries(const HostGraph& g) { return g.weighted ? kWTurnSteps : g.m + 1; }
 
 // 2^S for the value weights: the largest power of two with sum |w_e| 2^S <= 2^(B-2), B the
 // fixed-point word size of the precision (32 for complex64, 64 for complex128).
@@ -335,7 +335,6 @@ TileFn<real> recipe_kernel_w(int r) {
     if constexpr (std::is_same<real, float>::value) {
         switch (r) {
             case 0: return recipe_fn<real, 0, true>();
-            case 1: return recipe_fn<real, 1, true>();
             case 2: return recipe_fn<real, 2, true>();
             case 3: return recipe_fn<real, 3, true>();
             case 5: return recipe_fn<real, 5, true>();
@@ -362,9 +361,12 @@ TileFn<real> recipe_kernel(int r) {
 
 // The pass kernel for a program: a recipe instantiation when one matches (those with compiled-in
 // masks first, and only when the program's masks are exactly those), else the interpreting one.
+// Edge weights enter only the phase, <C> and cut-value ops: a program without them (a plain mixer
+// pass) runs the unit-weight instance, whatever the graph.
 template <typename real>
-TileFn<real> pick_tile_kernel(const TileArgs<PrecTraits<real>::Q>& a, bool weighted) {
+TileFn<real> pick_tile_kernel(const TileArgs<PrecTraits<real>::Q>& a, bool weighted_graph) {
     constexpr int Q = PrecTraits<real>::Q, R = PrecTraits<real>::R;
+    const bool weighted = weighted_graph && a.need_cut;
     if (a.nops <= 10) {
         uint64_t code = 0;
         for (int i = 0; i < a.nops; ++i) code |= recipe_step(i, a.ops[i].kind, a.ops[i].layout);

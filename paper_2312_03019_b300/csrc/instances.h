@@ -21,11 +21,11 @@
     QAOA_INSTANCE __global__ void tile_kernel<real, Q, R, w, recipe_def(r).code, recipe_def(r).nops,         \
                                               recipe_masks<real>(r)>(const __grid_constant__ TileArgs<Q>);
 
-// edge-weighted complex64 passes (recipes 0..3 and their full-mask forms)
+// edge-weighted complex64 passes: the recipes with a phase or <C> op (first, fused, last, and
+// the full-mask first and last); plain mixer passes of weighted graphs run the unit-weight ones
 #define QAOA_RECIPE_W_INSTANCES(real, Q, R)                                                               \
     namespace qaoa {                                                                                       \
     QAOA_RECIPE_W(real, Q, R, 0, true)                                                                     \
-    QAOA_RECIPE_W(real, Q, R, 1, true)                                                                     \
     QAOA_RECIPE_W(real, Q, R, 2, true)                                                                     \
     QAOA_RECIPE_W(real, Q, R, 3, true)                                                                     \
     QAOA_RECIPE_W(real, Q, R, 5, true)                                                                     \

@@ -4,7 +4,8 @@
 //   coeff_kernel   per level k: phase table T_k[c] = exp(-i gamma_k c), c = 0..|E| (FP64
 //                  sincos, rounded to the state precision), the mixer coefficients (cos b,
 //                  sin b) and the factored butterfly t, f described at `rx`, and for
-//                  edge-weighted graphs the fixed-point rows of the weighted split.
+//                  edge-weighted graphs the fixed-point rows of the weighted split and the
+//                  256-step rotation table of `phase_tab` in place of T_k.
 //   tile_kernel    one pass over the state in tiles of 2^Q amplitudes (see plan.h): loads a
 //                  tile (or synthesises |+>^n), runs the pass program (RX butterflies in
 //                  registers, register-layout exchanges through swizzled shared memory, the
@@ -38,7 +39,8 @@
 // 2^B.  Two kinds of f are used.  For the cost phase of level k, f_e = gamma_k w_e / (2 pi) in
 // units of 2^-B turns, reduced modulo one turn: since z_u xor z_v is 0 or 1, the sum is
 // gamma_k C(z) / (2 pi) modulo one turn up to the rounding of the m per-edge angles, and each
-// amplitude takes one sincospi of it.  For <C> and the adjoint's C psi, f_e = w_e 2^S, with S
+// amplitude turns it into exp(-i gamma_k C(z)) by one table read and a short series
+// (`phase_tab`).  For <C> and the adjoint's C psi, f_e = w_e 2^S, with S
 // chosen so that sum |w_e| 2^S < 2^(B-2).  Register-bit pairs enter through R(R-1)/2 pair terms
 // P_jk (z_j z_k coefficients) instead of the 2^R-entry table.
 #pragma once
@@ -202,16 +204,32 @@ struct WAcc<double> {
     using stype = int64_t;
 };
 
-// exp(-i 2 pi th / 2^B) times g, with th read as a signed fraction of a turn (|angle| <= pi).
-__device__ __forceinline__ float2 phase_of(uint32_t th, float2 g) {
-    float sn, cs;
-    sincospif((float)(int32_t)th * 0x1p-31f, &sn, &cs);
-    return make_float2(g.x * cs + g.y * sn, g.y * cs - g.x * sn);
+// Entries per level of the weighted phase table: T[k] = g exp(-2 pi i k / kWTurnSteps), g the
+// level's folded factor (T[0] = g).
+constexpr int kWTurnSteps = 256;
+
+// g exp(-2 pi i th / 2^B) from the level's table T, by angle addition (table-driven evaluation):
+// the nearest step k = round(th 256 / 2^B) mod 256 comes from T, the remainder
+// x = 2 pi (th - k 2^B / 256) / 2^B, |x| <= pi / 256, from the Taylor series of exp(-i x).
+// complex64: cos x = 1 - x^2/2, sin x = x - x^3/6 (truncation <= x^4/24 < 1e-9, below the
+// rounding of T); complex128: through x^6 and x^5 (truncation < 1e-17).
+__device__ __forceinline__ float2 phase_tab(uint32_t th, const float2* __restrict__ T) {
+    const int32_t r = (int32_t)(th << 8) >> 8;  // signed remainder, in [-2^23, 2^23)
+    const float2 t = __ldg(T + ((th - (uint32_t)r) >> 24));
+    const float x = (float)r * 1.4629180792671596e-09f;  // 2 pi / 2^32
+    const float x2 = x * x;
+    const float c = fmaf(-0.5f, x2, 1.0f);
+    const float sn = x * fmaf(x2, -0.16666667f, 1.0f);
+    return make_float2(fmaf(t.x, c, t.y * sn), fmaf(t.y, c, -t.x * sn));  // t (c - i sn)
 }
-__device__ __forceinline__ double2 phase_of(uint64_t th, double2 g) {
-    double sn, cs;
-    sincospi((double)(int64_t)th * 0x1p-63, &sn, &cs);
-    return make_double2(g.x * cs + g.y * sn, g.y * cs - g.x * sn);
+__device__ __forceinline__ double2 phase_tab(uint64_t th, const double2* __restrict__ T) {
+    const int64_t r = (int64_t)(th << 8) >> 8;  // signed remainder, in [-2^55, 2^55)
+    const double2 t = __ldg(T + ((th - (uint64_t)r) >> 56));
+    const double x = (double)r * 3.4061215800865545e-19;  // 2 pi / 2^64
+    const double x2 = x * x;
+    const double c = fma(x2, fma(x2, fma(x2, -1.0 / 720.0, 1.0 / 24.0), -0.5), 1.0);
+    const double sn = x * fma(x2, fma(x2, 1.0 / 120.0, -1.0 / 6.0), 1.0);
+    return make_double2(fma(t.x, c, t.y * sn), fma(t.y, c, -t.x * sn));
 }
 
 template <typename WA>
@@ -579,13 +597,13 @@ struct Tile {
     template <int L, bool kW = false>
     static __device__ __forceinline__ void phase(C2 (&v)[NE], const Ctx& c, uint32_t tid, int level) {
         const TileArgs<Q>& a = *c.a;
-        if constexpr (kW) {  // the table holds one entry per level: the folded factor
+        if constexpr (kW) {  // the level's table holds kWTurnSteps rotations of the folded factor
             WA s[R], P[NP];
             const WA base = wsetup<L>(c, tid, a.wslot[level], s, P);
-            const C2 g = __ldg(reinterpret_cast<const C2*>(a.phase) + level);
+            const C2* __restrict__ T = reinterpret_cast<const C2*>(a.phase) + (size_t)level * a.E1;
             for_x<NE>([&](auto X) {
                 constexpr int x = decltype(X)::value;
-                v[x] = apply_phase<x>(v[x], phase_of(wat<x>(base, s, P), g), c.sg);
+                v[x] = apply_phase<x>(v[x], phase_tab(wat<x>(base, s, P), T), c.sg);
             });
             return;
         }
@@ -610,14 +628,14 @@ struct Tile {
         if constexpr (kW) {
             WA s[R], P[NP];
             const WA base = wsetup<L>(c, tid, 0, s, P);
-            real sc = 0, sn = 0;
+            real sc = 0, sn = 0;  // sc in the value rows' fixed-point unit, scaled once below
             for_x<NE>([&](auto X) {
                 constexpr int x = decltype(X)::value;
                 const real p = v[x].x * v[x].x + v[x].y * v[x].y;
                 sn += p;
-                sc += p * wval(wat<x>(base, s, P), a.vscale);
+                sc += p * (real)(SWA)wat<x>(base, s, P);
             });
-            accC += (double)sc;
+            accC += (double)sc * a.vscale;
             accN += (double)sn;
             return;
         }
@@ -746,13 +764,13 @@ struct Tile {
         if constexpr (kW) {
             WA s[R], P[NP];
             const WA base = wsetup<L>(c, tid, 0, s, P);
-            real acc = 0;
+            real acc = 0;  // in the value rows' fixed-point unit, scaled once at the end
             for_x<NE>([&](auto X) {
                 constexpr int x = decltype(X)::value;
-                acc += wval(wat<x>(base, s, P), a.vscale) *
+                acc += (real)(SWA)wat<x>(base, s, P) *
                        (re_of<x>(w[x]) * im_of<x>(v[x]) - im_of<x>(w[x]) * re_of<x>(v[x]));
             });
-            return acc;
+            return (real)((double)acc * a.vscale);
         }
         int s[R];
         const int base = cut_setup<L>(c, tid, s);
@@ -775,10 +793,10 @@ struct Tile {
         if constexpr (kW) {
             WA s[R], P[NP];
             const WA base = wsetup<L>(c, tid, a.wslot[level], s, P);
-            const C2 g = __ldg(reinterpret_cast<const C2*>(a.phase) + level);
+            const C2* __restrict__ T = reinterpret_cast<const C2*>(a.phase) + (size_t)level * a.E1;
             for_x<NE>([&](auto X) {
                 constexpr int x = decltype(X)::value;
-                const C2 f = phase_of(wat<x>(base, s, P), g);
+                const C2 f = phase_tab(wat<x>(base, s, P), T);
                 const real pr = re_of<x>(v[x]), pi = im_of<x>(v[x]);
                 v[x] = mk<x>(pr * f.x + pi * f.y, pi * f.x - pr * f.y);
                 const real lr = re_of<x>(w[x]), li = im_of<x>(w[x]);
@@ -1388,7 +1406,7 @@ __global__ void __launch_bounds__(kSmallThreadsGrad) small_grad_kernel(const __g
         if (k > 0) {
             const C2* Tk = reinterpret_cast<const C2*>(j.phase) + (size_t)k * j.E1;
             for (uint32_t z = tid; z < dim; z += kSmallThreadsGrad) {
-                const C2 f = W ? phase_of(wsum_full(W, j.m, 2 + k, z), Tk[0]) : Tk[cut_count_full(gm, n, z)];
+                const C2 f = W ? phase_tab(wsum_full(W, j.m, 2 + k, z), Tk) : Tk[cut_count_full(gm, n, z)];
                 const C2 fc = make_c2(f.x, -f.y);
                 ps[z] = cmul(ps[z], fc);
                 lm[z] = cmul(lm[z], fc);
@@ -1424,7 +1442,7 @@ __device__ __forceinline__ void small_body(const SmallJob& j) {
     for (int k = 0; k < j.levels; ++k) {
         const C2* T = reinterpret_cast<const C2*>(j.phase) + (size_t)k * j.E1;
         if (W)
-            for (uint32_t z = tid; z < dim; z += kSmallThreads) st[z] = cmul(st[z], phase_of(wsum_full(W, j.m, 2 + k, z), T[0]));
+            for (uint32_t z = tid; z < dim; z += kSmallThreads) st[z] = cmul(st[z], phase_tab(wsum_full(W, j.m, 2 + k, z), T));
         else
             for (uint32_t z = tid; z < dim; z += kSmallThreads) st[z] = cmul(st[z], __ldg(T + cut_count_full(gm, n, z)));
         const C2 cs = mix[3 * k];
@@ -1539,7 +1557,10 @@ __global__ void coeff_kernel(const __grid_constant__ CoeffArgs a) {
     if (k >= a.levels) return;  // levels == 0: only the endpoint and value rows
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < a.E1; c += gridDim.x * blockDim.x) {
         double s, co;
-        sincos(a.gamma[k] * (double)c, &s, &co);
+        if (a.weighted)  // rotation steps of a turn (the weighted sums carry gamma_k)
+            sincospi((double)c * (2.0 / kWTurnSteps), &s, &co);
+        else
+            sincos(a.gamma[k] * (double)c, &s, &co);
         double re = co * mult, im = -s * mult;
         if (last) {  // (re + i im)(gre + i gim), exact for g in {1, -i, -1, i}
             const double r2 = re * a.gre - im * a.gim, i2 = re * a.gim + im * a.gre;

@@ -172,6 +172,28 @@ def test_weighted_phase_samples_n30(B):
 
 
 @pytest.mark.parametrize("prec", ["c64", "c128"])
+@pytest.mark.parametrize("n", [11, 16])
+def test_weighted_phase_every_amplitude(B, prec, n):
+    """beta = 0: psi_z = 2^(-n/2) exp(-i sum_k gamma_k C(z)) exactly, so every amplitude checks the
+    weighted phase (fixed-point angle sums, 256-step rotation table and the remainder's series)
+    against exp of the oracle's cut value.  complex128: 1e-13 of the amplitude, far below a
+    dropped series term (~2e-12) or a wrong table step (~0.02); complex64: 1e-6 (float
+    rounding of the table and products over two levels).  n = 11 runs the small-state kernel,
+    n = 16 the tile passes; the angles span many turns of the table."""
+    g = weighted(I.regular3(n, n) if n % 2 == 0 else I.gnp(n, 0.3, n), 41, lo=0.1, hi=2.0)
+    gamma = np.array([2.9, -5.3])
+    cuts = oracle_weighted_cuts(g)
+    amp = 2.0 ** (-n / 2)
+    ref = amp * np.exp(-1j * gamma.sum() * cuts)
+    s = B.QAOAState(g, prec)
+    s.apply_layers(gamma, np.zeros(2))
+    psi = s.amplitudes().astype(np.complex128)
+    s.close()
+    err = np.max(np.abs(psi - ref)) / amp
+    assert err < (1e-13 if prec == "c128" else 1e-6), err
+
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
 def test_weights_all_one_take_the_unit_path(B, prec):
     g = I.gnp(17, 0.4, 3)
     g1 = I.Graph(n=g.n, edges=g.edges, weights=np.ones(g.m), name=g.name + "+ones")
