@@ -63,13 +63,15 @@ struct HostGraph {
 int table_entries(const HostGraph& g) { return g.weighted ? kWTurnSteps : g.m + 1; }
 
 // 2^S for the value weights: the largest power of two with sum |w_e| 2^S <= 2^(B-2), B the
-// fixed-point word size of the precision (32 for complex64, 64 for complex128).
+// fixed-point word size of the precision (32 for complex64, 64 for complex128), and S <= 1000 so
+// that 2^S stays finite for the tiniest weights (those then round to zero, within the
+// m 2^-(S+1) bound).
 double value_mul(const HostGraph& g, int prec) {
     double tot = 0.0;
     for (double x : g.w) tot += std::fabs(x);
     const int B = prec == QAOA_C64 ? 32 : 64;
     if (!(tot > 0.0)) return std::ldexp(1.0, B - 2);
-    return std::ldexp(1.0, B - 2 - (int)std::ceil(std::log2(tot)));
+    return std::ldexp(1.0, std::min(1000, B - 2 - (int)std::ceil(std::log2(tot))));
 }
 
 qaoa_status encode_graph(const qaoa_graph* g, HostGraph& hg) {

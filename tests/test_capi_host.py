@@ -59,6 +59,19 @@ def test_invalid_graph_rejected_before_any_gpu_work(lib, edges, msg):
     assert msg in str(ei.value)
 
 
+@pytest.mark.parametrize("w,msg", [(np.nan, "non-finite"), (np.inf, "non-finite"), (-np.inf, "non-finite"),
+                                   (1.5e12, "1e12")])
+def test_invalid_weights_rejected_before_any_gpu_work(lib, w, msg):
+    g = I.gnp(8, 0.5, 3)
+    wts = np.linspace(0.5, 1.5, g.m)
+    wts[g.m // 2] = w
+    bad = I.Graph(n=g.n, edges=g.edges, weights=wts)
+    with pytest.raises(lib.QAOAError) as ei:
+        lib.qaoa_state_init(bad, "c64", 1 << 20, 1 << 20, 0)
+    assert ei.value.status == lib.QAOA_ERR_INVALID
+    assert msg in str(ei.value)
+
+
 def test_invalid_sizes_rejected(lib):
     g = I.ring(5)
     with pytest.raises(lib.QAOAError):

@@ -194,6 +194,29 @@ def test_weighted_phase_every_amplitude(B, prec, n):
 
 
 @pytest.mark.parametrize("prec", ["c64", "c128"])
+@pytest.mark.parametrize("n", [11, 16])
+def test_weight_scale_covariance(B, prec, n):
+    """Weights times 2^-600 with gamma times 2^600: the per-edge angles gamma w are the same
+    doubles and the value rows the same integers (the scale 2^S moves with them), so the state
+    is bit-identical and <C> exactly 2^-600 times the unscaled one; tiny weights keep their
+    relative accuracy."""
+    g = weighted(I.regular3(n, n) if n % 2 == 0 else I.gnp(n, 0.3, n), 43, lo=-1.0, hi=2.0)
+    k = 2.0 ** -600
+    gs = I.Graph(n=g.n, edges=g.edges, weights=g.weights * k)
+    gamma, beta = np.array([0.45, -1.2]), np.array([0.3, 0.8])
+    out = []
+    for gg, gm in ((g, gamma), (gs, gamma / k)):
+        s = B.QAOAState(gg, prec)
+        s.apply_layers(gm, beta)
+        c, nrm = s.expectation()
+        out.append((s.amplitudes(), c, nrm))
+        s.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[1][1] == out[0][1] * k
+    assert out[1][2] == out[0][2]
+
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
 def test_weights_all_one_take_the_unit_path(B, prec):
     g = I.gnp(17, 0.4, 3)
     g1 = I.Graph(n=g.n, edges=g.edges, weights=np.ones(g.m), name=g.name + "+ones")
