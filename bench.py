@@ -35,11 +35,19 @@ METRIC = "QAOA layers/s"
 UNIT = "layers/s"
 # DRAM bytes (read + write) per launch of the read+write pass kernel from an ncu capture of the
 # same kernel build (None when the kernel changed since it was captured), for 2^n amplitudes.
-# Captured at n = 28 (the full-size state is too large for a multi-metric capture): 4.2320 GB
-# per launch (2.1476 GB read + 2.0844 GB written, the same for the group-0, fused and last
-# passes), against 4.2950 GB algorithmic; a pass reads and writes every amplitude once, so the
-# traffic scales with 2^n.
-NCU_TRAFFIC_BYTES_PER_AMPLITUDE = 4.2320e9 / 2 ** 28
+# Captured at n = 28 (the full-size state is too large for a multi-metric capture), against
+# 4.2950 GB algorithmic per launch: the group-0 and fused passes 4.2317 GB (2.1476 GB read +
+# 2.0841 GB written: the last writes of a launch are still in L2 when it ends), the last pass of
+# a step 4.3465 GB (2.1476 + 2.1990: it also writes back what the passes before it left in L2).
+# A pass reads and writes every amplitude once, so the traffic scales with 2^n.
+NCU_TRAFFIC_BYTES_PER_AMPLITUDE = 4.2317e9 / 2 ** 28
+NCU_TRAFFIC_LAST_PASS_BYTES_PER_AMPLITUDE = 4.3465e9 / 2 ** 28
+
+
+def traffic_per_launch(n: int, rw_passes_per_step: int):
+    """Mean DRAM bytes per read+write pass launch of a step (one of them the last pass)."""
+    k = max(1, rw_passes_per_step)
+    return (1 << n) * ((k - 1) * NCU_TRAFFIC_BYTES_PER_AMPLITUDE + NCU_TRAFFIC_LAST_PASS_BYTES_PER_AMPLITUDE) / k
 
 
 def parse_args():
@@ -356,7 +364,7 @@ def run_ours(args):
         bytes_per_launch = 2.0 * elem * (1 << g.n)
         achieved = bytes_per_launch / per_launch_s / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": (NCU_TRAFFIC_BYTES_PER_AMPLITUDE * (1 << g.n)
+                "traffic": (traffic_per_launch(g.n, prof["pass_launches"] // max(1, args.steps))
                             if NCU_TRAFFIC_BYTES_PER_AMPLITUDE and args.prec == "c64" and g.weights is None else None),
                 "peak_kind": f"{peak_kind} copy bandwidth",
                 "kernel": "tile_kernel (read+write state pass)",

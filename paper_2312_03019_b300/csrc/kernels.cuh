@@ -1000,7 +1000,7 @@ __global__ void __launch_bounds__(1 << (Q - R), tile_min_blocks<real, kW>(kRecip
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int sE[Q];
     __shared__ int sK;
-    __shared__ double sred[2][T::NT / 32];
+
     __shared__ WA sKw[kW ? kWSlots : 1];
     __shared__ WA sEw[kW ? kWSlots : 1][Q];
 
@@ -1141,20 +1141,23 @@ __global__ void __launch_bounds__(1 << (Q - R), tile_min_blocks<real, kW>(kRecip
     }
 
     if (did_expect) {
-        accC = warp_sum_double(accC);
-        accN = warp_sum_double(accN);
-        if ((tid & 31u) == 0) {
-            sred[0][tid >> 5] = accC;
-            sred[1][tid >> 5] = accN;
-        }
+        // FP64 sums by warp 0 alone (FP64 adds issue at 1/64 of the FP32 rate here), through
+        // the tile buffer once every thread is past its last exchange
+        double* red = reinterpret_cast<double*>(tile);
         __syncthreads();
-        if (tid == 0) {
+        red[tid] = accC;
+        red[T::NT + tid] = accN;
+        __syncthreads();
+        if (tid < 32) {
             double sc = 0.0, sn = 0.0;
-            for (int w = 0; w < T::NT / 32; ++w) {
-                sc += sred[0][w];
-                sn += sred[1][w];
+#pragma unroll
+            for (int i = 0; i < T::NT / 32; ++i) {
+                sc += red[tid + 32 * i];
+                sn += red[T::NT + tid + 32 * i];
             }
-            a.partials[t] = make_double2(sc, sn);
+            sc = warp_sum_double(sc);
+            sn = warp_sum_double(sn);
+            if (tid == 0) a.partials[t] = make_double2(sc, sn);
         }
     }
 }
@@ -1173,7 +1176,7 @@ __global__ void __launch_bounds__(1 << (Q - R), sizeof(real) == 4 ? 2 : 1) grad_
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int sE[Q];
     __shared__ int sK;
-    __shared__ double sred[4][T::NT / 32];
+
     __shared__ WA sKw[kW ? kWSlots : 1];
     __shared__ WA sEw[kW ? kWSlots : 1][Q];
 
@@ -1275,18 +1278,25 @@ __global__ void __launch_bounds__(1 << (Q - R), sizeof(real) == 4 ? 2 : 1) grad_
         }
     }
 #undef QAOA_BY_LAYOUT
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const double r = warp_sum_double(acc[k]);
-        if ((tid & 31u) == 0) sred[k][tid >> 5] = r;
-    }
+    // summed in FP64 by warp 0 alone, through the tile buffer once every thread is past its
+    // last exchange
+    double* red = reinterpret_cast<double*>(tile);
     __syncthreads();
-    if (tid == 0) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) red[k * T::NT + tid] = acc[k];
+    __syncthreads();
+    if (tid < 32) {
         double r[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int wi = 0; wi < T::NT / 32; ++wi)
-            for (int k = 0; k < 4; ++k) r[k] += sred[k][wi];
-        a.partials[2 * t] = make_double2(r[0], r[1]);
-        a.partials[2 * t + 1] = make_double2(r[2], r[3]);
+#pragma unroll
+        for (int i = 0; i < T::NT / 32; ++i)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) r[k] += red[k * T::NT + tid + 32 * i];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) r[k] = warp_sum_double(r[k]);
+        if (tid == 0) {
+            a.partials[2 * t] = make_double2(r[0], r[1]);
+            a.partials[2 * t + 1] = make_double2(r[2], r[3]);
+        }
     }
 }
 
