@@ -355,11 +355,13 @@ def test_max_size_n34_complex128_closed_form(B):
 
 
 @pytest.mark.slow
-def test_full_size_n33_c128_closed_form(B):
-    """complex128 at n = 33 (128 GiB): p = 1 <C> equals the closed form to 1e-12 relative."""
+@pytest.mark.parametrize("n", [30, 33])
+def test_full_size_c128_closed_form(B, n):
+    """complex128 at n = 30 (16 GiB) and n = 33 (128 GiB): p = 1 <C> equals the closed form to
+    1e-12 relative."""
     import torch
     from tests.test_oracle_pins import p1_closed_form
-    g, _, _ = I.workload_regular3_n33_p8()
+    g = I.regular3(n, 0)
     s = B.QAOAState(g, "c128")
     s.apply_layers([0.4], [0.3])
     c, nrm = s.expectation()
@@ -370,12 +372,10 @@ def test_full_size_n33_c128_closed_form(B):
     torch.cuda.empty_cache()
 
 
-def test_full_size_n33_c64_against_c128(B):
-    """The benchmark's run (near-3-regular n = 33, p = 8) in complex64 against the same run in
-    complex128 on the GPU (64 + 128 GiB on the device together): fidelity >= 1 - 1e-5 and <C>
-    within 1e-5 |E|.  The complex128 path itself is pinned at this size by the p = 1 closed form."""
+def _c64_against_c128_on_device(B, g, gamma, beta):
+    """Runs the circuit in both precisions on the GPU and returns (fidelity, <C> c64, <C> c128,
+    norm c128, largest amplitude difference), the overlap taken on the device in chunks."""
     import torch
-    g, gamma, beta = I.workload_regular3_n33_p8()
     s128 = B.QAOAState(g, "c128")
     s128.apply_layers(gamma, beta)
     c128, n128 = s128.expectation()
@@ -397,6 +397,18 @@ def test_full_size_n33_c64_against_c128(B):
     s128.close()
     s64.close()
     torch.cuda.empty_cache()
+    return fid, c64, c128, n128, worst
+
+
+@pytest.mark.parametrize("n", [30, 33])
+def test_full_size_c64_against_c128(B, n):
+    """The benchmark's runs (3-regular n = 30 and near-3-regular n = 33, seed 0, p = 8 seeded
+    levels) in complex64 against the same runs in complex128 on the GPU (at n = 33, 64 + 128 GiB
+    on the device together): fidelity >= 1 - 1e-5 and <C> within 1e-5 |E|.  The complex128 path
+    is pinned at these sizes by the p = 1 closed form."""
+    g = I.regular3(n, 0)
+    gamma, beta = I.angles(8, 0)
+    fid, c64, c128, n128, worst = _c64_against_c128_on_device(B, g, gamma, beta)
     assert abs(n128 - 1) < 1e-12
     assert fid >= 1 - 1e-5, fid
     assert abs(c64 - c128) <= 1e-5 * g.m, (c64, c128)
