@@ -1521,10 +1521,16 @@ __global__ void __launch_bounds__(kSmallThreads) small_batch_kernel(const SmallJ
 // folded into T_k, and those of the chunk's last mixer into the last table as well (real
 // scalars commute with every gate; between two phases the state is off by at most
 // (1 / |f|)^n <= 2^(n/2), far inside the floating-point range).
+// The butterflies use t rounded to the state precision (t~), so f is taken as
+// sign(cos b or sin b) / sqrt(1 + t~^2): each butterfly is then an exact rotation (by atan t~,
+// within half an ulp of t from the requested angle) and the level keeps the norm up to the
+// arithmetic rounding, instead of drifting by f^2 (1 + t~^2) per qubit.
+template <typename real>
 __device__ __forceinline__ double mixer_factor(double beta, int fold) {
     double s, co;
     sincos(beta, &s, &co);
-    return fold ? s : co;
+    const double tr = (double)(real)(fold ? -co / s : s / co);  // the coefficient the passes use
+    return copysign(1.0 / sqrt(1.0 + tr * tr), fold ? s : co);
 }
 
 // Fixed-point rows of an edge-weighted graph (see the weighted split above).  Row 0: endpoints;
@@ -1560,8 +1566,8 @@ __global__ void coeff_kernel(const __grid_constant__ CoeffArgs a) {
     const bool last = k == a.levels - 1;
     double mult = 1.0;
     if (a.fold_factors) {
-        if (k > 0) mult *= pow(mixer_factor(a.beta[k - 1], a.fold[k - 1]), (double)a.n);
-        if (last) mult *= pow(mixer_factor(a.beta[k], a.fold[k]), (double)a.n);
+        if (k > 0) mult *= pow(mixer_factor<real>(a.beta[k - 1], a.fold[k - 1]), (double)a.n);
+        if (last) mult *= pow(mixer_factor<real>(a.beta[k], a.fold[k]), (double)a.n);
     }
     if (a.weighted) coeff_weighted_rows<real>(a, k);
     if (k >= a.levels) return;  // levels == 0: only the endpoint and value rows
