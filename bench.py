@@ -64,6 +64,8 @@ def parse_args():
                     help="the CPU baseline times oracle levels at --cpu-sample-n until this much time has passed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the untimed complex128 rerun that gives the line's error against FP64")
     ap.add_argument("--weighted", action="store_true",
                     help="edge weights U[0.1, 2] on the same graph (Algorithm 2 path), for context")
     ap.add_argument("--cpu-report", action="store_true",
@@ -388,6 +390,8 @@ def run_ours(args):
         "e2e": e2e,
         "expectation": results[-1][0], "norm": results[-1][1],
     }
+    if rank == 0 and not args.no_accuracy:
+        rec["accuracy"] = accuracy_block(B, g, gamma, beta, st, args.prec, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         del st
         torch.cuda.empty_cache()
@@ -398,6 +402,46 @@ def run_ours(args):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def accuracy_block(B, g, gamma, beta, st, prec, dev):
+    """The error of this line's result against FP64: after the timed region, the same circuit is
+    run once more in complex64 on `st` and once in complex128 on the same GPU (the tests pin the
+    complex128 path to the p = 1 closed form at these sizes), and the two states are compared on
+    the device in chunks.  Untimed."""
+    import torch
+    if prec != "c64":
+        return {"reference": "none: this run is complex128 (FP64 throughout)"}
+    need = (16 << g.n) + (6 << 30)
+    free, _ = torch.cuda.mem_get_info(dev)
+    if free < need:
+        return {"unavailable": f"the complex128 rerun needs {need / 2**30:.0f} GiB, {free / 2**30:.0f} GiB free"}
+    st.reset()
+    st.apply_layers(gamma, beta)
+    c64, n64 = st.expectation()
+    ref = B.QAOAState(g, "c128", device=dev)
+    try:
+        ref.apply_layers(gamma, beta)
+        c128, n128 = ref.expectation()
+        t64, t128 = st.as_tensor(), ref.as_tensor()
+        ip = torch.zeros((), dtype=torch.complex128, device=dev)
+        worst = 0.0
+        chunk = 1 << 27
+        for i in range(0, t64.numel(), chunk):
+            a = t64[i:i + chunk].to(torch.complex128)
+            b = t128[i:i + chunk]
+            ip += torch.vdot(b, a)
+            worst = max(worst, (a - b).abs().max().item())
+            del a, b
+        fid = abs(ip.item()) ** 2 / (n64 * n128)
+        del t64, t128
+    finally:
+        ref.close()
+        torch.cuda.empty_cache()
+    return {"reference": "the same circuit in complex128 on this GPU", "expectation": c64,
+            "expectation_ref": c128, "abs_err": c64 - c128, "rel_err": (c64 - c128) / c128 if c128 else None,
+            "norm_err": n64 - 1.0, "fidelity_deficit": 1.0 - fid,
+            "max_amp_err_rel": worst * 2.0 ** (g.n / 2), "untimed": True}
 
 
 def serve_stream(B, reqs, cfg):
