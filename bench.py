@@ -596,6 +596,37 @@ def run_grad(args):
     return 0
 
 
+def serve_accuracy(B, reqs, done, samples=32):
+    """Error of served results against FP64: a seeded sample of the requests is run alone in
+    complex128 (QAOAState, and its adjoint gradient where the request asked for one) and
+    compared with what the server returned.  Untimed."""
+    import numpy as np
+    import torch
+    rng = np.random.default_rng(0)
+    pick = sorted(rng.choice(len(reqs), size=min(samples, len(reqs)), replace=False).tolist())
+    worst_c, worst_g, ngrad = 0.0, 0.0, 0
+    for i in pick:
+        r, d = reqs[i], done[i]
+        s = B.QAOAState(r.graph, "c128")
+        try:
+            if r.want_grad:
+                c, dg, db = s.gradient(r.gamma, r.beta)
+                scale = max(1.0, float(np.max(np.abs(np.concatenate([dg, db])))))
+                err = max(np.max(np.abs(d["d_gamma"] - dg)), np.max(np.abs(d["d_beta"] - db))) / scale
+                worst_g = max(worst_g, float(err))
+                ngrad += 1
+            else:
+                s.apply_layers(r.gamma, r.beta)
+                c, _ = s.expectation()
+            worst_c = max(worst_c, abs(d["expectation"] - c) / max(1, r.graph.m))
+        finally:
+            s.close()
+    torch.cuda.empty_cache()
+    return {"reference": "the same requests run alone in complex128 on this GPU", "sampled": len(pick),
+            "with_gradient": ngrad, "max_abs_err_C_over_edges": worst_c,
+            "max_grad_err_rel": worst_g if ngrad else None, "untimed": True}
+
+
 def run_serve(args):
     import torch
 
@@ -622,6 +653,8 @@ def run_serve(args):
                       "prec": args.prec, "hbm_budget_gib": args.serve_budget_gib},
            "served": served, "serial": serial,
            "speedup_vs_serial": served["requests_per_s"] / serial["requests_per_s"]}
+    if args.prec == "c64" and not args.no_accuracy:
+        rec["accuracy"] = serve_accuracy(B, reqs, done)
     print(json.dumps(rec), flush=True)
     return 0
 
