@@ -592,6 +592,18 @@ def run_grad(args):
            "speedup_vs_central_differences": 4 * p * t_fwd / t_grad,
            "expectation": c}
     s.close()
+    if args.prec == "c64" and not args.no_accuracy:  # the same gradient in complex128 (untimed)
+        r = B.QAOAState(g, "c128")
+        try:
+            c2, dg2, db2 = r.gradient(gamma, beta)
+        finally:
+            r.close()
+        import numpy as np
+        ref = np.concatenate([dg2, db2])
+        err = np.abs(np.concatenate([dg, db]) - ref)
+        rec["accuracy"] = {"reference": "the same gradient in complex128 on this GPU", "abs_err_C": c - c2,
+                           "max_abs_err_grad": float(err.max()),
+                           "max_err_grad_rel": float(err.max() / max(1e-300, np.abs(ref).max())), "untimed": True}
     print(json.dumps(rec), flush=True)
     return 0
 
