@@ -413,3 +413,40 @@ def test_full_size_c64_against_c128(B, n):
     assert fid >= 1 - 1e-5, fid
     assert abs(c64 - c128) <= 1e-5 * g.m, (c64, c128)
     assert worst < 1e-3 * 2 ** (-g.n / 2), worst
+
+
+@pytest.mark.parametrize("n,prec", [(32, "c64"), (32, "c128"), (34, "c64")])
+def test_complete_graph_cut_values_above_255(B, n, prec):
+    """The complete graph K_n at n = 32 and 34 (496 and 561 edges, the most the library takes at
+    n = 34): C(z) = |z| (n - |z|) reaches 256 and 289, beyond one byte, so the phase tables run
+    past entry 255.  beta = 0 gives psi_z = 2^(-n/2) exp(-i sum gamma |z| (n - |z|)) for sampled
+    z (balanced Hamming weights included), and p = 1 matches the closed form."""
+    import torch
+    from tests.test_oracle_pins import p1_closed_form
+    g = I.complete(n)
+    assert g.m == n * (n - 1) // 2
+    rng = np.random.default_rng(n)
+    half = (1 << (n // 2)) - 1
+    idx = np.unique(np.concatenate([rng.integers(0, 1 << n, 200), [0, (1 << n) - 1, half, half << (n - n // 2),
+                                                                    0x5555555555555555 & ((1 << n) - 1)]]))
+    w = np.array([bin(int(z)).count("1") for z in idx])
+    assert (w * (n - w)).max() == (n // 2) * (n - n // 2)
+    gamma = np.array([0.7, 2.3])
+    amp = 2.0 ** (-n / 2)
+    ref = amp * np.exp(-1j * gamma.sum() * (w * (n - w)))
+    s = B.QAOAState(g, prec)
+    s.apply_layers(gamma, np.zeros(2))
+    t = s.as_tensor()
+    samp = t[torch.tensor(idx, device=t.device)].cpu().numpy().astype(np.complex128)
+    del t
+    assert np.max(np.abs(samp - ref)) < (1e-11 if prec == "c128" else 1e-6) * amp
+    s.reset()
+    s.apply_layers([0.4], [0.3])
+    c, nrm = s.expectation()
+    s.close()
+    torch.cuda.empty_cache()
+    ref_c = p1_closed_form(g, 0.4, 0.3)
+    if prec == "c128":
+        assert abs(c - ref_c) <= 1e-12 * abs(ref_c) and abs(nrm - 1) < 1e-12
+    else:
+        assert abs(c - ref_c) <= 1e-5 * g.m and abs(nrm - 1) < 1e-5
