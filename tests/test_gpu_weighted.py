@@ -321,3 +321,34 @@ def test_weighted_rejections(B):
         B.QAOAState(huge, "c64")
     with pytest.raises(B.QAOAError):  # the uint16 table is for cut counts only
         B.qaoa_cut_table(weighted(g, 1))
+
+
+def test_weighted_max_size_n34(B):
+    """n = 34 (128 GiB complex64, four groups, three passes per level) on the weighted path, with
+    every weight 2: exp(-i gamma C_w) = exp(-i 2 gamma C), so beta = 0 gives
+    psi_z = 2^(-n/2) exp(-2 i gamma C(z)) (sampled against the oracle's cut value) and the p = 1
+    <C_w> is twice the unweighted closed form at 2 gamma."""
+    import oracle
+    import torch
+    from tests.test_oracle_pins import p1_closed_form
+    g0 = I.regular3(34, 0)
+    g = I.Graph(n=g0.n, edges=g0.edges, weights=np.full(g0.m, 2.0))
+    n = g.n
+    rng = np.random.default_rng(34)
+    idx = np.unique(np.concatenate([rng.integers(0, 1 << n, 200), [0, (1 << n) - 1, (1 << 33) + 7]]))
+    gamma = np.array([0.35, 1.1])
+    amp = 2.0 ** (-n / 2)
+    ref = amp * np.exp(-2j * gamma.sum() * np.array([oracle.cut_value(g0, int(z)) for z in idx]))
+    s = B.QAOAState(g, "c64")
+    s.apply_layers(gamma, np.zeros(2))
+    t = s.as_tensor()
+    samp = t[torch.tensor(idx, device=t.device)].cpu().numpy().astype(np.complex128)
+    del t
+    assert np.max(np.abs(samp - ref)) < 1e-6 * amp
+    s.reset()
+    s.apply_layers([0.4], [0.3])
+    c, nrm = s.expectation()
+    s.close()
+    torch.cuda.empty_cache()
+    assert abs(c - 2.0 * p1_closed_form(g0, 0.8, 0.3)) <= 1e-5 * float(np.sum(g.weights))
+    assert abs(nrm - 1) < 1e-5
