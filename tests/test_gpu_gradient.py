@@ -185,3 +185,26 @@ def test_state_gradient_method_matches_the_c_call(B):
     c2, dg2, db2 = s.gradient(gamma, beta)  # the kept work buffer is reused
     s.close()
     assert c0 == c1 == c2 and np.array_equal(dg0, dg1) and np.array_equal(db1, db2)
+
+
+@pytest.mark.parametrize("n,prec", [(33, "c64"), (30, "c128")])
+def test_gradient_full_size_p1_closed_form(B, n, prec):
+    """Full size (n = 33 complex64: psi and lambda 64 GiB each; n = 30 complex128), p = 1: the
+    adjoint gradient against the derivatives of the closed-form p = 1 <C> (central differences
+    of the formula in FP64, h = 1e-5, accurate to about 1e-9)."""
+    import torch
+    from tests.test_oracle_pins import p1_closed_form
+    g = I.regular3(n, 0)
+    ga, be = 0.4, 0.3
+    c, dg, db = gpu_gradient(B, g, [ga], [be], prec)
+    torch.cuda.empty_cache()
+    f = lambda x, y: p1_closed_form(g, x, y)
+    h = 1e-5
+    ref_dg = (f(ga + h, be) - f(ga - h, be)) / (2 * h)
+    ref_db = (f(ga, be + h) - f(ga, be - h)) / (2 * h)
+    if prec == "c128":
+        assert abs(c - f(ga, be)) <= 1e-12 * f(ga, be)
+        assert abs(dg[0] - ref_dg) <= 1e-7 * g.m and abs(db[0] - ref_db) <= 1e-7 * g.m
+    else:
+        assert abs(c - f(ga, be)) <= 1e-5 * g.m
+        assert abs(dg[0] - ref_dg) <= 1e-4 * g.m and abs(db[0] - ref_db) <= 1e-4 * g.m
