@@ -389,6 +389,36 @@ TileFn<real> pick_tile_kernel(const TileArgs<PrecTraits<real>::Q>& a, bool weigh
     return weighted ? tile_kernel<real, Q, R, true> : tile_kernel<real, Q, R, false>;
 }
 
+template <typename real>
+using GradFn = void (*)(TileArgs<GradTraits<real>::Q>);
+
+// The straight-line adjoint-pass instantiation of sweep program r (complex64, unit weights).
+template <int r>
+constexpr GradFn<float> grad_recipe_fn() {
+    return grad_kernel<float, GradTraits<float>::Q, GradTraits<float>::R, false, grad_recipe(r).code,
+                       grad_recipe(r).nops>;
+}
+template <typename real>
+GradFn<real> grad_recipe_kernel(int r) {
+    if constexpr (std::is_same<real, float>::value)
+        return r == 0 ? grad_recipe_fn<0>() : r == 1 ? grad_recipe_fn<1>() : grad_recipe_fn<2>();
+    return nullptr;
+}
+
+// The adjoint-pass kernel for a program: a compiled sweep program when one matches (complex64,
+// unit weights), else the interpreting instantiation.
+template <typename real>
+GradFn<real> pick_grad_kernel(const TileArgs<GradTraits<real>::Q>& a, bool weighted) {
+    constexpr int Q = GradTraits<real>::Q, R = GradTraits<real>::R;
+    if (std::is_same<real, float>::value && !weighted && a.nops <= 10) {
+        uint64_t code = 0;
+        for (int i = 0; i < a.nops; ++i) code |= recipe_step(i, a.ops[i].kind, a.ops[i].layout);
+        for (int r = 0; r < kGradRecipes; ++r)
+            if (grad_recipe(r).nops == a.nops && grad_recipe(r).code == code) return grad_recipe_kernel<real>(r);
+    }
+    return weighted ? grad_kernel<real, Q, R, true> : grad_kernel<real, Q, R, false>;
+}
+
 // Dynamic shared-memory limits of every kernel, set once per device (the attribute belongs to
 // the device's instance of the function) and thread-safely (the server's scheduler thread and
 // callers' threads both launch).
@@ -417,6 +447,10 @@ qaoa_status ensure_attributes() {
                                   (int)((1u << GQ) * sizeof(C2))));
     CUDA_TRY(cudaFuncSetAttribute(grad_kernel<real, GQ, GR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)((1u << GQ) * sizeof(C2))));
+    if constexpr (std::is_same<real, float>::value)
+        for (int r = 0; r < kGradRecipes; ++r)
+            CUDA_TRY(cudaFuncSetAttribute(grad_recipe_kernel<real>(r), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)((1u << GQ) * sizeof(C2))));
     CUDA_TRY(cudaFuncSetAttribute(small_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024));
     CUDA_TRY(cudaFuncSetAttribute(small_batch_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024));
     CUDA_TRY(cudaFuncSetAttribute(small_grad_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -988,7 +1022,6 @@ qaoa_status gradient_async(qaoa_state s, int p, const double* gamma, const doubl
             return fail(QAOA_ERR_UNSUPPORTED, ex.what());
         }
         const uint64_t gt = grad_tiles(s->n);
-        auto kfn = s->g.weighted ? grad_kernel<real, Q, R, true> : grad_kernel<real, Q, R, false>;
         const size_t smem = (size_t)(1u << Q) * sizeof(C2);
         qaoa_status ast = ensure_attributes<real>();
         if (ast != QAOA_OK) return ast;
@@ -1006,7 +1039,7 @@ qaoa_status gradient_async(qaoa_state s, int p, const double* gamma, const doubl
             int lev[2] = {-1, -1};
             for (const Op& op : ps.ops)
                 if (op.kind == OP_RXD || op.kind == OP_GRADG) lev[(op.arg >> 16) & 1] = op.arg & 0xffff;
-            kfn<<<(unsigned)gt, 1u << (Q - R), smem, s->stream>>>(a);
+            pick_grad_kernel<real>(a, s->g.weighted)<<<(unsigned)gt, 1u << (Q - R), smem, s->stream>>>(a);
             CUDA_TRY(cudaGetLastError());
             grad_reduce_kernel<<<1, 1024, 0, s->stream>>>(s->d_gpart, gt, lev[0], lev[1], p, s->d_gacc);
             CUDA_TRY(cudaGetLastError());

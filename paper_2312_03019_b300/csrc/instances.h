@@ -1,6 +1,6 @@
 // instances.h -- the heavy kernel template instantiations (the pass kernels and the adjoint-sweep
 // kernels), each compiled in a translation unit of its own (tile_c64.cu, tile_c128.cu,
-// grad_kernels.cu) so that the library builds in parallel.  capi.cu includes this file after
+// grad_kernels.cu, grad_recipes.cu, ...) so that the library builds in parallel.  capi.cu includes this file after
 // kernels.cuh with QAOA_INSTANCE = "extern template" (declarations); each instance unit defines
 // QAOA_OWN_* for the set it owns and instantiates that set with QAOA_INSTANCE = "template".
 // Building this way needs -static-global-template-stub=false (external kernel stubs).
@@ -50,6 +50,18 @@
     QAOA_INSTANCE __global__ void grad_kernel<real, Q, R, true>(const __grid_constant__ TileArgs<Q>);   \
     }
 
+// complex64 adjoint-sweep passes specialised to the compiled sweep programs (unit weights; the
+// complex128 ones spill at 255 registers and stay on the interpreting instance)
+#define QAOA_GRAD_RECIPE(real, Q, R, r)                                                               \
+    QAOA_INSTANCE __global__ void grad_kernel<real, Q, R, false, grad_recipe(r).code, grad_recipe(r).nops>( \
+        const __grid_constant__ TileArgs<Q>);
+#define QAOA_GRAD_RECIPE_INSTANCES(real, Q, R)                                                        \
+    namespace qaoa {                                                                                   \
+    QAOA_GRAD_RECIPE(real, Q, R, 0)                                                                    \
+    QAOA_GRAD_RECIPE(real, Q, R, 1)                                                                    \
+    QAOA_GRAD_RECIPE(real, Q, R, 2)                                                                    \
+    }
+
 #if !defined(QAOA_OWN_TILE_C64)
 QAOA_TILE_INSTANCES(float, 13, 5)
 #endif
@@ -66,4 +78,7 @@ QAOA_RECIPE_INSTANCES(double, 12, 4)
 #if !defined(QAOA_OWN_GRAD)
 QAOA_GRAD_INSTANCES(float, 12, 4)
 QAOA_GRAD_INSTANCES(double, 12, 4)
+#endif
+#if !defined(QAOA_OWN_GRAD_RECIPES)
+QAOA_GRAD_RECIPE_INSTANCES(float, 12, 4)
 #endif

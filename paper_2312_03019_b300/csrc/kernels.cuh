@@ -991,6 +991,25 @@ __host__ __device__ constexpr int tile_min_blocks(uint64_t recipe, int nops) {
     return QAOA_TILE_MIN_BLOCKS;
 }
 
+// Adjoint-sweep pass programs compiled as straight-line grad_kernel instantiations: 0 the
+// group-0 pass and 1 the fused boundary pass of sweeps with three or more groups (n >= 21),
+// 2 the high-group pass of two-group sweeps; other programs run the interpreting instance.
+__host__ __device__ constexpr Recipe grad_recipe(int r) {
+    return r == 0 ? Recipe{recipe_step(0, OP_LOAD, 1) | recipe_step(1, OP_RXD, 0) | recipe_step(2, OP_XCHG, 2) |
+                               recipe_step(3, OP_RXD, 0) | recipe_step(4, OP_XCHG, 0) | recipe_step(5, OP_RXD, 0) |
+                               recipe_step(6, OP_STORE, 0),
+                           7}
+         : r == 1 ? Recipe{recipe_step(0, OP_LOAD, 0) | recipe_step(1, OP_RXD, 0) | recipe_step(2, OP_XCHG, 1) |
+                               recipe_step(3, OP_RXD, 0) | recipe_step(4, OP_GRADG, 0) | recipe_step(5, OP_PHASED, 0) |
+                               recipe_step(6, OP_RXD, 0) | recipe_step(7, OP_XCHG, 0) | recipe_step(8, OP_RXD, 0) |
+                               recipe_step(9, OP_STORE, 0),
+                           10}
+                  : Recipe{recipe_step(0, OP_LOAD, 0) | recipe_step(1, OP_RXD, 0) | recipe_step(2, OP_GRADG, 0) |
+                               recipe_step(3, OP_PHASED, 0) | recipe_step(4, OP_RXD, 0) | recipe_step(5, OP_STORE, 0),
+                           6};
+}
+constexpr int kGradRecipes = 3;
+
 template <typename real, int Q, int R, bool kW, uint64_t kRecipe = 0, int kNops = 0, uint64_t kMasks = 0>
 __global__ void __launch_bounds__(1 << (Q - R), tile_min_blocks<real, kW>(kRecipe, kNops))
     tile_kernel(const __grid_constant__ TileArgs<Q> a) {
@@ -1168,7 +1187,7 @@ __global__ void __launch_bounds__(1 << (Q - R), tile_min_blocks<real, kW>(kRecip
 // tile_kernel.  Per CTA it writes, for accumulator slots 0 and 1, (sum of RXD pair terms,
 // sum of GRADG terms) to partials[2 t + slot].
 // (complex64 holds both states in 64 registers and runs two CTAs per SM; complex128 needs 128)
-template <typename real, int Q, int R, bool kW>
+template <typename real, int Q, int R, bool kW, uint64_t kRecipe = 0, int kNops = 0>
 __global__ void __launch_bounds__(1 << (Q - R), sizeof(real) == 4 ? 2 : 1) grad_kernel(const __grid_constant__ TileArgs<Q> a) {
     using T = Tile<real, Q, R>;
     using C2 = typename T::C2;
@@ -1220,7 +1239,43 @@ __global__ void __launch_bounds__(1 << (Q - R), sizeof(real) == 4 ? 2 : 1) grad_
         else T::template F<2>(__VA_ARGS__);        \
     } while (0)
 
-    for (int i = 0; i < a.nops; ++i) {
+    if constexpr (kNops > 0) {  // a compiled program: kinds and layouts are template constants
+        T::template for_x<kNops>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            constexpr int kind = recipe_kind(kRecipe, i);
+            constexpr int Lc = recipe_layout(kRecipe, i);
+            constexpr int Lp = i == 0 ? 0 : recipe_layout(kRecipe, i - 1);
+            if constexpr (kind == OP_LOAD) {
+                T::template load_from<Lc>(v, c, tid, a.state);
+                T::template load_from<Lc>(w, c, tid, a.state2);
+            } else if constexpr (kind == OP_XCHG) {
+                __syncthreads();
+                T::template to_smem<Lp>(v, tile, tid);
+                __syncthreads();
+                T::template from_smem<Lc>(v, tile, tid);
+                __syncthreads();
+                T::template to_smem<Lp>(w, tile, tid);
+                __syncthreads();
+                T::template from_smem<Lc>(w, tile, tid);
+            } else if constexpr (kind == OP_RXD) {
+                const Op op = a.ops[i];
+                const C2 cs = reinterpret_cast<const C2*>(a.mix)[3 * (op.arg & 0xffff)];
+                const double d = (double)T::rx_dual(v, w, op.mask, cs.x, cs.y);
+                if (op.arg >> 16) acc[2] += d;
+                else acc[0] += d;
+            } else if constexpr (kind == OP_GRADG) {
+                const double d = (double)T::template grad_gamma<Lc, kW>(v, w, c, tid);
+                if (a.ops[i].arg >> 16) acc[3] += d;
+                else acc[1] += d;
+            } else if constexpr (kind == OP_PHASED) {
+                T::template phase_dual<Lc, kW>(v, w, c, tid, a.ops[i].arg);
+            } else if constexpr (kind == OP_STORE) {
+                T::template store_to<Lc>(v, c, tid, a.state);
+                T::template store_to<Lc>(w, c, tid, a.state2);
+            }
+        });
+    }
+    for (int i = 0; kNops == 0 && i < a.nops; ++i) {
         const Op op = a.ops[i];
         switch (op.kind) {
             case OP_LOAD:
