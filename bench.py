@@ -33,21 +33,18 @@ from paper_2312_03019_b300 import inputs as I  # noqa: E402
 
 METRIC = "QAOA layers/s"
 UNIT = "layers/s"
-# DRAM bytes (read + write) per launch of the read+write pass kernel from an ncu capture of the
-# same kernel build (None when the kernel changed since it was captured), for 2^n amplitudes.
-# Captured at n = 28 (the full-size state is too large for a multi-metric capture), against
-# 4.2950 GB algorithmic per launch: the group-0 and fused passes 4.2317 GB (2.1476 GB read +
-# 2.0841 GB written: the last writes of a launch are still in L2 when it ends), the last pass of
-# a step 4.3465 GB (2.1476 + 2.1990: it also writes back what the passes before it left in L2).
-# A pass reads and writes every amplitude once, so the traffic scales with 2^n.
-NCU_TRAFFIC_BYTES_PER_AMPLITUDE = 4.2317e9 / 2 ** 28
-NCU_TRAFFIC_LAST_PASS_BYTES_PER_AMPLITUDE = 4.3465e9 / 2 ** 28
-
-
-def traffic_per_launch(n: int, rw_passes_per_step: int):
-    """Mean DRAM bytes per read+write pass launch of a step (one of them the last pass)."""
-    k = max(1, rw_passes_per_step)
-    return (1 << n) * ((k - 1) * NCU_TRAFFIC_BYTES_PER_AMPLITUDE + NCU_TRAFFIC_LAST_PASS_BYTES_PER_AMPLITUDE) / k
+# DRAM bytes (read + write) per launch of each read+write pass kind (the library's profile
+# categories: [0] the mixer-only pass (group 0 at n <= 33), [1] the fused boundary pass with the cost phase,
+# [2] the last pass with <C>), complex64, unit weights, per amplitude, from one ncu capture of
+# the same kernel build at n = 28 (the full-size state is too large for a multi-metric capture),
+# against 16 B per amplitude algorithmic (4.2950 GB per launch at n = 28): 4.2319, 4.2313 and
+# 4.3465 GB.  A pass's last writes are still in L2 when it ends; the last pass of a step also
+# writes back what the passes before it left there.  A pass reads and writes every amplitude
+# once, so the traffic scales with 2^n.
+NCU_TRAFFIC_BY_KIND = (4.2319e9 / 2 ** 28, 4.2313e9 / 2 ** 28, 4.3465e9 / 2 ** 28)
+PASS_KINDS = ("tile_kernel, mixer-only pass (read+write; the group-0 pass at n <= 33)",
+              "tile_kernel, fused boundary pass with the cost phase (read+write)",
+              "tile_kernel, last pass with <C> (read+write)")
 
 
 def parse_args():
@@ -361,17 +358,35 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     elem = 8 if args.prec == "c64" else 16
     roof = None
+    layer_frac = None
     if prof["pass_launches"] > 0:
-        per_launch_s = prof["pass_ms"] / prof["pass_launches"] / 1e3
+        # the dominant kernel: the pass kind with the most event time in the timed steps (one
+        # instantiation of tile_kernel each); the all-pass mean is given beside it
         bytes_per_launch = 2.0 * elem * (1 << g.n)
-        achieved = bytes_per_launch / per_launch_s / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": (traffic_per_launch(g.n, prof["pass_launches"] // max(1, args.steps))
-                            if NCU_TRAFFIC_BYTES_PER_AMPLITUDE and args.prec == "c64" and g.weights is None else None),
-                "peak_kind": f"{peak_kind} copy bandwidth",
-                "kernel": "tile_kernel (read+write state pass)",
-                "bytes_per_launch": bytes_per_launch, "launch_ms": per_launch_s * 1e3,
-                "launches": prof["pass_launches"]}
+        known = args.prec == "c64" and g.weights is None
+        kinds = []
+        for c, name in enumerate(PASS_KINDS):
+            L = prof["kind_launches"][c]
+            if not L:
+                continue
+            ms = prof["kind_ms"][c] / L
+            ach = bytes_per_launch / (ms / 1e3) / 1e9
+            kinds.append({"kernel": name, "launches": L, "launch_ms": ms, "achieved": ach, "frac": ach / peak,
+                          "share_of_timed_ms": prof["kind_ms"][c] / ms_max,
+                          "traffic": NCU_TRAFFIC_BY_KIND[c] * (1 << g.n) if known else None})
+        dom = max(kinds, key=lambda d: d["launch_ms"] * d["launches"])
+        mean_ms = prof["pass_ms"] / prof["pass_launches"]
+        roof = {"bound": "hbm", "achieved": dom["achieved"], "peak": peak, "unit": "GB/s", "frac": dom["frac"],
+                "traffic": dom["traffic"], "peak_kind": f"{peak_kind} copy bandwidth", "kernel": dom["kernel"],
+                "bytes_per_launch": bytes_per_launch, "launch_ms": dom["launch_ms"], "launches": dom["launches"],
+                "all_read_write_passes": {"launches": prof["pass_launches"], "launch_ms": mean_ms,
+                                          "achieved": bytes_per_launch / (mean_ms / 1e3) / 1e9,
+                                          "frac": bytes_per_launch / (mean_ms / 1e3) / 1e9 / peak},
+                "per_kind": kinds}
+        # every byte the step's passes move (read+write passes and the write-only first pass) over
+        # the passes' event time: the fraction of peak per layer
+        moved = prof["pass_bytes"] + prof["synth_bytes"]
+        layer_frac = moved / ((prof["pass_ms"] + prof["synth_ms"]) / 1e3) / 1e9 / peak
     state_gbs = value * 2.0 * elem * (1 << g.n) / 1e9
 
     rec = {
@@ -383,6 +398,7 @@ def run_ours(args):
                    "parallelism": f"{world} independent replicas" if world > 1 else "single GPU"},
         "state_gbs_algorithmic": state_gbs,
         "hbm_frac_algorithmic": state_gbs / world / peak,
+        "hbm_frac_passes": layer_frac,
         "passes_per_step": (prof["pass_launches"] + prof["synth_launches"]) / args.steps,
         "roofline": roof,
         "gpu_launches": prof["kernel_launches"],

@@ -179,6 +179,10 @@ typedef struct {
     int64_t synth_launches;      /* passes that write without reading (deferred |+>^n) */
     double synth_ms;
     double synth_bytes;
+    /* the read+write passes split by program: [0] mixer only, [1] with the cost phase (the
+     * fused boundary passes), [2] with <C> (the last pass) */
+    int64_t kind_launches[3];
+    double kind_ms[3];
 } qaoa_profile_stats;
 
 /* enable != 0 starts recording (and resets the counters); 0 stops. */

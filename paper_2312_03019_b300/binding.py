@@ -55,7 +55,8 @@ class ProfileStats(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_int64), ("pass_launches", ctypes.c_int64),
                 ("pass_ms", ctypes.c_double), ("pass_bytes", ctypes.c_double),
                 ("synth_launches", ctypes.c_int64), ("synth_ms", ctypes.c_double),
-                ("synth_bytes", ctypes.c_double)]
+                ("synth_bytes", ctypes.c_double), ("kind_launches", ctypes.c_int64 * 3),
+                ("kind_ms", ctypes.c_double * 3)]
 
 
 _vp = ctypes.c_void_p
@@ -258,7 +259,10 @@ def qaoa_profile_enable(h: int, enable: bool = True) -> None:
 def qaoa_profile_read(h: int) -> dict:
     st = ProfileStats()
     _check(_lib.qaoa_profile_read(_vp(h), ctypes.byref(st)))
-    return {k: getattr(st, k) for k, _ in ProfileStats._fields_}
+    out = {k: getattr(st, k) for k, _ in ProfileStats._fields_}
+    out["kind_launches"] = list(st.kind_launches)
+    out["kind_ms"] = list(st.kind_ms)
+    return out
 
 
 class QAOAState:

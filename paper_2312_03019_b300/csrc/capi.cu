@@ -263,7 +263,9 @@ uint64_t grad_tiles(int n) { return n > 12 ? 1ull << (n - 12) : 1ull; }
 
 struct EventPair {
     cudaEvent_t a = nullptr, b = nullptr;
-    int kind = 0;  // 1 read+write pass, 2 synthesising pass
+    // 1 read+write mixer-only pass, 2 synthesising pass, 3 read+write pass with a cost phase,
+    // 4 read+write pass with <C>
+    int kind = 0;
 };
 
 }  // namespace
@@ -531,7 +533,13 @@ qaoa_status run_plan(qaoa_state s, const Plan& plan) {
         std::memset(&a, 0, sizeof(a));
         fill_program<real>(a, s, ps);
         int kind = 0;
-        if (ps.store) kind = ps.synth ? 2 : 1;
+        if (ps.store) {
+            kind = ps.synth ? 2 : 1;
+            for (int i = 0; kind == 1 && i < a.nops; ++i) {
+                if (a.ops[i].kind == OP_PHASE) kind = 3;
+                if (a.ops[i].kind == OP_EXPECT) kind = 4;
+            }
+        }
         qaoa_status st = launch_tile<real>(s, a, kind);
         if (st != QAOA_OK) return st;
     }
@@ -1291,11 +1299,15 @@ qaoa_status qaoa_profile_read(qaoa_state s, qaoa_profile_stats* out) {
     for (size_t i = 0; i < s->ev_used; ++i) {
         float ms = 0.f;
         CUDA_TRY(cudaEventElapsedTime(&ms, s->events[i].a, s->events[i].b));
-        if (s->events[i].kind == 1) {
+        const int k = s->events[i].kind;
+        if (k == 1 || k == 3 || k == 4) {
             out->pass_launches++;
             out->pass_ms += ms;
             out->pass_bytes += 2.0 * eb * (double)s->dim;
-        } else if (s->events[i].kind == 2) {
+            const int c = k == 1 ? 0 : (k == 3 ? 1 : 2);
+            out->kind_launches[c]++;
+            out->kind_ms[c] += ms;
+        } else if (k == 2) {
             out->synth_launches++;
             out->synth_ms += ms;
             out->synth_bytes += eb * (double)s->dim;
