@@ -42,6 +42,7 @@ UNIT = "layers/s"
 # writes back what the passes before it left there.  A pass reads and writes every amplitude
 # once, so the traffic scales with 2^n.
 NCU_TRAFFIC_BY_KIND = (4.2319e9 / 2 ** 28, 4.2313e9 / 2 ** 28, 4.3465e9 / 2 ** 28)
+NOMINAL_HBM_GBS = 7700.0  # B300 HBM3e, nominal (the fractions are also given against it)
 PASS_KINDS = ("tile_kernel, mixer-only pass (read+write; the group-0 pass at n <= 33)",
               "tile_kernel, fused boundary pass with the cost phase (read+write)",
               "tile_kernel, last pass with <C> (read+write)")
@@ -372,12 +373,14 @@ def run_ours(args):
             ms = prof["kind_ms"][c] / L
             ach = bytes_per_launch / (ms / 1e3) / 1e9
             kinds.append({"kernel": name, "launches": L, "launch_ms": ms, "achieved": ach, "frac": ach / peak,
+                          "frac_nominal": ach / NOMINAL_HBM_GBS,
                           "share_of_timed_ms": prof["kind_ms"][c] / ms_max,
                           "traffic": NCU_TRAFFIC_BY_KIND[c] * (1 << g.n) if known else None})
         dom = max(kinds, key=lambda d: d["launch_ms"] * d["launches"])
         mean_ms = prof["pass_ms"] / prof["pass_launches"]
         roof = {"bound": "hbm", "achieved": dom["achieved"], "peak": peak, "unit": "GB/s", "frac": dom["frac"],
                 "traffic": dom["traffic"], "peak_kind": f"{peak_kind} copy bandwidth", "kernel": dom["kernel"],
+                "peak_nominal": NOMINAL_HBM_GBS, "frac_nominal": dom["achieved"] / NOMINAL_HBM_GBS,
                 "bytes_per_launch": bytes_per_launch, "launch_ms": dom["launch_ms"], "launches": dom["launches"],
                 "all_read_write_passes": {"launches": prof["pass_launches"], "launch_ms": mean_ms,
                                           "achieved": bytes_per_launch / (mean_ms / 1e3) / 1e9,
