@@ -450,3 +450,26 @@ def test_complete_graph_cut_values_above_255(B, n, prec):
         assert abs(c - ref_c) <= 1e-12 * abs(ref_c) and abs(nrm - 1) < 1e-12
     else:
         assert abs(c - ref_c) <= 1e-5 * g.m and abs(nrm - 1) < 1e-5
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("n,mk", [
+    (5, lambda n: I.complete(n)), (11, lambda n: I.gnp(n, 0.4, 11)), (14, lambda n: I.regular3(n, 2)),
+    (16, lambda n: I.gnp(n, 0.3, 16)), (19, lambda n: I.regular3(n, 3)), (21, lambda n: I.gnp(n, 0.25, 21)),
+])
+def test_mixer_only_and_phase_only(B, prec, n, mk):
+    """The two halves of a level alone, whole state, every plan shape from one CTA to two and
+    three groups.  gamma = 0: |+>^n is an eigenstate of every X, so psi_z = 2^(-n/2)
+    exp(-i n sum beta) for every z (beta up to pi: the |tan beta| > 1 form with its pending
+    complement is used).  beta = 0: psi_z = 2^(-n/2) exp(-i sum gamma C(z)) with the oracle's
+    cut values."""
+    import oracle
+    g = mk(n)
+    gamma, beta = I.angles(3, seed=n, gamma_hi=math.pi, beta_hi=math.pi)
+    amp = 2.0 ** (-n / 2)
+    tol = (1e-12 if prec == "c128" else 1e-5) * amp
+    _, _, psi = run(B, g, np.zeros(3), beta, prec)
+    assert np.max(np.abs(psi - amp * np.exp(-1j * n * beta.sum()))) < tol
+    _, _, psi = run(B, g, gamma, np.zeros(3), prec)
+    ref = amp * np.exp(-1j * gamma.sum() * oracle.cut_table(g).astype(np.float64))
+    assert np.max(np.abs(psi - ref)) < (1e-12 if prec == "c128" else 1e-6) * amp
