@@ -185,6 +185,17 @@ typedef struct {
     double kind_ms[3];
 } qaoa_profile_stats;
 
+/* Index checks (a development aid; the paper has no counterpart).  A library built with
+ * -DQAOA_DEBUG_BOUNDS (`python -m paper_2312_03019_b300.build --debug-bounds`, written to
+ * libqaoa_b300_debug.so) checks, in its pass and adjoint kernels, every state load and store,
+ * shared-memory exchange, phase-table read, cut-value write and weighted-row read against the
+ * buffer it belongs to; a failed check sets a bit in one word on the device and skips the access
+ * (1 state load, 2 state store, 4 shared-memory write, 8 shared-memory read, 16 phase-table
+ * read, 32 cut-value write, 64 weighted row read).  This call synchronises `device`, returns the
+ * word in *out_flags (0: no check failed since it was last cleared) and clears it if `clear`.
+ * A release build returns QAOA_ERR_UNSUPPORTED. */
+qaoa_status qaoa_debug_bounds_read(int32_t device, uint32_t *out_flags, int32_t clear);
+
 /* enable != 0 starts recording (and resets the counters); 0 stops. */
 qaoa_status qaoa_profile_enable(qaoa_state s, int32_t enable);
 /* Synchronises the stream and returns the counters since the last enable. */

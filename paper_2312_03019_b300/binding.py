@@ -16,7 +16,8 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libqaoa_b300.so")
+# QAOA_LIBRARY may name another build of the same library (the index-checking debug build)
+LIB_PATH = os.environ.get("QAOA_LIBRARY") or os.path.join(_HERE, "libqaoa_b300.so")
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(
@@ -88,6 +89,7 @@ _sig("qaoa_plan_describe", ctypes.c_int, [_i32, ctypes.c_int, _i32, ctypes.POINT
                                            ctypes.POINTER(_i32)])
 _sig("qaoa_profile_enable", ctypes.c_int, [_vp, _i32])
 _sig("qaoa_profile_read", ctypes.c_int, [_vp, ctypes.POINTER(ProfileStats)])
+_sig("qaoa_debug_bounds_read", ctypes.c_int, [_i32, ctypes.POINTER(ctypes.c_uint32), _i32])
 _sig("qaoa_expectation_static", ctypes.c_int, [ctypes.POINTER(_Graph), ctypes.c_int, _vp, ctypes.c_size_t, _vp, _dp, _dp])
 SERVE_MAX_P = 64
 
@@ -250,6 +252,14 @@ def qaoa_plan_describe(n: int, prec, p: int) -> list:
     buf = (_i32 * max(1, cnt.value))()
     _check(_lib.qaoa_plan_describe(int(n), _prec(prec), int(p), buf, cnt.value, ctypes.byref(cnt)))
     return list(buf[: cnt.value])
+
+
+def qaoa_debug_bounds_read(device: int = 0, clear: bool = True) -> int:
+    """The index-check word of a debug build (0: no check failed); raises QAOAError with
+    QAOA_ERR_UNSUPPORTED on a release build."""
+    f = ctypes.c_uint32()
+    _check(_lib.qaoa_debug_bounds_read(int(device), ctypes.byref(f), 1 if clear else 0))
+    return f.value
 
 
 def qaoa_profile_enable(h: int, enable: bool = True) -> None:

@@ -111,10 +111,32 @@ bool is_small(int n, int prec) { return n <= (prec == QAOA_C64 ? kSmallMaxC64 : 
 
 size_t elem_bytes(int prec) { return prec == QAOA_C64 ? 8 : 16; }
 
+#ifdef QAOA_DEBUG_BOUNDS
+// The index-check word of the debug build (see QAOA_IN_BOUNDS in kernels.cuh).  Host code only
+// holds a stand-in for it: its device address is looked up once per device.
+static __device__ unsigned int g_bounds_flag;
+unsigned* bounds_flag_ptr() {
+    static std::mutex mu;
+    static std::vector<unsigned*> ptrs;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    if ((int)ptrs.size() <= dev) ptrs.resize(dev + 1, nullptr);
+    if (!ptrs[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_bounds_flag) == cudaSuccess) ptrs[dev] = static_cast<unsigned*>(p);
+    }
+    return ptrs[dev];
+}
+#else
+unsigned* bounds_flag_ptr() { return nullptr; }
+#endif
+
 // Per-geometry decomposition tables of the on-the-fly cut count.
 template <int Q>
 void fill_geometry(TileArgs<Q>& a, const HostGraph& hg, const Geometry& geo, const TileConfig& tc) {
     a.n = hg.n;
+    a.bounds_flag = bounds_flag_ptr();
     for (int v = 0; v < kMaxN; ++v) a.gmask[v] = v < hg.n ? hg.upper[v] : 0;
     int lpos[kMaxN];
     for (int w = 0; w < kMaxN; ++w) lpos[w] = -1;
@@ -1287,6 +1309,24 @@ qaoa_status qaoa_profile_enable(qaoa_state s, int32_t enable) {
     s->ev_used = 0;
     s->launches = 0;
     return QAOA_OK;
+}
+
+qaoa_status qaoa_debug_bounds_read(int32_t device, uint32_t* out_flags, int32_t clear) {
+    if (!out_flags) return fail(QAOA_ERR_INVALID, "NULL argument");
+    *out_flags = 0;
+#ifdef QAOA_DEBUG_BOUNDS
+    CUDA_TRY(cudaSetDevice(device));
+    unsigned* p = bounds_flag_ptr();
+    if (!p) return fail(QAOA_ERR_CUDA, "cannot find the index-check word on this device");
+    CUDA_TRY(cudaDeviceSynchronize());
+    CUDA_TRY(cudaMemcpy(out_flags, p, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (clear) CUDA_TRY(cudaMemset(p, 0, sizeof(unsigned)));
+    return QAOA_OK;
+#else
+    (void)device;
+    (void)clear;
+    return fail(QAOA_ERR_UNSUPPORTED, "this library was built without QAOA_DEBUG_BOUNDS (index checks)");
+#endif
 }
 
 qaoa_status qaoa_profile_read(qaoa_state s, qaoa_profile_stats* out) {

@@ -68,6 +68,21 @@ struct C2T<double> {
 __device__ __forceinline__ float2 make_c2(float x, float y) { return make_float2(x, y); }
 __device__ __forceinline__ double2 make_c2(double x, double y) { return make_double2(x, y); }
 
+// Index checks of the debug build (-DQAOA_DEBUG_BOUNDS, `python -m paper_2312_03019_b300.build
+// --debug-bounds`): a failed check sets `bit` in the word at `flag` (TileArgs::bounds_flag) and
+// the access is skipped, so a wrong index is reported instead of reaching memory.  Release
+// builds compile every check to `true`.  Bits: 1 state load, 2 state store, 4 shared-memory
+// write, 8 shared-memory read, 16 phase-table read, 32 cut-value write, 64 weighted row read.
+#ifdef QAOA_DEBUG_BOUNDS
+__device__ __forceinline__ bool qaoa_in_bounds(unsigned* flag, bool ok, unsigned bit) {
+    if (!ok && flag) atomicOr(flag, bit);
+    return ok;
+}
+#define QAOA_IN_BOUNDS(flag, ok, bit) qaoa_in_bounds((flag), (ok), (bit))
+#else
+#define QAOA_IN_BOUNDS(flag, ok, bit) true
+#endif
+
 template <int Q>
 struct TileArgs {
     int32_t n, nops, nruns;
@@ -101,6 +116,7 @@ struct TileArgs {
     const void* mix;     // [3 * level + i]: (cos b, sin b), (t, 0), (f, 0) as complex<real>
     double2* partials;   // [tile] (sum |psi|^2 C, sum |psi|^2); adjoint sweep: [2 tile + slot]
     uint16_t* cutout;    // [2^n] cut values (OP_CUTVAL)
+    unsigned* bounds_flag;  // debug builds: the index-check word (NULL: no reporting)
 };
 
 struct SmallJob {
@@ -422,7 +438,7 @@ struct Tile {
         const WA* __restrict__ W = reinterpret_cast<const WA*>(a.wfix) + (size_t)a.wrow[ls] * a.m;
         for (int i = 0; i < a.wn; ++i) {
             const uint32_t ent = a.wloc[i];
-            const WA f = __ldg(W + (ent & 1023u));
+            const WA f = QAOA_IN_BOUNDS(a.bounds_flag, (int)(ent & 1023u) < a.m, 64u) ? __ldg(W + (ent & 1023u)) : (WA)0;
             const int ua = (ent >> 10) & 15, ub = (ent >> 14) & 15;
             const int ja = ua - rlo(L), jb = ub - rlo(L);
             const bool ra = (unsigned)ja < (unsigned)R, rb = (unsigned)jb < (unsigned)R;
@@ -507,7 +523,10 @@ struct Tile {
         for (int j = 0; j < R; ++j) d[j] = a.rstep[L][j];
         for_x<NE>([&](auto X) {
             constexpr int x = decltype(X)::value;
-            v[x] = to_reg<x>(*g);
+            if (QAOA_IN_BOUNDS(a.bounds_flag, (uint64_t)(g - reinterpret_cast<const C2*>(base)) >> a.n == 0, 1u))
+                v[x] = to_reg<x>(*g);
+            else
+                v[x] = make_c2((real)0, (real)0);
             if constexpr (x + 1 < NE) g += d[ctz_next(x)];
         });
     }
@@ -521,44 +540,59 @@ struct Tile {
         for (int j = 0; j < R; ++j) d[j] = a.rstep[L][j];
         for_x<NE>([&](auto X) {
             constexpr int x = decltype(X)::value;
-            *g = from_reg<x>(v[x]);
+            if (QAOA_IN_BOUNDS(a.bounds_flag, (uint64_t)(g - reinterpret_cast<C2*>(base)) >> a.n == 0, 2u))
+                *g = from_reg<x>(v[x]);
             if constexpr (x + 1 < NE) g += d[ctz_next(x)];
         });
     }
 
     // Shared-memory exchange: byte offset = (swizzled thread part) XOR (compile-time register part).
     template <int L>
-    static __device__ __forceinline__ void to_smem(const C2 (&v)[NE], unsigned char* tile, uint32_t tid) {
+    static __device__ __forceinline__ void to_smem(const C2 (&v)[NE], unsigned char* tile, uint32_t tid,
+                                                   unsigned* bf = nullptr) {
+        constexpr uint32_t kBytes = (1u << Q) * (uint32_t)sizeof(C2);
         const uint32_t P = swz(tbits(L, tid)) * (uint32_t)sizeof(C2);
         if constexpr (kPair && L == 2) {  // register bit 0 is local bit 0: store amplitude pairs
             for_x<NE / 2>([&](auto H) {
                 constexpr int x = 2 * decltype(H)::value;
                 const C2 a = from_reg<x>(v[x]), b = from_reg<x + 1>(v[x + 1]);
-                *reinterpret_cast<float4*>(tile + (P ^ (swz((uint32_t)x) * 8u))) =
-                    make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
+                const uint32_t o = P ^ (swz((uint32_t)x) * 8u);
+                if (QAOA_IN_BOUNDS(bf, o + 16u <= kBytes && (o & 15u) == 0, 4u))
+                    *reinterpret_cast<float4*>(tile + o) = make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
             });
         } else {
             for_x<NE>([&](auto X) {
                 constexpr int x = decltype(X)::value;
-                *reinterpret_cast<C2*>(tile + (P ^ (swz((uint32_t)x << rlo(L)) * (uint32_t)sizeof(C2)))) = from_reg<x>(v[x]);
+                const uint32_t o = P ^ (swz((uint32_t)x << rlo(L)) * (uint32_t)sizeof(C2));
+                if (QAOA_IN_BOUNDS(bf, o + (uint32_t)sizeof(C2) <= kBytes, 4u))
+                    *reinterpret_cast<C2*>(tile + o) = from_reg<x>(v[x]);
             });
         }
     }
 
     template <int L>
-    static __device__ __forceinline__ void from_smem(C2 (&v)[NE], const unsigned char* tile, uint32_t tid) {
+    static __device__ __forceinline__ void from_smem(C2 (&v)[NE], const unsigned char* tile, uint32_t tid,
+                                                     unsigned* bf = nullptr) {
+        constexpr uint32_t kBytes = (1u << Q) * (uint32_t)sizeof(C2);
         const uint32_t P = swz(tbits(L, tid)) * (uint32_t)sizeof(C2);
         if constexpr (kPair && L == 2) {
             for_x<NE / 2>([&](auto H) {
                 constexpr int x = 2 * decltype(H)::value;
-                const float4 q = *reinterpret_cast<const float4*>(tile + (P ^ (swz((uint32_t)x) * 8u)));
+                const uint32_t o = P ^ (swz((uint32_t)x) * 8u);
+                float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (QAOA_IN_BOUNDS(bf, o + 16u <= kBytes && (o & 15u) == 0, 8u))
+                    q = *reinterpret_cast<const float4*>(tile + o);
                 v[x] = to_reg<x>(make_c2((real)q.x, (real)q.y));
                 v[x + 1] = to_reg<x + 1>(make_c2((real)q.z, (real)q.w));
             });
         } else {
             for_x<NE>([&](auto X) {
                 constexpr int x = decltype(X)::value;
-                v[x] = to_reg<x>(*reinterpret_cast<const C2*>(tile + (P ^ (swz((uint32_t)x << rlo(L)) * (uint32_t)sizeof(C2)))));
+                const uint32_t o = P ^ (swz((uint32_t)x << rlo(L)) * (uint32_t)sizeof(C2));
+                if (QAOA_IN_BOUNDS(bf, o + (uint32_t)sizeof(C2) <= kBytes, 8u))
+                    v[x] = to_reg<x>(*reinterpret_cast<const C2*>(tile + o));
+                else
+                    v[x] = make_c2((real)0, (real)0);
             });
         }
     }
@@ -617,6 +651,7 @@ struct Tile {
             for (int j = 0; j < R; ++j)
                 if ((x >> j) & 1) cidx += s[j];
             // the count is always in [0, |E|]; the unsigned clamp keeps every table read in bounds
+            (void)QAOA_IN_BOUNDS(a.bounds_flag, (unsigned)cidx < (unsigned)a.E1, 16u);
             v[x] = apply_phase<x>(v[x], __ldg(T + min((unsigned)cidx, (unsigned)(a.E1 - 1))), c.sg);
         });
     }
@@ -669,7 +704,8 @@ struct Tile {
 #pragma unroll
                 for (int j = 0; j < R; ++j)
                     if ((x >> j) & 1) o += a.rstride[L][j];
-                g[o] = (double)(SWA)wat<x>(base, s, P) * a.vscale;
+                if (QAOA_IN_BOUNDS(a.bounds_flag, (uint64_t)(g + o - a.cutout_w) >> a.n == 0, 32u))
+                    g[o] = (double)(SWA)wat<x>(base, s, P) * a.vscale;
             });
             return;
         }
@@ -686,7 +722,7 @@ struct Tile {
                     cidx += s[j];
                     o += a.rstride[L][j];
                 }
-            g[o] = (uint16_t)cidx;
+            if (QAOA_IN_BOUNDS(a.bounds_flag, (uint64_t)(g + o - a.cutout) >> a.n == 0, 32u)) g[o] = (uint16_t)cidx;
         }
     }
 
@@ -813,6 +849,7 @@ struct Tile {
 #pragma unroll
             for (int j = 0; j < R; ++j)
                 if ((x >> j) & 1) cidx += s[j];
+            (void)QAOA_IN_BOUNDS(a.bounds_flag, (unsigned)cidx < (unsigned)a.E1, 16u);
             const C2 f = __ldg(T + min((unsigned)cidx, (unsigned)(a.E1 - 1)));
             const real pr = re_of<x>(v[x]), pi = im_of<x>(v[x]);
             v[x] = mk<x>(pr * f.x + pi * f.y, pi * f.x - pr * f.y);
@@ -1078,9 +1115,9 @@ __global__ void __launch_bounds__(1 << (Q - R), tile_min_blocks<real, kW>(kRecip
                 T::template load<Lc>(v, c, tid);
             } else if constexpr (kind == OP_XCHG) {
                 __syncthreads();
-                T::template to_smem<Lp>(v, tile, tid);
+                T::template to_smem<Lp>(v, tile, tid, a.bounds_flag);
                 __syncthreads();
-                T::template from_smem<Lc>(v, tile, tid);
+                T::template from_smem<Lc>(v, tile, tid, a.bounds_flag);
             } else if constexpr (kind == OP_RX) {
                 const Op op = a.ops[i];
                 constexpr uint32_t fm = (uint32_t)((kMasks >> (6 * i)) & 63u);
@@ -1121,14 +1158,14 @@ __global__ void __launch_bounds__(1 << (Q - R), tile_min_blocks<real, kW>(kRecip
                 break;
             case OP_XCHG:
                 __syncthreads();
-                if (L == 0) T::template to_smem<0>(v, tile, tid);
-                else if (L == 1) T::template to_smem<1>(v, tile, tid);
-                else T::template to_smem<2>(v, tile, tid);
+                if (L == 0) T::template to_smem<0>(v, tile, tid, a.bounds_flag);
+                else if (L == 1) T::template to_smem<1>(v, tile, tid, a.bounds_flag);
+                else T::template to_smem<2>(v, tile, tid, a.bounds_flag);
                 __syncthreads();
                 L = op.layout;
-                if (L == 0) T::template from_smem<0>(v, tile, tid);
-                else if (L == 1) T::template from_smem<1>(v, tile, tid);
-                else T::template from_smem<2>(v, tile, tid);
+                if (L == 0) T::template from_smem<0>(v, tile, tid, a.bounds_flag);
+                else if (L == 1) T::template from_smem<1>(v, tile, tid, a.bounds_flag);
+                else T::template from_smem<2>(v, tile, tid, a.bounds_flag);
                 break;
             case OP_RX:
                 T::rx(v, op.mask, c.sg * reinterpret_cast<const C2*>(a.mix)[3 * op.arg + 1].x);
@@ -1250,13 +1287,13 @@ __global__ void __launch_bounds__(1 << (Q - R), sizeof(real) == 4 ? 2 : 1) grad_
                 T::template load_from<Lc>(w, c, tid, a.state2);
             } else if constexpr (kind == OP_XCHG) {
                 __syncthreads();
-                T::template to_smem<Lp>(v, tile, tid);
+                T::template to_smem<Lp>(v, tile, tid, a.bounds_flag);
                 __syncthreads();
-                T::template from_smem<Lc>(v, tile, tid);
+                T::template from_smem<Lc>(v, tile, tid, a.bounds_flag);
                 __syncthreads();
-                T::template to_smem<Lp>(w, tile, tid);
+                T::template to_smem<Lp>(w, tile, tid, a.bounds_flag);
                 __syncthreads();
-                T::template from_smem<Lc>(w, tile, tid);
+                T::template from_smem<Lc>(w, tile, tid, a.bounds_flag);
             } else if constexpr (kind == OP_RXD) {
                 const Op op = a.ops[i];
                 const C2 cs = reinterpret_cast<const C2*>(a.mix)[3 * (op.arg & 0xffff)];
@@ -1291,16 +1328,16 @@ __global__ void __launch_bounds__(1 << (Q - R), sizeof(real) == 4 ? 2 : 1) grad_
             case OP_XCHG: {
                 const int Lold = L;
                 __syncthreads();
-                QAOA_BY_LAYOUT(to_smem, v, tile, tid);
+                QAOA_BY_LAYOUT(to_smem, v, tile, tid, a.bounds_flag);
                 __syncthreads();
                 L = op.layout;
-                QAOA_BY_LAYOUT(from_smem, v, tile, tid);
+                QAOA_BY_LAYOUT(from_smem, v, tile, tid, a.bounds_flag);
                 __syncthreads();
                 L = Lold;
-                QAOA_BY_LAYOUT(to_smem, w, tile, tid);
+                QAOA_BY_LAYOUT(to_smem, w, tile, tid, a.bounds_flag);
                 __syncthreads();
                 L = op.layout;
-                QAOA_BY_LAYOUT(from_smem, w, tile, tid);
+                QAOA_BY_LAYOUT(from_smem, w, tile, tid, a.bounds_flag);
                 break;
             }
             case OP_RXD: {

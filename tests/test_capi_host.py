@@ -40,6 +40,13 @@ def test_library_exports_every_declared_symbol(lib):
     assert not missing, missing
 
 
+def test_index_checks_only_in_the_debug_build(lib):
+    # the release library has no index checks: the call says so without touching a GPU
+    with pytest.raises(lib.QAOAError) as ei:
+        lib.qaoa_debug_bounds_read(0)
+    assert ei.value.status == lib.QAOA_ERR_UNSUPPORTED
+
+
 def test_state_bytes(lib):
     assert lib.qaoa_state_bytes(10, "c64") == 8 << 10
     assert lib.qaoa_state_bytes(33, "c64") == 8 << 33
