@@ -255,6 +255,10 @@ typedef struct {
     const double *gamma;  /* p angles, copied at submit */
     const double *beta;   /* p angles, copied at submit */
     int32_t want_grad;    /* 1: also d<C>/d gamma, d<C>/d beta (adjoint sweep) */
+    double deadline_s;    /* 0: none; else seconds after submit by which the request must have
+                           * been dispatched to the GPU: one still queued then completes with
+                           * status QAOA_ERR_TIMEOUT without running (work already dispatched
+                           * always finishes) */
 } qaoa_request;
 
 typedef struct {
@@ -275,6 +279,7 @@ typedef struct {
     int64_t submitted, completed, failed, rejected_full;
     int64_t batches, batched_requests, single_requests, graph_launches;
     size_t arena_peak_bytes;
+    int64_t timed_out;    /* requests whose deadline passed before dispatch (counted in failed) */
 } qaoa_server_stats;
 
 typedef struct qaoa_server_s *qaoa_server;
@@ -284,8 +289,8 @@ typedef struct qaoa_server_s *qaoa_server;
 qaoa_status qaoa_server_create(const qaoa_server_config *cfg, qaoa_server *out);
 /* Queues a request (graph and angles are copied); *ticket identifies it.  Edge-weighted graphs
  * are accepted and always run alone (never packed with other small requests).  QAOA_ERR_AGAIN when the
- * queue is full; QAOA_ERR_INVALID for a bad request; QAOA_ERR_OOM when its footprint exceeds the
- * whole arena.  Thread-safe. */
+ * queue is full; QAOA_ERR_INVALID for a bad request (including a negative or non-finite
+ * deadline); QAOA_ERR_OOM when its footprint exceeds the whole arena.  Thread-safe. */
 qaoa_status qaoa_submit(qaoa_server sv, const qaoa_request *r, uint64_t *ticket);
 /* Non-blocking: QAOA_PENDING while the request is queued or running; QAOA_OK with *out filled
  * (the ticket is then released); QAOA_ERR_INVALID for an unknown ticket.  Thread-safe. */

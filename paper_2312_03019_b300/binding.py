@@ -100,7 +100,8 @@ class ServerConfig(ctypes.Structure):
 
 
 class Request(ctypes.Structure):
-    _fields_ = [("graph", _Graph), ("p", _i32), ("gamma", _dp), ("beta", _dp), ("want_grad", _i32)]
+    _fields_ = [("graph", _Graph), ("p", _i32), ("gamma", _dp), ("beta", _dp), ("want_grad", _i32),
+                ("deadline_s", ctypes.c_double)]
 
 
 class Result(ctypes.Structure):
@@ -114,7 +115,7 @@ class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
                 ("rejected_full", ctypes.c_int64), ("batches", ctypes.c_int64), ("batched_requests", ctypes.c_int64),
                 ("single_requests", ctypes.c_int64), ("graph_launches", ctypes.c_int64),
-                ("arena_peak_bytes", ctypes.c_size_t)]
+                ("arena_peak_bytes", ctypes.c_size_t), ("timed_out", ctypes.c_int64)]
 
 
 _sig("qaoa_server_create", ctypes.c_int, [ctypes.POINTER(ServerConfig), ctypes.POINTER(_vp)])
@@ -353,12 +354,15 @@ def qaoa_server_create(hbm_budget_bytes: int, prec="c64", max_inflight: int = 64
     return h.value
 
 
-def qaoa_submit(sv: int, g, gamma, beta, want_grad: bool = False) -> int:
-    """Returns the ticket; raises QAOAError (status QAOA_ERR_AGAIN when the queue is full)."""
+def qaoa_submit(sv: int, g, gamma, beta, want_grad: bool = False, deadline_s: float = 0.0) -> int:
+    """Returns the ticket; raises QAOAError (status QAOA_ERR_AGAIN when the queue is full).
+    deadline_s > 0: a request not dispatched within that many seconds completes with status
+    QAOA_ERR_TIMEOUT without running."""
     gs, keep = _graph(g)
     ga = np.ascontiguousarray(np.asarray(gamma, dtype=np.float64).reshape(-1))
     be = np.ascontiguousarray(np.asarray(beta, dtype=np.float64).reshape(-1))
-    req = Request(gs, int(ga.size), ga.ctypes.data_as(_dp), be.ctypes.data_as(_dp), 1 if want_grad else 0)
+    req = Request(gs, int(ga.size), ga.ctypes.data_as(_dp), be.ctypes.data_as(_dp), 1 if want_grad else 0,
+                  float(deadline_s))
     t = ctypes.c_uint64()
     _check(_lib.qaoa_submit(_vp(sv), ctypes.byref(req), ctypes.byref(t)))
     return t.value

@@ -76,6 +76,7 @@ struct SReq {
     std::vector<double> gamma, beta;
     bool grad = false;
     double t_submit = 0.0;
+    double deadline = 0.0;  // server clock by which it must be dispatched (0: none)
 };
 
 // Device block of a request that runs alone (offsets from the block start).
@@ -534,7 +535,23 @@ bool scheduler_turn(qaoa_server_s* sv) {
         sv->batches.pop_back();
         progress = true;
     }
-    // (2) admission in arrival order, (3) packing, (4) dispatch
+    // (2) requests still queued past their deadline complete with QAOA_ERR_TIMEOUT, unrun
+    if (!sv->pending.empty()) {
+        const double now = sv->now();
+        for (auto it = sv->pending.begin(); it != sv->pending.end();) {
+            if (it->deadline > 0.0 && now > it->deadline) {
+                qaoa_result res = base_result(*it, now, now);
+                res.status = QAOA_ERR_TIMEOUT;
+                finish(sv, *it, res);
+                bump(sv, &qaoa_server_stats::timed_out, 1);
+                it = sv->pending.erase(it);
+                progress = true;
+            } else {
+                ++it;
+            }
+        }
+    }
+    // (3) admission in arrival order, (4) packing, (5) dispatch
     std::vector<SReq> small;
     std::vector<size_t> small_offs;
     size_t head_off = 0;
@@ -697,6 +714,8 @@ qaoa_status qaoa_submit(qaoa_server sv, const qaoa_request* r, uint64_t* ticket)
     if (r->p < 1 || r->p > QAOA_SERVE_MAX_P) return fail(QAOA_ERR_INVALID, "p out of range for the server");
     if (!r->gamma || !r->beta) return fail(QAOA_ERR_INVALID, "angle array is NULL");
     if (!angles_ok(r->p, r->gamma) || !angles_ok(r->p, r->beta)) return fail(QAOA_ERR_INVALID, "non-finite angle");
+    if (!(r->deadline_s >= 0.0) || !std::isfinite(r->deadline_s))
+        return fail(QAOA_ERR_INVALID, "deadline must be finite and >= 0");
     SReq q;
     qaoa_status st = encode_graph(&r->graph, q.g);
     if (st != QAOA_OK) return st;
@@ -716,6 +735,7 @@ qaoa_status qaoa_submit(qaoa_server sv, const qaoa_request* r, uint64_t* ticket)
     }
     q.ticket = sv->next_ticket++;
     q.t_submit = sv->now();
+    q.deadline = r->deadline_s > 0.0 ? q.t_submit + r->deadline_s : 0.0;
     *ticket = q.ticket;
     sv->live.insert(q.ticket);
     sv->queue.push_back(std::move(q));
