@@ -19,6 +19,8 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/qaoa.h"
 #include "kernels.cuh"
 #include "instances.h"
@@ -110,6 +112,16 @@ qaoa_status encode_graph(const qaoa_graph* g, HostGraph& hg) {
 bool is_small(int n, int prec) { return n <= (prec == QAOA_C64 ? kSmallMaxC64 : kSmallMaxC128); }
 
 size_t elem_bytes(int prec) { return prec == QAOA_C64 ? 8 : 16; }
+
+// NVTX ranges (header-only NVTX 3): a profiler that records them (Nsight Systems, or ncu's
+// --nvtx filters) sees each API call and each state pass by name; without one attached a push
+// and a pop cost nanoseconds.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 #ifdef QAOA_DEBUG_BOUNDS
 // The index-check word of the debug build (see QAOA_IN_BOUNDS in kernels.cuh).  Host code only
@@ -562,6 +574,10 @@ qaoa_status run_plan(qaoa_state s, const Plan& plan) {
                 if (a.ops[i].kind == OP_EXPECT) kind = 4;
             }
         }
+        static const char* const kPassName[] = {"qaoa pass (read only)", "qaoa pass (mixer)",
+                                                "qaoa pass (first, synthesised)", "qaoa pass (fused, cost phase)",
+                                                "qaoa pass (last, <C>)"};
+        NvtxRange range(kPassName[kind]);
         qaoa_status st = launch_tile<real>(s, a, kind);
         if (st != QAOA_OK) return st;
     }
@@ -1069,6 +1085,7 @@ qaoa_status gradient_async(qaoa_state s, int p, const double* gamma, const doubl
             int lev[2] = {-1, -1};
             for (const Op& op : ps.ops)
                 if (op.kind == OP_RXD || op.kind == OP_GRADG) lev[(op.arg >> 16) & 1] = op.arg & 0xffff;
+            NvtxRange range("qaoa adjoint pass");
             pick_grad_kernel<real>(a, s->g.weighted)<<<(unsigned)gt, 1u << (Q - R), smem, s->stream>>>(a);
             CUDA_TRY(cudaGetLastError());
             grad_reduce_kernel<<<1, 1024, 0, s->stream>>>(s->d_gpart, gt, lev[0], lev[1], p, s->d_gacc);
@@ -1187,6 +1204,7 @@ qaoa_status qaoa_apply_layers(qaoa_state s, int32_t p, const double* gamma, cons
     if (p > 0 && (!gamma || !beta)) return fail(QAOA_ERR_INVALID, "angle array is NULL");
     if (!angles_ok(p, gamma) || !angles_ok(p, beta)) return fail(QAOA_ERR_INVALID, "non-finite angle");
     CUDA_TRY(cudaSetDevice(s->dev));
+    NvtxRange range("qaoa_apply_layers");
     if (p == 0) return s->prec == QAOA_C64 ? materialize<float>(s) : materialize<double>(s);
     for (int k0 = 0; k0 < p; k0 += kLayerChunk) {
         const int levels = std::min(kLayerChunk, p - k0);
@@ -1209,6 +1227,7 @@ qaoa_status qaoa_gradient(qaoa_state s, int32_t p, const double* gamma, const do
     if (((uintptr_t)dev_work & 15u) != 0) return fail(QAOA_ERR_INVALID, "work buffer not 16-byte aligned");
     if (dev_work == s->buf) return fail(QAOA_ERR_INVALID, "work buffer must differ from the state buffer");
     CUDA_TRY(cudaSetDevice(s->dev));
+    NvtxRange range("qaoa_gradient");
     double c = 0.0;
     qaoa_status st = s->prec == QAOA_C64 ? gradient_impl<float>(s, p, gamma, beta, dev_work, &c, d_gamma, d_beta)
                                          : gradient_impl<double>(s, p, gamma, beta, dev_work, &c, d_gamma, d_beta);
