@@ -153,22 +153,24 @@ def test_c128_server_gradient(B):
 
 
 def test_deadline_expires_while_queued(B):
-    """With one request in flight at a time, a gradient at n = 24 holds the GPU: requests queued
-    behind it with a 0.1 ms deadline complete with QAOA_ERR_TIMEOUT without running, one with a
-    60 s deadline and the gradient itself complete normally; bad deadlines are rejected at submit."""
-    sv = B.qaoa_server_create(hbm_budget_bytes=2 << 30, prec="c64", max_inflight=1)
+    """With one request in flight at a time, a gradient at n = 26 holds the GPU for several
+    milliseconds: requests queued behind it with a 0.1 ms deadline complete with
+    QAOA_ERR_TIMEOUT without running; one with a 60 s deadline and the gradient itself complete
+    normally; bad deadlines are rejected at submit.  Every input is prepared before the first
+    submit, so all requests are queued while the gradient runs."""
+    g_big = I.gnp(26, 0.5, 0)
+    ga, be = I.angles(6, 0)
+    shorts = [(I.regular3(16, i), *I.angles(2, i)) for i in range(3)]
+    g_ok = I.regular3(16, 9)
+    g2, b2 = I.angles(2, 9)
+    sv = B.qaoa_server_create(hbm_budget_bytes=4 << 30, prec="c64", max_inflight=1)
     try:
-        ga, be = I.angles(6, 0)
-        big = B.qaoa_submit(sv, I.gnp(24, 0.5, 0), ga, be, want_grad=True)
-        short = []
-        for i in range(3):
-            g2, b2 = I.angles(2, i)
-            short.append(B.qaoa_submit(sv, I.regular3(16, i), g2, b2, deadline_s=1e-4))
-        g2, b2 = I.angles(2, 9)
-        ok = B.qaoa_submit(sv, I.regular3(16, 9), g2, b2, deadline_s=60.0)
+        big = B.qaoa_submit(sv, g_big, ga, be, want_grad=True)
+        short = [B.qaoa_submit(sv, g, x, y, deadline_s=1e-4) for g, x, y in shorts]
+        ok = B.qaoa_submit(sv, g_ok, g2, b2, deadline_s=60.0)
         for bad in (-1.0, float("nan"), float("inf")):
             with pytest.raises(B.QAOAError) as ei:
-                B.qaoa_submit(sv, I.regular3(16, 9), g2, b2, deadline_s=bad)
+                B.qaoa_submit(sv, g_ok, g2, b2, deadline_s=bad)
             assert ei.value.status == B.QAOA_ERR_INVALID
         res = wait_all(B, sv, [big] + short + [ok])
         stats = B.qaoa_server_stats_read(sv)
@@ -176,9 +178,10 @@ def test_deadline_expires_while_queued(B):
         B.qaoa_server_destroy(sv)
     assert res[big]["status"] == B.QAOA_OK and res[big]["has_grad"]
     assert res[ok]["status"] == B.QAOA_OK
-    c, _, _ = alone(B, I.regular3(16, 9), g2, b2, False)
+    c, _, _ = alone(B, g_ok, g2, b2, False)
     assert res[ok]["expectation"] == c
     for t in short:
         assert res[t]["status"] == B.QAOA_ERR_TIMEOUT
         assert res[t]["t_done"] - res[t]["t_submit"] >= 1e-4
+        assert res[t]["t_submit"] < res[big]["t_done"]
     assert stats["timed_out"] == 3
