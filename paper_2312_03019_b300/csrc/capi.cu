@@ -364,7 +364,7 @@ using TileFn = void (*)(TileArgs<PrecTraits<real>::Q>);
 template <typename real, int r, bool kW = false>
 constexpr TileFn<real> recipe_fn() {
     return tile_kernel<real, PrecTraits<real>::Q, PrecTraits<real>::R, kW, recipe_def(r).code, recipe_def(r).nops,
-                       recipe_masks<real>(r)>;
+                       recipe_masks<real>(r), recipe_def(r).hi>;
 }
 
 // The weighted (complex64) instantiation of recipe r, or NULL where none is compiled.
@@ -383,8 +383,20 @@ TileFn<real> recipe_kernel_w(int r) {
     return nullptr;
 }
 
+// The unit-weight instantiation of recipe r, or NULL where none is compiled (the two-group
+// programs 8..11 exist for complex64 only).
 template <typename real>
 TileFn<real> recipe_kernel(int r) {
+    if constexpr (std::is_same<real, float>::value) {
+        switch (r) {
+            case 8: return recipe_fn<real, 8>();
+            case 9: return recipe_fn<real, 9>();
+            case 10: return recipe_fn<real, 10>();
+            case 11: return recipe_fn<real, 11>();
+            default: break;
+        }
+    }
+    if (r >= 8) return nullptr;
     switch (r) {
         case 0: return recipe_fn<real, 0>();
         case 1: return recipe_fn<real, 1>();
@@ -405,20 +417,27 @@ template <typename real>
 TileFn<real> pick_tile_kernel(const TileArgs<PrecTraits<real>::Q>& a, bool weighted_graph) {
     constexpr int Q = PrecTraits<real>::Q, R = PrecTraits<real>::R;
     const bool weighted = weighted_graph && a.need_cut;
-    if (a.nops <= 10) {
-        uint64_t code = 0;
-        for (int i = 0; i < a.nops; ++i) code |= recipe_step(i, a.ops[i].kind, a.ops[i].layout);
-        const int order[] = {1, 5, 7, 0, 2, 3, 4};  // the full-mask fused pass (6) spills: not used
+    if (a.nops <= 20) {
+        uint64_t code = 0, hi = 0;
+        for (int i = 0; i < a.nops; ++i) {
+            code |= recipe_step_lo(i, a.ops[i].kind, a.ops[i].layout);
+            hi |= recipe_step_hi(i, a.ops[i].kind, a.ops[i].layout);
+        }
+        // the full-mask fused pass (6) spills: not used
+        const int order[] = {1, 5, 7, 0, 2, 3, 4, 8, 9, 10, 11};
         for (int r : order) {
             const Recipe d = recipe_def(r);
-            if (d.nops != a.nops || d.code != code) continue;
+            if (d.nops != a.nops || d.code != code || d.hi != hi) continue;
             bool masks_ok = true;
-            for (int i = 0; i < a.nops; ++i) {
+            for (int i = 0; i < a.nops && i < 10; ++i) {
                 const uint32_t fm = (uint32_t)((recipe_masks<real>(r) >> (6 * i)) & 63u);
                 if ((fm & 32u) && a.ops[i].mask != (fm & 31u)) masks_ok = false;
             }
             if (!masks_ok) continue;
-            if (!weighted) return recipe_kernel<real>(r);
+            if (!weighted) {
+                if (TileFn<real> f = recipe_kernel<real>(r)) return f;
+                continue;
+            }
             if (TileFn<real> f = recipe_kernel_w<real>(r)) return f;
         }
     }
@@ -473,8 +492,8 @@ qaoa_status ensure_attributes() {
     CUDA_TRY(cudaFuncSetAttribute(tile_kernel<real, Q, R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)((1u << Q) * sizeof(C2))));
     for (int r = 0; r < kRecipes; ++r) {
-        CUDA_TRY(cudaFuncSetAttribute(recipe_kernel<real>(r), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)((1u << Q) * sizeof(C2))));
+        if (TileFn<real> f = recipe_kernel<real>(r))
+            CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)((1u << Q) * sizeof(C2))));
         if (TileFn<real> f = recipe_kernel_w<real>(r))
             CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)((1u << Q) * sizeof(C2))));
     }

@@ -50,6 +50,20 @@
     QAOA_INSTANCE __global__ void grad_kernel<real, Q, R, true>(const __grid_constant__ TileArgs<Q>);   \
     }
 
+// complex64 passes of the two-group plans (recipes 8..11, runtime masks; recipe 9 has 13 ops and
+// uses the second program word)
+#define QAOA_RECIPE_2G(real, Q, R, r)                                                                 \
+    QAOA_INSTANCE __global__ void tile_kernel<real, Q, R, false, recipe_def(r).code, recipe_def(r).nops, \
+                                              recipe_masks<real>(r), recipe_def(r).hi>(                 \
+        const __grid_constant__ TileArgs<Q>);
+#define QAOA_RECIPE_2G_INSTANCES(real, Q, R)                                                          \
+    namespace qaoa {                                                                                   \
+    QAOA_RECIPE_2G(real, Q, R, 8)                                                                      \
+    QAOA_RECIPE_2G(real, Q, R, 9)                                                                      \
+    QAOA_RECIPE_2G(real, Q, R, 10)                                                                     \
+    QAOA_RECIPE_2G(real, Q, R, 11)                                                                     \
+    }
+
 // complex64 adjoint-sweep passes specialised to the compiled sweep programs (unit weights; the
 // complex128 ones spill at 255 registers and stay on the interpreting instance)
 #define QAOA_GRAD_RECIPE(real, Q, R, r)                                                               \
@@ -78,6 +92,9 @@ QAOA_RECIPE_INSTANCES(double, 12, 4)
 #if !defined(QAOA_OWN_GRAD)
 QAOA_GRAD_INSTANCES(float, 12, 4)
 QAOA_GRAD_INSTANCES(double, 12, 4)
+#endif
+#if !defined(QAOA_OWN_RECIPE_2G_C64)
+QAOA_RECIPE_2G_INSTANCES(float, 13, 5)
 #endif
 #if !defined(QAOA_OWN_GRAD_RECIPES)
 QAOA_GRAD_RECIPE_INSTANCES(float, 12, 4)

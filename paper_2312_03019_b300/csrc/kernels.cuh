@@ -957,9 +957,28 @@ __host__ __device__ constexpr uint64_t recipe_step(int i, int kind, int layout) 
 }
 
 struct Recipe {
-    uint64_t code;
+    uint64_t code;    // ops 0..9
     int nops;
+    uint64_t hi = 0;  // ops 10..19 (6 bits each, from bit 0)
 };
+// Kind and layout of op i of a program held in two words (ops 0..9 in lo, 10..19 in hi).
+__host__ __device__ constexpr int recipe_kind2(uint64_t lo, uint64_t hi, int i) {
+    return i < 10 ? recipe_kind(lo, i) : recipe_kind(hi, i - 10);
+}
+__host__ __device__ constexpr int recipe_layout2(uint64_t lo, uint64_t hi, int i) {
+    int L = 0;
+    for (int k = 0; k <= i; ++k)
+        if (sets_layout(recipe_kind2(lo, hi, k)))
+            L = (int)(((k < 10 ? lo >> (6 * k) : hi >> (6 * (k - 10))) >> 4) & 3u);
+    return L;
+}
+// Step i of a two-word program: in lo for i < 10, else in hi.
+__host__ __device__ constexpr uint64_t recipe_step_lo(int i, int kind, int layout) {
+    return i < 10 ? recipe_step(i, kind, layout) : 0;
+}
+__host__ __device__ constexpr uint64_t recipe_step_hi(int i, int kind, int layout) {
+    return i < 10 ? 0 : recipe_step(i - 10, kind, layout);
+}
 // Compiled-in RX masks of a recipe, 6 bits per op (bit 5 set: the op's register mask is bits
 // 0..4; clear: the mask is a runtime argument).
 __host__ __device__ constexpr uint64_t fixed_mask(int i, uint32_t m) { return (uint64_t)(32u | m) << (6 * i); }
@@ -990,8 +1009,37 @@ constexpr Recipe kRecipe0 = base_recipe(0), kRecipe1 = base_recipe(1), kRecipe2 
 // Instantiations 5..7 are recipes 0, 2 and 3 again with every RX mask compiled in as full (the
 // high-group passes of 10-bit complex64 / 8-bit complex128 groups, as at n = 33); the host
 // tries them before the runtime-mask versions.
-constexpr int kRecipes = 8;
-__host__ __device__ constexpr Recipe recipe_def(int r) { return base_recipe(r == 5 ? 0 : r == 6 ? 2 : r == 7 ? 3 : r); }
+// The complex64 programs of the two-group plans (n = 15..23, and n = 24's small fused passes):
+// 8 first pass, 9 fused group-0 boundary pass (13 ops: three layouts on each side of the phase),
+// 10 last pass, 11 fused pass of a high group that fits one register layout.
+__host__ __device__ constexpr Recipe two_group_recipe(int r) {
+    constexpr int kSteps9[13][2] = {{OP_LOAD, 0}, {OP_RX, 0}, {OP_XCHG, 2}, {OP_RX, 0}, {OP_XCHG, 1},
+                                    {OP_RX, 0},   {OP_PHASE, 0}, {OP_RX, 0}, {OP_XCHG, 2}, {OP_RX, 0},
+                                    {OP_XCHG, 0}, {OP_RX, 0},   {OP_STORE, 0}};
+    if (r == 1) {
+        Recipe d{0, 13, 0};
+        for (int i = 0; i < 13; ++i) {
+            d.code |= recipe_step_lo(i, kSteps9[i][0], kSteps9[i][1]);
+            d.hi |= recipe_step_hi(i, kSteps9[i][0], kSteps9[i][1]);
+        }
+        return d;
+    }
+    return r == 0 ? Recipe{recipe_step(0, OP_SYNTH, 1) | recipe_step(1, OP_PHASE, 0) | recipe_step(2, OP_RX, 0) |
+                               recipe_step(3, OP_XCHG, 2) | recipe_step(4, OP_RX, 0) | recipe_step(5, OP_XCHG, 0) |
+                               recipe_step(6, OP_RX, 0) | recipe_step(7, OP_STORE, 0),
+                           8}
+         : r == 2 ? Recipe{recipe_step(0, OP_LOAD, 1) | recipe_step(1, OP_RX, 0) | recipe_step(2, OP_XCHG, 2) |
+                               recipe_step(3, OP_RX, 0) | recipe_step(4, OP_XCHG, 0) | recipe_step(5, OP_RX, 0) |
+                               recipe_step(6, OP_EXPECT, 0) | recipe_step(7, OP_STORE, 0),
+                           8}
+                  : Recipe{recipe_step(0, OP_LOAD, 0) | recipe_step(1, OP_RX, 0) | recipe_step(2, OP_PHASE, 0) |
+                               recipe_step(3, OP_RX, 0) | recipe_step(4, OP_STORE, 0),
+                           5};
+}
+constexpr int kRecipes = 12;
+__host__ __device__ constexpr Recipe recipe_def(int r) {
+    return r >= 8 ? two_group_recipe(r - 8) : base_recipe(r == 5 ? 0 : r == 6 ? 2 : r == 7 ? 3 : r);
+}
 // Compiled-in masks.  The group-0 pass (recipe 1) always covers its Q bits with the same masks:
 // complex64 (R = 5) layouts 1, 2, 0 take local bits 3..7, 0..2 (the layout-2 op skips bits 3, 4,
 // done already), 8..12; complex128 (R = 4) takes 4..7, 0..3, 8..11.  Masks compiled in remove
@@ -1002,7 +1050,7 @@ __host__ __device__ constexpr uint64_t recipe_masks(int r) {
     if (r == 1)
         return sizeof(real) == 4 ? (fixed_mask(1, 31) | fixed_mask(3, 7) | fixed_mask(5, 31))
                                  : (fixed_mask(1, 15) | fixed_mask(3, 15) | fixed_mask(5, 15));
-    if (r < 5) return 0;
+    if (r < 5 || r >= 8) return 0;
     const Recipe d = recipe_def(r);
     uint64_t m = 0;
     for (int i = 0; i < d.nops; ++i)
@@ -1047,7 +1095,8 @@ __host__ __device__ constexpr Recipe grad_recipe(int r) {
 }
 constexpr int kGradRecipes = 3;
 
-template <typename real, int Q, int R, bool kW, uint64_t kRecipe = 0, int kNops = 0, uint64_t kMasks = 0>
+template <typename real, int Q, int R, bool kW, uint64_t kRecipe = 0, int kNops = 0, uint64_t kMasks = 0,
+          uint64_t kRecipeHi = 0>
 __global__ void __launch_bounds__(1 << (Q - R), tile_min_blocks<real, kW>(kRecipe, kNops))
     tile_kernel(const __grid_constant__ TileArgs<Q> a) {
     using T = Tile<real, Q, R, true>;
@@ -1101,9 +1150,9 @@ __global__ void __launch_bounds__(1 << (Q - R), tile_min_blocks<real, kW>(kRecip
         const C2* mix = reinterpret_cast<const C2*>(a.mix);
         T::template for_x<kNops>([&](auto I) {
             constexpr int i = decltype(I)::value;
-            constexpr int kind = recipe_kind(kRecipe, i);
-            constexpr int Lc = recipe_layout(kRecipe, i);
-            constexpr int Lp = i == 0 ? 0 : recipe_layout(kRecipe, i - 1);
+            constexpr int kind = recipe_kind2(kRecipe, kRecipeHi, i);
+            constexpr int Lc = recipe_layout2(kRecipe, kRecipeHi, i);
+            constexpr int Lp = i == 0 ? 0 : recipe_layout2(kRecipe, kRecipeHi, i - 1);
             if constexpr (kind == OP_SYNTH) {
                 const real amp = (real)a.init_amp;
                 T::template for_x<T::NE>([&](auto X) {
@@ -1120,7 +1169,7 @@ __global__ void __launch_bounds__(1 << (Q - R), tile_min_blocks<real, kW>(kRecip
                 T::template from_smem<Lc>(v, tile, tid, a.bounds_flag);
             } else if constexpr (kind == OP_RX) {
                 const Op op = a.ops[i];
-                constexpr uint32_t fm = (uint32_t)((kMasks >> (6 * i)) & 63u);
+                constexpr uint32_t fm = i < 10 ? (uint32_t)((kMasks >> (6 * i)) & 63u) : 0u;
                 if constexpr ((fm & 32u) != 0)
                     T::template rx_fixed<(fm & 31u)>(v, c.sg * mix[3 * op.arg + 1].x);
                 else
