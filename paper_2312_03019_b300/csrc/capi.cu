@@ -384,7 +384,7 @@ TileFn<real> recipe_kernel_w(int r) {
 }
 
 // The unit-weight instantiation of recipe r, or NULL where none is compiled (the two-group
-// programs 8..11 exist for complex64 only).
+// programs 8..12 exist for complex64 only).
 template <typename real>
 TileFn<real> recipe_kernel(int r) {
     if constexpr (std::is_same<real, float>::value) {
@@ -393,6 +393,7 @@ TileFn<real> recipe_kernel(int r) {
             case 9: return recipe_fn<real, 9>();
             case 10: return recipe_fn<real, 10>();
             case 11: return recipe_fn<real, 11>();
+            case 12: return recipe_fn<real, 12>();
             default: break;
         }
     }
@@ -424,7 +425,7 @@ TileFn<real> pick_tile_kernel(const TileArgs<PrecTraits<real>::Q>& a, bool weigh
             hi |= recipe_step_hi(i, a.ops[i].kind, a.ops[i].layout);
         }
         // the full-mask fused pass (6) spills: not used
-        const int order[] = {1, 5, 7, 0, 2, 3, 4, 8, 9, 10, 11};
+        const int order[] = {1, 5, 7, 0, 2, 3, 4, 8, 9, 10, 11, 12};
         for (int r : order) {
             const Recipe d = recipe_def(r);
             if (d.nops != a.nops || d.code != code || d.hi != hi) continue;

@@ -50,7 +50,7 @@
     QAOA_INSTANCE __global__ void grad_kernel<real, Q, R, true>(const __grid_constant__ TileArgs<Q>);   \
     }
 
-// complex64 passes of the two-group plans (recipes 8..11, runtime masks; recipe 9 has 13 ops and
+// complex64 passes of the two-group plans (recipes 8..12, runtime masks; recipe 9 has 13 ops and
 // uses the second program word)
 #define QAOA_RECIPE_2G(real, Q, R, r)                                                                 \
     QAOA_INSTANCE __global__ void tile_kernel<real, Q, R, false, recipe_def(r).code, recipe_def(r).nops, \
@@ -62,6 +62,7 @@
     QAOA_RECIPE_2G(real, Q, R, 9)                                                                      \
     QAOA_RECIPE_2G(real, Q, R, 10)                                                                     \
     QAOA_RECIPE_2G(real, Q, R, 11)                                                                     \
+    QAOA_RECIPE_2G(real, Q, R, 12)                                                                     \
     }
 
 // complex64 adjoint-sweep passes specialised to the compiled sweep programs (unit weights; the

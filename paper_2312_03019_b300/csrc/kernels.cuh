@@ -1011,7 +1011,8 @@ constexpr Recipe kRecipe0 = base_recipe(0), kRecipe1 = base_recipe(1), kRecipe2 
 // tries them before the runtime-mask versions.
 // The complex64 programs of the two-group plans (n = 15..23, and n = 24's small fused passes):
 // 8 first pass, 9 fused group-0 boundary pass (13 ops: three layouts on each side of the phase),
-// 10 last pass, 11 fused pass of a high group that fits one register layout.
+// 10 last pass, 11 fused pass of a high group that fits one register layout, 12 last pass on
+// such a group.
 __host__ __device__ constexpr Recipe two_group_recipe(int r) {
     constexpr int kSteps9[13][2] = {{OP_LOAD, 0}, {OP_RX, 0}, {OP_XCHG, 2}, {OP_RX, 0}, {OP_XCHG, 1},
                                     {OP_RX, 0},   {OP_PHASE, 0}, {OP_RX, 0}, {OP_XCHG, 2}, {OP_RX, 0},
@@ -1032,11 +1033,14 @@ __host__ __device__ constexpr Recipe two_group_recipe(int r) {
                                recipe_step(3, OP_RX, 0) | recipe_step(4, OP_XCHG, 0) | recipe_step(5, OP_RX, 0) |
                                recipe_step(6, OP_EXPECT, 0) | recipe_step(7, OP_STORE, 0),
                            8}
+         : r == 4 ? Recipe{recipe_step(0, OP_LOAD, 0) | recipe_step(1, OP_RX, 0) | recipe_step(2, OP_EXPECT, 0) |
+                               recipe_step(3, OP_STORE, 0),
+                           4}
                   : Recipe{recipe_step(0, OP_LOAD, 0) | recipe_step(1, OP_RX, 0) | recipe_step(2, OP_PHASE, 0) |
                                recipe_step(3, OP_RX, 0) | recipe_step(4, OP_STORE, 0),
                            5};
 }
-constexpr int kRecipes = 12;
+constexpr int kRecipes = 13;
 __host__ __device__ constexpr Recipe recipe_def(int r) {
     return r >= 8 ? two_group_recipe(r - 8) : base_recipe(r == 5 ? 0 : r == 6 ? 2 : r == 7 ? 3 : r);
 }

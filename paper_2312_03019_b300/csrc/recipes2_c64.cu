@@ -1,5 +1,5 @@
 // recipes2_c64.cu -- complex64 pass kernels specialised to the programs of the two-group plans
-// (recipes 8..11), one translation unit.
+// (recipes 8..12), one translation unit.
 #include "kernels.cuh"
 
 #define QAOA_OWN_RECIPE_2G_C64
