@@ -26,6 +26,9 @@
  * qaoa_last_error() returns a message for the calling thread.  Nothing aborts and no C++
  * exception crosses the ABI.  Work is enqueued on the CUDA stream given at init; calls that
  * return host results synchronise that stream.
+ *
+ * Threads: distinct state handles may be used from different host threads at the same time
+ * (each with its own stream); one handle must not be used by two threads at once.
  */
 #ifndef QAOA_B300_QAOA_H
 #define QAOA_B300_QAOA_H

@@ -473,3 +473,47 @@ def test_mixer_only_and_phase_only(B, prec, n, mk):
     _, _, psi = run(B, g, gamma, np.zeros(3), prec)
     ref = amp * np.exp(-1j * gamma.sum() * oracle.cut_table(g).astype(np.float64))
     assert np.max(np.abs(psi - ref)) < (1e-12 if prec == "c128" else 1e-6) * amp
+
+
+def test_states_on_concurrent_host_threads(B):
+    """Distinct state handles used from four host threads at once, each on its own CUDA stream
+    (small-state and tiled paths, both precisions): every result equals, bit for bit, the same
+    run done alone."""
+    import threading
+    import torch
+    jobs = [(I.regular3(n, n) if n % 2 == 0 else I.gnp(n, 0.4, n), prec, *I.angles(3, seed=n))
+            for n, prec in ((9, "c64"), (16, "c64"), (22, "c128"), (24, "c64"), (13, "c128"), (26, "c64"),
+                            (20, "c64"), (18, "c128"))]
+
+    def run_one(job):
+        g, prec, gamma, beta = job
+        s = B.QAOAState(g, prec, stream=torch.cuda.Stream())
+        with torch.cuda.stream(s.stream):
+            s.apply_layers(gamma, beta)
+            c, nrm = s.expectation()
+            psi = s.amplitudes() if g.n <= 16 else None
+        s.close()
+        return c, nrm, psi
+
+    serial = [run_one(j) for j in jobs]
+    out = [None] * len(jobs)
+    errors = []
+
+    def worker(k):
+        try:
+            for i in range(k, len(jobs), 4):
+                for _ in range(2):
+                    out[i] = run_one(jobs[i])
+        except Exception as e:  # reported below
+            errors.append(e)
+
+    threads = [threading.Thread(target=worker, args=(k,)) for k in range(4)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    for (c0, n0, p0), (c1, n1, p1) in zip(serial, out):
+        assert c0 == c1 and n0 == n1
+        if p0 is not None:
+            assert np.array_equal(p0, p1)
