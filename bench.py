@@ -576,6 +576,8 @@ def run_grad(args):
     from paper_2312_03019_b300 import binding as B
 
     g, gamma, beta = I.workload_gnp24_p10()
+    if args.weighted:  # the same graph with seeded U[0.1, 2] edge weights (Algorithm 2 path)
+        g = I.random_weights(g, seed=0, lo=0.1, hi=2.0)
     s = B.QAOAState(g, args.prec)
     work = torch.empty(s.nbytes, dtype=torch.uint8, device="cuda")
     warm, K = max(3, args.warmup), max(args.steps, 10)
@@ -604,7 +606,8 @@ def run_grad(args):
     rec = {"metric": "QAOA adjoint gradients/s", "value": 1.0 / t_grad, "unit": "gradients/s", "higher_is_better": True,
            "n_gpus": 1, "steps": K, "warmup": warm, "mode": "grad", "dtype": "f32" if args.prec == "c64" else "f64",
            "data": "synthetic",
-           "config": {"workload": f"G(24, 0.5) seed 0, |E|={g.m}, p={p} seeded levels ({2 * p} parameters), "
+           "config": {"workload": f"G(24, 0.5) seed 0{' with edge weights U[0.1, 2]' if args.weighted else ''}, "
+                                  f"|E|={g.m}, p={p} seeded levels ({2 * p} parameters), "
                                   f"{'complex64' if args.prec == 'c64' else 'complex128'}, host-timed calls"},
            "ms_per_gradient": t_grad * 1e3, "ms_per_forward": t_fwd * 1e3,
            "gradient_over_forward": t_grad / t_fwd,
