@@ -448,29 +448,33 @@ TileFn<real> pick_tile_kernel(const TileArgs<PrecTraits<real>::Q>& a, bool weigh
 template <typename real>
 using GradFn = void (*)(TileArgs<GradTraits<real>::Q>);
 
-// The straight-line adjoint-pass instantiation of sweep program r (complex64, unit weights).
-template <int r>
+// The straight-line adjoint-pass instantiation of sweep program r (complex64).
+template <int r, bool kW>
 constexpr GradFn<float> grad_recipe_fn() {
-    return grad_kernel<float, GradTraits<float>::Q, GradTraits<float>::R, false, grad_recipe(r).code,
+    return grad_kernel<float, GradTraits<float>::Q, GradTraits<float>::R, kW, grad_recipe(r).code,
                        grad_recipe(r).nops>;
 }
 template <typename real>
-GradFn<real> grad_recipe_kernel(int r) {
-    if constexpr (std::is_same<real, float>::value)
-        return r == 0 ? grad_recipe_fn<0>() : r == 1 ? grad_recipe_fn<1>() : grad_recipe_fn<2>();
+GradFn<real> grad_recipe_kernel(int r, bool weighted) {
+    if constexpr (std::is_same<real, float>::value) {
+        if (weighted)
+            return r == 0 ? grad_recipe_fn<0, true>() : r == 1 ? grad_recipe_fn<1, true>() : grad_recipe_fn<2, true>();
+        return r == 0 ? grad_recipe_fn<0, false>() : r == 1 ? grad_recipe_fn<1, false>() : grad_recipe_fn<2, false>();
+    }
     return nullptr;
 }
 
 // The adjoint-pass kernel for a program: a compiled sweep program when one matches (complex64,
-// unit weights), else the interpreting instantiation.
+// unit or edge weights), else the interpreting instantiation.
 template <typename real>
 GradFn<real> pick_grad_kernel(const TileArgs<GradTraits<real>::Q>& a, bool weighted) {
     constexpr int Q = GradTraits<real>::Q, R = GradTraits<real>::R;
-    if (std::is_same<real, float>::value && !weighted && a.nops <= 10) {
+    if (std::is_same<real, float>::value && a.nops <= 10) {
         uint64_t code = 0;
         for (int i = 0; i < a.nops; ++i) code |= recipe_step(i, a.ops[i].kind, a.ops[i].layout);
         for (int r = 0; r < kGradRecipes; ++r)
-            if (grad_recipe(r).nops == a.nops && grad_recipe(r).code == code) return grad_recipe_kernel<real>(r);
+            if (grad_recipe(r).nops == a.nops && grad_recipe(r).code == code)
+                return grad_recipe_kernel<real>(r, weighted);
     }
     return weighted ? grad_kernel<real, Q, R, true> : grad_kernel<real, Q, R, false>;
 }
@@ -505,8 +509,9 @@ qaoa_status ensure_attributes() {
                                   (int)((1u << GQ) * sizeof(C2))));
     if constexpr (std::is_same<real, float>::value)
         for (int r = 0; r < kGradRecipes; ++r)
-            CUDA_TRY(cudaFuncSetAttribute(grad_recipe_kernel<real>(r), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)((1u << GQ) * sizeof(C2))));
+            for (bool w : {false, true})
+                CUDA_TRY(cudaFuncSetAttribute(grad_recipe_kernel<real>(r, w), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)((1u << GQ) * sizeof(C2))));
     CUDA_TRY(cudaFuncSetAttribute(small_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024));
     CUDA_TRY(cudaFuncSetAttribute(small_batch_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024));
     CUDA_TRY(cudaFuncSetAttribute(small_grad_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -65,10 +65,12 @@
     QAOA_RECIPE_2G(real, Q, R, 12)                                                                     \
     }
 
-// complex64 adjoint-sweep passes specialised to the compiled sweep programs (unit weights; the
+// complex64 adjoint-sweep passes specialised to the compiled sweep programs (unit and edge weights; the
 // complex128 ones spill at 255 registers and stay on the interpreting instance)
 #define QAOA_GRAD_RECIPE(real, Q, R, r)                                                               \
     QAOA_INSTANCE __global__ void grad_kernel<real, Q, R, false, grad_recipe(r).code, grad_recipe(r).nops>( \
+        const __grid_constant__ TileArgs<Q>);                                                             \
+    QAOA_INSTANCE __global__ void grad_kernel<real, Q, R, true, grad_recipe(r).code, grad_recipe(r).nops>(  \
         const __grid_constant__ TileArgs<Q>);
 #define QAOA_GRAD_RECIPE_INSTANCES(real, Q, R)                                                        \
     namespace qaoa {                                                                                   \
