@@ -216,12 +216,16 @@ qaoa_status qaoa_profile_read(qaoa_state s, qaoa_profile_stats *out);
  * Scratch space is a fixed 1 MiB array in the library's device memory (one partial pair per
  * tile of the state plus the result), which every GPU that loads the library keeps until the
  * process exits.  That bounds the size: n <= 29 for complex64 and n <= 28 for complex128
- * (larger n returns QAOA_ERR_INVALID with a message).  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress); make that first call before any stream
- * capture.  All calls share the one array: every entry a call reads is written earlier in the
- * same call, so nothing has to be cleared, but two calls whose work overlaps on the GPU (on
- * different streams or host threads) race on it and give wrong results.  Unit weights only
- * (a graph with a weights array returns QAOA_ERR_UNSUPPORTED). */
+ * (larger n returns QAOA_ERR_INVALID with a message).  Each call looks up the array's address on
+ * the current device (cudaGetSymbolAddress, no allocation), so the call is right after a
+ * cudaDeviceReset too.  All calls share the one array: every entry a call reads is written
+ * earlier in the same call, so nothing has to be cleared, but two calls whose work overlaps on
+ * the GPU (on different streams or host threads) race on it and give wrong results.
+ * QAOA_ERR_INVALID as well when dev_state is not device (or managed) memory of the current
+ * device -- a host, pinned or other-device pointer is refused before any launch -- and when the
+ * stream is being captured into a CUDA graph (the call synchronises the stream).  Unit weights
+ * only: a weights array whose entries are all exactly 1 is the unit-weight graph; any other
+ * weight returns QAOA_ERR_UNSUPPORTED. */
 qaoa_status qaoa_expectation_static(const qaoa_graph *g, qaoa_prec prec, const void *dev_state,
                                     size_t state_bytes, void *cuda_stream, double *out_c,
                                     double *out_norm);

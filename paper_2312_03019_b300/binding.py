@@ -10,7 +10,6 @@ Device memory and streams come from PyTorch: ``QAOAState`` allocates the state b
 from __future__ import annotations
 
 import ctypes
-import math
 import os
 
 import numpy as np
@@ -339,10 +338,6 @@ class QAOAState:
             self.close()
         except Exception:
             pass
-
-
-def uniform_amplitude(n: int) -> float:
-    return math.pow(2.0, -0.5 * n)
 
 
 def qaoa_server_create(hbm_budget_bytes: int, prec="c64", max_inflight: int = 64, queue_capacity: int = 8192,

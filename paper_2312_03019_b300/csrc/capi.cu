@@ -883,12 +883,14 @@ qaoa_status cut_table_impl(const HostGraph& hg, int prec, int group, int layout,
 //
 // qaoa_expectation_static keeps its scratch (one partial-sum pair per tile plus the final
 // pair) in this file-scope device array instead of allocating workspace.  In host code
-// `g_static_scratch` only names a host-side shadow, so the device address is looked up once per
-// device with cudaGetSymbolAddress and passed to the kernels.
+// `g_static_scratch` only names a host-side shadow, so every call looks up the array's address
+// on the current device with cudaGetSymbolAddress (a table lookup inside the runtime, no
+// allocation) and passes it to the kernels.  Looking it up per call, rather than caching it per
+// device, keeps the address right after the device's context is torn down and rebuilt
+// (cudaDeviceReset), where the array gets a new address.
 namespace {
 
 constexpr uint64_t kStaticPartials = 1ull << 16;  // tiles per call (2^16 x 16 B = 1 MiB)
-constexpr int kStaticMaxDevices = 64;
 
 }  // namespace
 
@@ -896,16 +898,19 @@ static __device__ __align__(256) double2 g_static_scratch[kStaticPartials + 1];
 
 namespace {
 
-double2* g_static_ptr[kStaticMaxDevices] = {};
-std::mutex g_static_mu;
-
 // Graph checks of encode_graph without any heap use (repeated edges found in the bitmasks).
+// A weights array is accepted when every weight is exactly 1: such a graph is the unit-weight
+// graph (as for qaoa_state_init, which evaluates it with the integer cut count).
 qaoa_status encode_graph_static(const qaoa_graph* g, HostGraph& hg) {
     if (!g) return fail(QAOA_ERR_INVALID, "graph is NULL");
     if (g->n < 1 || g->n > kMaxN) return fail(QAOA_ERR_INVALID, "n must be in [1, 34]");
     if (g->m < 0) return fail(QAOA_ERR_INVALID, "m must be >= 0");
     if (g->m > 0 && !g->edges) return fail(QAOA_ERR_INVALID, "edges is NULL");
-    if (g->weights) return fail(QAOA_ERR_UNSUPPORTED, "weighted graphs are not supported by this entry point");
+    for (int e = 0; g->weights && e < g->m; ++e) {
+        if (!std::isfinite(g->weights[e])) return fail(QAOA_ERR_INVALID, "non-finite edge weight");
+        if (g->weights[e] != 1.0)
+            return fail(QAOA_ERR_UNSUPPORTED, "edge weights other than 1 are not supported by this entry point");
+    }
     hg.n = g->n;
     hg.m = g->m;
     for (int e = 0; e < g->m; ++e) {
@@ -921,18 +926,40 @@ qaoa_status encode_graph_static(const qaoa_graph* g, HostGraph& hg) {
     return QAOA_OK;
 }
 
-// Device address of the scratch array on the current device (looked up on first use).
+// Device address of the scratch array on the current device.
 qaoa_status static_scratch(double2** out) {
+    void* p = nullptr;
+    CUDA_TRY(cudaGetSymbolAddress(&p, g_static_scratch));
+    *out = reinterpret_cast<double2*>(p);
+    return QAOA_OK;
+}
+
+// The state must be device (or managed) memory of the current device: a host pointer, or memory
+// of another device, would be read by kernels launched on the current device.  A stream that is
+// being captured is refused too: the call waits for its result (cudaStreamSynchronize), which a
+// capturing stream does not allow.  Neither query allocates.
+qaoa_status check_static_target(const void* dev_state, cudaStream_t stream) {
+    // capture first: it is the one query that is always legal while a capture is open
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CUDA_TRY(cudaStreamIsCapturing(stream, &cap));
+    if (cap != cudaStreamCaptureStatusNone)
+        return fail(QAOA_ERR_INVALID, "the stream is being captured: this call synchronises the stream");
     int dev = 0;
     CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kStaticMaxDevices) return fail(QAOA_ERR_UNSUPPORTED, "device ordinal too large");
-    std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_ptr[dev]) {
-        void* p = nullptr;
-        CUDA_TRY(cudaGetSymbolAddress(&p, g_static_scratch));
-        g_static_ptr[dev] = reinterpret_cast<double2*>(p);
+    cudaPointerAttributes attr;
+    std::memset(&attr, 0, sizeof(attr));
+    const cudaError_t e = cudaPointerGetAttributes(&attr, dev_state);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(QAOA_ERR_INVALID, std::string("device state pointer not recognised: ") + cudaGetErrorString(e));
     }
-    *out = g_static_ptr[dev];
+    if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
+        return fail(QAOA_ERR_INVALID, "device state is not device memory (host, pinned or unregistered pointer)");
+    if (attr.type == cudaMemoryTypeDevice && attr.device != dev) {
+        char msg[96];
+        std::snprintf(msg, sizeof(msg), "device state lives on device %d, the current device is %d", attr.device, dev);
+        return fail(QAOA_ERR_INVALID, msg);
+    }
     return QAOA_OK;
 }
 
@@ -1413,10 +1440,12 @@ qaoa_status qaoa_expectation_static(const qaoa_graph* g, qaoa_prec prec, const v
         return fail(QAOA_ERR_INVALID, prec == QAOA_C64 ? "qaoa_expectation_static supports n <= 29 for complex64"
                                                        : "qaoa_expectation_static supports n <= 28 for complex128");
     if (state_bytes < qaoa_state_bytes(hg.n, prec)) return fail(QAOA_ERR_INVALID, "device state too small");
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    st = check_static_target(dev_state, stream);
+    if (st != QAOA_OK) return st;
     double2* scratch = nullptr;
     st = static_scratch(&scratch);
     if (st != QAOA_OK) return st;
-    cudaStream_t stream = (cudaStream_t)cuda_stream;
     return prec == QAOA_C64 ? expectation_static_impl<float>(hg, dev_state, stream, scratch, out_c, out_norm)
                             : expectation_static_impl<double>(hg, dev_state, stream, scratch, out_c, out_norm);
 }

@@ -4,7 +4,7 @@ phase-table read, cut-value write and weighted-row read against the buffer it be
 failed check sets a bit in a device word and skips the access (no trap).  This runs the paths
 through that build, in a child process, at many shapes (one CTA, two and three groups, ragged
 groups, the largest states; forward, <C>, read-out, gradients, edge weights, cut tables, the
-server) and requires that no check failed."""
+allocation-free <C>, the server) and requires that no check failed."""
 import json
 import os
 import subprocess
@@ -65,6 +65,18 @@ for prec in ("c64", "c128"):
     B.qaoa_cut_table_f64(graph(16, True), prec)
     check(f"cut tables {prec}")
     torch.cuda.empty_cache()
+
+# the allocation-free <C> (its own kernel arguments, built outside the pass planner): one-CTA
+# and tiled sizes, up to the largest its scratch allows
+for prec, sizes in (("c64", (12, 21, 29)), ("c128", (11, 20, 28))):
+    for n in sizes:
+        gamma, beta = I.angles(2, 60 + n)
+        s = B.QAOAState(graph(n), prec)
+        s.apply_layers(gamma, beta)
+        B.qaoa_expectation_static(graph(n), prec, s.buffer.data_ptr(), s.nbytes, s.stream.cuda_stream)
+        s.close()
+        torch.cuda.empty_cache()
+        check(f"static <C> {prec} n={n}")
 
 for n, p in ((33, 2), (34, 1)):
     gamma, beta = I.angles(p, n)

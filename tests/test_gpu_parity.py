@@ -1,7 +1,16 @@
 """GPU parity of the CUDA path (through the C ABI) against the CPU oracle.
 
 Tolerances: cut values bit-exact; complex128 <C> within 1e-12 relative and the state within
-1e-12 in the 2-norm; complex64 <C> within 1e-5 * |E| and state fidelity >= 1 - 1e-5.
+1e-12 in the 2-norm; complex64 <C> within 1e-5 * |E|, state fidelity >= 1 - 1e-5, and every
+amplitude within C64_AMP_K * u * sqrt(p (n + 2)) * max|psi_ref| of the oracle's (u = 2^-24).
+
+The per-amplitude bound: a level puts every amplitude through one phase product and n
+butterflies, each rounded once per component in FP32 (relative error <= u), and the rounding
+errors are carried on by norm-preserving maps, so after p levels the error of one amplitude is a
+sum of about p (n + 2) independent roundings of size <= u times the amplitudes they act on; their
+typical sum is u sqrt(p (n + 2)) max|psi|.  An FP32 emulation of the same arithmetic against the
+oracle gives at most 0.85 of that (n = 8..21, p up to 10); C64_AMP_K = 16 leaves a margin of about
+20, while an amplitude that is wrong by more than 2e-5 of the largest one still fails.
 """
 import json
 import math
@@ -37,19 +46,29 @@ def run(B, g, gamma, beta, prec):
     return c, nrm, psi.astype(np.complex128)
 
 
-def check_c128(g, c, nrm, psi, ref_psi):
+def check_c128(g, c, nrm, psi, ref_psi, p=None):
     ref_c, _ = oracle_expectation(g, ref_psi)
     assert abs(c - ref_c) <= 1e-12 * max(1.0, abs(ref_c))
     assert abs(nrm - 1.0) < 1e-12
     assert np.linalg.norm(psi - ref_psi) <= 1e-12
 
 
-def check_c64(g, c, nrm, psi, ref_psi):
+C64_AMP_K = 16.0
+
+
+def c64_amp_tol(n, p, ref_psi):
+    """Largest allowed |psi_z - psi_ref,z| of a complex64 run of p levels (see the module doc)."""
+    return C64_AMP_K * 2.0 ** -24 * math.sqrt(max(1, p) * (n + 2)) * float(np.max(np.abs(ref_psi)))
+
+
+def check_c64(g, c, nrm, psi, ref_psi, p):
     ref_c, _ = oracle_expectation(g, ref_psi)
     assert abs(c - ref_c) <= 1e-5 * max(1, g.m)
     assert abs(nrm - 1.0) < 1e-5
     fid = abs(np.vdot(ref_psi, psi)) ** 2
     assert fid >= 1 - 1e-5
+    err = float(np.max(np.abs(psi - ref_psi)))
+    assert err <= c64_amp_tol(g.n, p, ref_psi), (err, c64_amp_tol(g.n, p, ref_psi))
 
 
 def oracle_expectation(g, psi):
@@ -110,7 +129,7 @@ def test_state_parity(B, prec, n, p, mk):
     gamma, beta = I.angles(p, seed=n)
     ref = oracle.qaoa_state(g, gamma, beta)
     c, nrm, psi = run(B, g, gamma, beta, prec)
-    (check_c128 if prec == "c128" else check_c64)(g, c, nrm, psi, ref)
+    (check_c128 if prec == "c128" else check_c64)(g, c, nrm, psi, ref, p)
 
 
 def test_config_n10_regular3_p1(B):
@@ -160,6 +179,7 @@ def test_c64_matches_c128_full_state_n26(B):
     c2, n2, b = run(B, g, gamma, beta, "c64")
     assert abs(c1 - c2) <= 1e-5 * g.m
     assert abs(np.vdot(a, b)) ** 2 >= 1 - 1e-5
+    assert np.max(np.abs(a - b)) <= c64_amp_tol(g.n, len(gamma), a)
 
 
 # ----------------------------------------------------------------------------- semantics / edge cases
@@ -204,7 +224,7 @@ def test_read_out_between_calls(B, prec, n):
     psi = s.amplitudes().astype(np.complex128)
     s.close()
     ref = oracle.qaoa_state(g, gamma, beta)
-    (check_c128 if prec == "c128" else check_c64)(g, c, 1.0, psi, ref)
+    (check_c128 if prec == "c128" else check_c64)(g, c, 1.0, psi, ref, len(gamma))
 
 
 @pytest.mark.parametrize("prec", ["c64", "c128"])
@@ -384,20 +404,21 @@ def _c64_against_c128_on_device(B, g, gamma, beta):
     c64, n64 = s64.expectation()
     t128, t64 = s128.as_tensor(), s64.as_tensor()
     ip = torch.zeros((), dtype=torch.complex128, device=t64.device)
-    worst = 0.0
+    worst, amax = 0.0, 0.0
     chunk = 1 << 28
     for i in range(0, t64.numel(), chunk):
         a = t64[i:i + chunk].to(torch.complex128)
         b = t128[i:i + chunk]
         ip += torch.vdot(b, a)
         worst = max(worst, (a - b).abs().max().item())
+        amax = max(amax, b.abs().max().item())
         del a, b
     fid = abs(ip.item()) ** 2 / (n64 * n128)
     del t128, t64
     s128.close()
     s64.close()
     torch.cuda.empty_cache()
-    return fid, c64, c128, n128, worst
+    return fid, c64, c128, n128, worst, amax
 
 
 @pytest.mark.parametrize("n", [30, 33])
@@ -408,11 +429,12 @@ def test_full_size_c64_against_c128(B, n):
     is pinned at these sizes by the p = 1 closed form."""
     g = I.regular3(n, 0)
     gamma, beta = I.angles(8, 0)
-    fid, c64, c128, n128, worst = _c64_against_c128_on_device(B, g, gamma, beta)
+    fid, c64, c128, n128, worst, amax = _c64_against_c128_on_device(B, g, gamma, beta)
     assert abs(n128 - 1) < 1e-12
     assert fid >= 1 - 1e-5, fid
     assert abs(c64 - c128) <= 1e-5 * g.m, (c64, c128)
-    assert worst < 1e-3 * 2 ** (-g.n / 2), worst
+    tol = C64_AMP_K * 2.0 ** -24 * math.sqrt(len(gamma) * (g.n + 2)) * amax
+    assert worst <= tol, (worst, tol)
 
 
 @pytest.mark.parametrize("n,prec", [(32, "c64"), (32, "c128"), (34, "c64")])

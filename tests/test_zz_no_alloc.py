@@ -78,6 +78,63 @@ def test_static_expectation_alternating_sizes(B):
         s.close()
 
 
+def test_static_expectation_matches_the_oracle(B):
+    """One comparison with the oracle itself (not only with the library's other entry): the
+    oracle's complex128 state is written to the device and both precisions of the static entry
+    reduce it (complex128 within 1e-12 relative of the oracle's <C>; complex64, on the state
+    rounded to complex64, within 1e-5 |E|).  A weights array of ones is the unit-weight graph."""
+    import oracle
+    import torch
+    for n, mk in ((11, lambda: I.gnp(11, 0.4, 3)), (19, lambda: I.regular3(19, 4))):
+        g = mk()
+        gamma, beta = I.angles(3, 50 + n)
+        psi = oracle.qaoa_state(g, gamma, beta)
+        ref_c, ref_n = oracle.expectation(g, psi)
+        ones = I.Graph(g.n, g.edges, np.ones(g.m))
+        for prec, dt in (("c128", torch.complex128), ("c64", torch.complex64)):
+            t = torch.from_numpy(psi).to(dt).cuda()
+            nbytes = t.numel() * t.element_size()
+            for gg in (g, ones):
+                c, nrm = B.qaoa_expectation_static(gg, prec, t.data_ptr(), nbytes, 0)
+                if prec == "c128":
+                    assert abs(c - ref_c) <= 1e-12 * abs(ref_c) and abs(nrm - ref_n) <= 1e-12
+                else:
+                    assert abs(c - ref_c) <= 1e-5 * g.m and abs(nrm - ref_n) <= 1e-5
+            del t
+
+
+def test_static_expectation_refuses_bad_targets(B):
+    """Refused on the host before any launch: a pinned host buffer, an unregistered host
+    buffer, a stream under capture, and a weight other than 1."""
+    import torch
+    g = I.ring(10)
+    nbytes = B.qaoa_state_bytes(10, "c64")
+    pinned = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    plain = np.zeros(nbytes // 8 + 2, dtype=np.complex64)
+    addr = plain.ctypes.data + (-plain.ctypes.data) % 16
+    for ptr in (pinned.data_ptr(), addr):
+        with pytest.raises(B.QAOAError) as ei:
+            B.qaoa_expectation_static(g, "c64", ptr, nbytes, 0)
+        assert ei.value.status == B.QAOA_ERR_INVALID
+        assert "not device memory" in str(ei.value)
+    dev = torch.zeros(nbytes, dtype=torch.uint8, device="cuda")
+    side = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    refused = None
+    with torch.cuda.graph(graph, stream=side):
+        try:
+            B.qaoa_expectation_static(g, "c64", dev.data_ptr(), nbytes, side.cuda_stream)
+        except B.QAOAError as e:
+            refused = e
+    assert refused is not None and refused.status == B.QAOA_ERR_INVALID
+    assert "captured" in str(refused)
+    heavy = I.Graph(g.n, g.edges, np.full(g.m, 2.0))
+    with pytest.raises(B.QAOAError) as ei:
+        B.qaoa_expectation_static(heavy, "c64", dev.data_ptr(), nbytes, 0)
+    assert ei.value.status == B.QAOA_ERR_UNSUPPORTED
+    torch.cuda.synchronize()
+
+
 def test_static_expectation_rejects_sizes_beyond_its_scratch(B):
     import torch
     buf = torch.empty(16, dtype=torch.uint8, device="cuda")
