@@ -11,8 +11,13 @@ levels, complex64 state of 2^33 amplitudes (64 GiB), larger than L2, so no L2 fl
   python bench.py --serve      # request-serving mode (qaoa_submit / qaoa_poll), its own JSON line
   python bench.py --grad       # adjoint-gradient mode (qaoa_gradient), its own JSON line
 
-Prints ONE JSON line on rank 0.  `--impl reference` times the CPU oracle (gate-level complex128
-simulator, the paper's Algorithm 1) on a bounded sample of the same workload on the host cores.
+Prints ONE JSON line on rank 0.  On one GPU the default line also carries the rest of the metric,
+measured after the headline on the same GPU (`--no-extra` skips them): `n30` (3-regular n = 30,
+p = 8: layers/s and the pass roofline), `grad` (adjoint gradients/s on G(24, 0.5), p = 10) and
+`serve` (the request stream at 2000/s and at a sustainable 300/s: the server against the plain
+one-request-at-a-time C API, requests/s and p50/p99 latency).  `--impl reference` times the CPU
+oracle (gate-level complex128 simulator, the paper's Algorithm 1) on a bounded sample of the same
+workload on the host cores.
 """
 from __future__ import annotations
 
@@ -46,6 +51,7 @@ NOMINAL_HBM_GBS = 7700.0  # B300 HBM3e, nominal (the fractions are also given ag
 PASS_KINDS = ("tile_kernel, mixer-only pass (read+write; the group-0 pass at n <= 33)",
               "tile_kernel, fused boundary pass with the cost phase (read+write)",
               "tile_kernel, last pass with <C> (read+write)")
+SYNTH_KIND = "tile_kernel, first pass (synthesises |+>, write only)"
 
 
 def parse_args():
@@ -75,6 +81,12 @@ def parse_args():
     ap.add_argument("--serve-requests", type=int, default=4096)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-budget-gib", type=float, default=64.0)
+    ap.add_argument("--serve-sustain-rate", type=float, default=300.0,
+                    help="second arrival rate of the serving comparison, one the GPU keeps up with")
+    ap.add_argument("--extra-serve-requests", type=int, default=1024,
+                    help="requests per arrival rate in the default line's serving block")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the n=30, gradient and serving blocks of the default line")
     return ap.parse_args()
 
 
@@ -281,6 +293,49 @@ def replica_rate(units_per_rank: float, seconds_max: float, world: int) -> float
 
 # --------------------------------------------------------------------------------- our arm
 
+def roofline_from_profile(prof, g, elem, known_traffic, ms_total):
+    """The roofline object of the dominant pass kind and the fraction of peak per layer, from the
+    library's per-pass CUDA events over a timed region of ms_total milliseconds."""
+    peak, peak_kind = measured_peaks()
+    if prof["pass_launches"] <= 0:
+        return None, None
+    # the dominant kernel: the pass kind with the most event time in the timed steps (one
+    # instantiation of tile_kernel each); the all-pass mean is given beside it
+    bytes_per_launch = 2.0 * elem * (1 << g.n)
+    kinds = []
+    for c, name in enumerate(PASS_KINDS):
+        L = prof["kind_launches"][c]
+        if not L:
+            continue
+        ms = prof["kind_ms"][c] / L
+        ach = bytes_per_launch / (ms / 1e3) / 1e9
+        kinds.append({"kernel": name, "launches": L, "launch_ms": ms, "achieved": ach, "frac": ach / peak,
+                      "frac_nominal": ach / NOMINAL_HBM_GBS,
+                      "share_of_timed_ms": prof["kind_ms"][c] / ms_total,
+                      "traffic": NCU_TRAFFIC_BY_KIND[c] * (1 << g.n) if known_traffic else None})
+    if prof["synth_launches"]:
+        ms = prof["synth_ms"] / prof["synth_launches"]
+        ach = bytes_per_launch / 2 / (ms / 1e3) / 1e9
+        kinds.append({"kernel": SYNTH_KIND, "launches": prof["synth_launches"], "launch_ms": ms, "achieved": ach,
+                      "frac": ach / peak, "frac_nominal": ach / NOMINAL_HBM_GBS,
+                      "share_of_timed_ms": prof["synth_ms"] / ms_total, "traffic": None})
+    dom = max((k for k in kinds if k["kernel"] != SYNTH_KIND), key=lambda d: d["launch_ms"] * d["launches"])
+    mean_ms = prof["pass_ms"] / prof["pass_launches"]
+    roof = {"bound": "hbm", "achieved": dom["achieved"], "peak": peak, "unit": "GB/s", "frac": dom["frac"],
+            "traffic": dom["traffic"], "peak_kind": f"{peak_kind} copy bandwidth", "kernel": dom["kernel"],
+            "peak_nominal": NOMINAL_HBM_GBS, "frac_nominal": dom["achieved"] / NOMINAL_HBM_GBS,
+            "bytes_per_launch": bytes_per_launch, "launch_ms": dom["launch_ms"], "launches": dom["launches"],
+            "all_read_write_passes": {"launches": prof["pass_launches"], "launch_ms": mean_ms,
+                                      "achieved": bytes_per_launch / (mean_ms / 1e3) / 1e9,
+                                      "frac": bytes_per_launch / (mean_ms / 1e3) / 1e9 / peak},
+            "per_kind": kinds}
+    # every byte the step's passes move (read+write passes and the write-only first pass) over
+    # the passes' event time: the fraction of peak per layer
+    moved = prof["pass_bytes"] + prof["synth_bytes"]
+    layer_frac = moved / ((prof["pass_ms"] + prof["synth_ms"]) / 1e3) / 1e9 / peak
+    return roof, layer_frac
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -364,38 +419,7 @@ def run_ours(args):
 
     peak, peak_kind = measured_peaks()
     elem = 8 if args.prec == "c64" else 16
-    roof = None
-    layer_frac = None
-    if prof["pass_launches"] > 0:
-        # the dominant kernel: the pass kind with the most event time in the timed steps (one
-        # instantiation of tile_kernel each); the all-pass mean is given beside it
-        bytes_per_launch = 2.0 * elem * (1 << g.n)
-        known = args.prec == "c64" and g.weights is None
-        kinds = []
-        for c, name in enumerate(PASS_KINDS):
-            L = prof["kind_launches"][c]
-            if not L:
-                continue
-            ms = prof["kind_ms"][c] / L
-            ach = bytes_per_launch / (ms / 1e3) / 1e9
-            kinds.append({"kernel": name, "launches": L, "launch_ms": ms, "achieved": ach, "frac": ach / peak,
-                          "frac_nominal": ach / NOMINAL_HBM_GBS,
-                          "share_of_timed_ms": prof["kind_ms"][c] / ms_max,
-                          "traffic": NCU_TRAFFIC_BY_KIND[c] * (1 << g.n) if known else None})
-        dom = max(kinds, key=lambda d: d["launch_ms"] * d["launches"])
-        mean_ms = prof["pass_ms"] / prof["pass_launches"]
-        roof = {"bound": "hbm", "achieved": dom["achieved"], "peak": peak, "unit": "GB/s", "frac": dom["frac"],
-                "traffic": dom["traffic"], "peak_kind": f"{peak_kind} copy bandwidth", "kernel": dom["kernel"],
-                "peak_nominal": NOMINAL_HBM_GBS, "frac_nominal": dom["achieved"] / NOMINAL_HBM_GBS,
-                "bytes_per_launch": bytes_per_launch, "launch_ms": dom["launch_ms"], "launches": dom["launches"],
-                "all_read_write_passes": {"launches": prof["pass_launches"], "launch_ms": mean_ms,
-                                          "achieved": bytes_per_launch / (mean_ms / 1e3) / 1e9,
-                                          "frac": bytes_per_launch / (mean_ms / 1e3) / 1e9 / peak},
-                "per_kind": kinds}
-        # every byte the step's passes move (read+write passes and the write-only first pass) over
-        # the passes' event time: the fraction of peak per layer
-        moved = prof["pass_bytes"] + prof["synth_bytes"]
-        layer_frac = moved / ((prof["pass_ms"] + prof["synth_ms"]) / 1e3) / 1e9 / peak
+    roof, layer_frac = roofline_from_profile(prof, g, elem, args.prec == "c64" and g.weights is None, ms_max)
     state_gbs = value * 2.0 * elem * (1 << g.n) / 1e9
 
     rec = {
@@ -422,11 +446,63 @@ def run_ours(args):
         torch.cuda.empty_cache()
         rec["cpu_baseline"] = cpu_baseline_block(args, g)
         rec["cpu_paper_method"] = paper_method_block(g)
+    if rank == 0 and world == 1 and not args.no_extra:
+        # the rest of the metric on the same GPU, after the headline: n = 30, the adjoint
+        # gradient workload and the serving workload (each untimed by the headline's clock)
+        st = None
+        torch.cuda.empty_cache()
+        t0 = time.perf_counter()
+        if args.n != 30:
+            rec["n30"] = size_block(B, 30, 8, "c64", steps=10, warmup=3)
+        rec["grad"] = grad_block(B, "c64", False, 10, 3, not args.no_accuracy)
+        rec["serve"] = serve_block(B, count=args.extra_serve_requests,
+                                   rates=(args.serve_rate, args.serve_sustain_rate), prec="c64")
+        rec["extra_blocks_s"] = time.perf_counter() - t0
     if rank == 0:
         print(json.dumps(rec), flush=True)
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def size_block(B, n, p, prec="c64", steps=10, warmup=3):
+    """Layers/s and the pass kernels' roofline on (near-)3-regular n, seed 0, p seeded levels:
+    the same step as the headline (reset, p levels, <C> read back), device-timed with CUDA events
+    on the library's stream."""
+    import torch
+    g, gamma, beta = workload(n, p)
+    st = B.QAOAState(g, prec)
+
+    def step():
+        st.reset()
+        st.apply_layers(gamma, beta)
+        return st.expectation()
+
+    for _ in range(max(3, warmup)):
+        step()
+    B.qaoa_profile_enable(st.handle, True)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st.stream)
+    for _ in range(steps):
+        c, nrm = step()
+    e1.record(st.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    prof = B.qaoa_profile_read(st.handle)
+    B.qaoa_profile_enable(st.handle, False)
+    elem = 8 if prec == "c64" else 16
+    roof, layer_frac = roofline_from_profile(prof, g, elem, prec == "c64", ms)
+    st.close()
+    torch.cuda.empty_cache()
+    value = steps * p / (ms / 1e3)
+    peak, _ = measured_peaks()
+    return {"metric": METRIC, "value": value, "unit": UNIT, "steps": steps, "ms_per_step": ms / steps,
+            "config": {"workload": workload_name(g, p, prec), "n": n, "p": p, "edges": g.m,
+                       "state_bytes": elem << n},
+            "hbm_frac_algorithmic": value * 2.0 * elem * (1 << n) / 1e9 / peak, "hbm_frac_passes": layer_frac,
+            "roofline": roof, "expectation": c, "norm": nrm}
 
 
 def accuracy_block(B, g, gamma, beta, st, prec, dev):
@@ -519,6 +595,84 @@ def serve_stream(B, reqs, cfg):
             "stats": stats}, done
 
 
+def plain_stream(B, reqs, prec="c64"):
+    """The same open-loop stream run one request at a time through the plain C API (no server):
+    each request, once it has arrived, gets qaoa_state_init on a preallocated device buffer,
+    qaoa_apply_layers + qaoa_expectation (or qaoa_gradient) and qaoa_state_free, in arrival order.
+    Latency = completion - scheduled arrival, on the host clock."""
+    import torch
+    nmax = max(r.graph.n for r in reqs)
+    nbytes = B.qaoa_state_bytes(nmax, prec)
+    buf = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    work = torch.empty(nbytes, dtype=torch.uint8, device="cuda") if any(r.want_grad for r in reqs) else None
+    stream = torch.cuda.current_stream().cuda_stream
+
+    def one(r):
+        h = B.qaoa_state_init(r.graph, prec, buf.data_ptr(), nbytes, stream)
+        try:
+            if r.want_grad:
+                c, dg, db = B.qaoa_gradient(h, r.gamma, r.beta, work.data_ptr(), nbytes)
+            else:
+                B.qaoa_apply_layers(h, r.gamma, r.beta)
+                c, _ = B.qaoa_expectation(h)
+                dg = db = None
+        finally:
+            B.qaoa_state_free(h)
+        return c, dg, db
+
+    seen = {}
+    for r in reqs:  # warm-up: one request of each size and kind, as for the server
+        if (r.graph.n, r.want_grad) not in seen:
+            seen[(r.graph.n, r.want_grad)] = one(r)
+    torch.cuda.synchronize()
+    out = []
+    t0 = time.perf_counter()
+    for r in reqs:
+        while time.perf_counter() - t0 < r.arrival_s:
+            pass
+        c, dg, db = one(r)
+        out.append({"expectation": c, "d_gamma": dg, "d_beta": db,
+                    "latency": time.perf_counter() - t0 - r.arrival_s})
+    span = time.perf_counter() - t0
+    lat = sorted(d["latency"] for d in out)
+    q = lambda f: lat[min(len(lat) - 1, int(f * len(lat)))] * 1e3
+    del buf, work
+    torch.cuda.empty_cache()
+    return {"requests_per_s": len(out) / span, "p50_ms": q(0.50), "p99_ms": q(0.99), "makespan_s": span}, out
+
+
+SERVE_CFG = dict(prec="c64", max_inflight=64, queue_capacity=8192, max_batch=64, streams=8, use_graphs=True)
+
+
+def serve_block(B, count=1024, rates=(2000.0, 300.0), budget_gib=64.0, prec="c64"):
+    """The serving workload (Poisson arrivals, n ~ U{14..28}, half 3-regular and half G(n, 0.3),
+    p ~ U{1..6}, 25 % with gradient, complex64) at each arrival rate: the server
+    (qaoa_submit / qaoa_poll) against the plain one-request-at-a-time C API on the same stream,
+    with the largest difference between their results."""
+    import numpy as np
+    rows = []
+    for rate in rates:
+        reqs = I.request_stream(count=count, rate_hz=rate, seed=0).requests
+        cfg = dict(SERVE_CFG, prec=prec, hbm_budget_bytes=int(budget_gib * (1 << 30)))
+        served, done = serve_stream(B, reqs, cfg)
+        plain, pdone = plain_stream(B, reqs, prec)
+        diff_c = max(abs(a["expectation"] - b["expectation"]) / max(1, r.graph.m)
+                     for a, b, r in zip(done, pdone, reqs))
+        diff_g = max([float(np.max(np.abs(np.concatenate([a["d_gamma"] - b["d_gamma"], a["d_beta"] - b["d_beta"]]))))
+                      for a, b, r in zip(done, pdone, reqs) if r.want_grad] or [0.0])
+        rows.append({"arrival_rate_hz": rate, "requests": len(reqs), "served": served, "plain_c_api": plain,
+                     "speedup_vs_plain": served["requests_per_s"] / plain["requests_per_s"],
+                     "max_diff_C_over_edges": diff_c, "max_diff_grad": diff_g})
+    return {"metric": "QAOA serving throughput and latency", "unit": "requests/s",
+            "config": {"workload": f"{count} seeded requests (the first of the 4096-request stream's draws), "
+                                   "n 14-28 (half 3-regular, half G(n,0.3)), p 1-6, 25% with gradient",
+                       "prec": prec, "hbm_budget_gib": budget_gib,
+                       "server": {k: v for k, v in SERVE_CFG.items() if k != "prec"},
+                       "plain_c_api": "qaoa_state_init / apply_layers / expectation (or qaoa_gradient) / "
+                                      "state_free per request, in arrival order, one at a time"},
+            "rates": rows}
+
+
 def run_cpu_report(args):
     """The oracle (gate-level complex128, Algorithm 1) timed on this host with all threads and
     with one: 3-regular n=10, p=1 (gamma 0.4, beta 0.3); one level of G(26, 0.5) (one thread:
@@ -568,25 +722,20 @@ def oracle_level_seconds_graph(g, gamma, beta):
     return time.perf_counter() - t0, g
 
 
-def run_grad(args):
-    """Adjoint gradients per second on G(24, 0.5), seed 0, p = 10 (20 parameters), complex64,
-    through qaoa_gradient (forward levels, lambda = C psi, reverse sweep; host-synchronous per
-    call), beside the forward evaluation of the same circuit and the 4p forward evaluations
-    central differences would need."""
+def grad_block(B, prec="c64", weighted=False, steps=10, warmup=3, accuracy=True):
+    """Adjoint gradients per second on G(24, 0.5), seed 0, p = 10 (20 parameters), through
+    qaoa_gradient (forward levels, lambda = C psi, reverse sweep; host-synchronous per call),
+    beside the forward evaluation of the same circuit and the 4p forward evaluations central
+    differences would need."""
+    import numpy as np
     import torch
 
-    if not torch.cuda.is_available():
-        raise SystemExit("the gradient benchmark needs a CUDA device")
-    from paper_2312_03019_b300 import build as bld
-    bld.build()
-    from paper_2312_03019_b300 import binding as B
-
     g, gamma, beta = I.workload_gnp24_p10()
-    if args.weighted:  # the same graph with seeded U[0.1, 2] edge weights (Algorithm 2 path)
+    if weighted:  # the same graph with seeded U[0.1, 2] edge weights (Algorithm 2 path)
         g = I.random_weights(g, seed=0, lo=0.1, hi=2.0)
-    s = B.QAOAState(g, args.prec)
+    s = B.QAOAState(g, prec)
     work = torch.empty(s.nbytes, dtype=torch.uint8, device="cuda")
-    warm, K = max(3, args.warmup), max(args.steps, 10)
+    warm, K = max(3, warmup), max(steps, 10)
 
     def grad():
         return B.qaoa_gradient(s.handle, gamma, beta, work.data_ptr(), s.nbytes)
@@ -609,29 +758,43 @@ def run_grad(args):
         forward()
     t_fwd = (time.perf_counter() - t0) / K
     p = len(gamma)
-    rec = {"metric": "QAOA adjoint gradients/s", "value": 1.0 / t_grad, "unit": "gradients/s", "higher_is_better": True,
-           "n_gpus": 1, "steps": K, "warmup": warm, "mode": "grad", "dtype": "f32" if args.prec == "c64" else "f64",
-           "data": "synthetic",
-           "config": {"workload": f"G(24, 0.5) seed 0{' with edge weights U[0.1, 2]' if args.weighted else ''}, "
+    rec = {"metric": "QAOA adjoint gradients/s", "value": 1.0 / t_grad, "unit": "gradients/s",
+           "higher_is_better": True, "steps": K, "warmup": warm, "dtype": "f32" if prec == "c64" else "f64",
+           "config": {"workload": f"G(24, 0.5) seed 0{' with edge weights U[0.1, 2]' if weighted else ''}, "
                                   f"|E|={g.m}, p={p} seeded levels ({2 * p} parameters), "
-                                  f"{'complex64' if args.prec == 'c64' else 'complex128'}, host-timed calls"},
+                                  f"{'complex64' if prec == 'c64' else 'complex128'}, host-timed calls"},
            "ms_per_gradient": t_grad * 1e3, "ms_per_forward": t_fwd * 1e3,
            "gradient_over_forward": t_grad / t_fwd,
            "speedup_vs_central_differences": 4 * p * t_fwd / t_grad,
            "expectation": c}
     s.close()
-    if args.prec == "c64" and not args.no_accuracy:  # the same gradient in complex128 (untimed)
+    del work
+    if prec == "c64" and accuracy:  # the same gradient in complex128 (untimed)
         r = B.QAOAState(g, "c128")
         try:
             c2, dg2, db2 = r.gradient(gamma, beta)
         finally:
             r.close()
-        import numpy as np
         ref = np.concatenate([dg2, db2])
         err = np.abs(np.concatenate([dg, db]) - ref)
         rec["accuracy"] = {"reference": "the same gradient in complex128 on this GPU", "abs_err_C": c - c2,
                            "max_abs_err_grad": float(err.max()),
                            "max_err_grad_rel": float(err.max() / max(1e-300, np.abs(ref).max())), "untimed": True}
+    torch.cuda.empty_cache()
+    return rec
+
+
+def run_grad(args):
+    import torch
+
+    if not torch.cuda.is_available():
+        raise SystemExit("the gradient benchmark needs a CUDA device")
+    from paper_2312_03019_b300 import build as bld
+    bld.build()
+    from paper_2312_03019_b300 import binding as B
+
+    rec = grad_block(B, args.prec, args.weighted, args.steps, args.warmup, not args.no_accuracy)
+    rec.update({"n_gpus": 1, "mode": "grad", "data": "synthetic"})
     print(json.dumps(rec), flush=True)
     return 0
 
@@ -685,14 +848,16 @@ def run_serve(args):
     for a, b in zip(done, done_serial):
         if a["expectation"] != b["expectation"]:
             raise RuntimeError("served and serial results differ")
+    plain, _ = plain_stream(B, reqs, args.prec)
     rec = {"metric": "QAOA serving throughput", "value": served["requests_per_s"], "unit": "requests/s",
            "higher_is_better": True, "n_gpus": 1, "dtype": "f32" if args.prec == "c64" else "f64",
            "data": "synthetic", "mode": "serve",
            "config": {"workload": f"{len(reqs)} requests, Poisson {args.serve_rate:g}/s, n 14-28 "
                                   "(half 3-regular, half G(n,0.3)), p 1-6, 25% with gradient",
                       "prec": args.prec, "hbm_budget_gib": args.serve_budget_gib},
-           "served": served, "serial": serial,
-           "speedup_vs_serial": served["requests_per_s"] / serial["requests_per_s"]}
+           "served": served, "serial": serial, "plain_c_api": plain,
+           "speedup_vs_serial": served["requests_per_s"] / serial["requests_per_s"],
+           "speedup_vs_plain": served["requests_per_s"] / plain["requests_per_s"]}
     if args.prec == "c64" and not args.no_accuracy:
         rec["accuracy"] = serve_accuracy(B, reqs, done)
     print(json.dumps(rec), flush=True)

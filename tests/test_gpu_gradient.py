@@ -4,6 +4,7 @@ import numpy as np
 import pytest
 
 from paper_2312_03019_b300 import inputs as I
+from tests.tolerances import FD_TOL, c64_grad_tol
 
 pytestmark = pytest.mark.gpu
 
@@ -47,9 +48,10 @@ def test_gradient_matches_oracle_adjoint(B, prec, n, p, mk):
         assert np.max(np.abs(dg - ref_dg)) <= 1e-10 * scale
         assert np.max(np.abs(db - ref_db)) <= 1e-10 * scale
     else:
+        tol = c64_grad_tol(n, p, g.m, np.max(np.abs(np.concatenate([ref_dg, ref_db]))))
         assert abs(c - ref_c) <= 1e-5 * g.m
-        assert np.max(np.abs(dg - ref_dg)) <= 1e-4 * g.m
-        assert np.max(np.abs(db - ref_db)) <= 1e-4 * g.m
+        assert np.max(np.abs(dg - ref_dg)) <= tol
+        assert np.max(np.abs(db - ref_db)) <= tol
 
 
 def test_gradient_workload_g24_p10_against_finite_differences(B):
@@ -76,8 +78,9 @@ def test_gradient_workload_g24_p10_against_finite_differences(B):
         fd_b[k] = (f(gamma, beta + e) - f(gamma, beta - e)) / (2 * h)
     s.close()
     scale = np.max(np.abs(np.concatenate([fd_g, fd_b])))
-    assert np.max(np.abs(dg - fd_g)) <= 1e-3 * scale + 1e-3
-    assert np.max(np.abs(db - fd_b)) <= 1e-3 * scale + 1e-3
+    tol = c64_grad_tol(g.n, 10, g.m, scale) + FD_TOL
+    assert np.max(np.abs(dg - fd_g)) <= tol
+    assert np.max(np.abs(db - fd_b)) <= tol
 
 
 def test_gradient_fp64_cpu_adjoint_n14_p10(B):
@@ -90,7 +93,7 @@ def test_gradient_fp64_cpu_adjoint_n14_p10(B):
     c, dg, db = gpu_gradient(B, g, gamma, beta, "c128")
     assert np.max(np.abs(np.concatenate([dg - ref_dg, db - ref_db]))) <= 1e-10 * scale
     c, dg, db = gpu_gradient(B, g, gamma, beta, "c64")
-    assert np.max(np.abs(np.concatenate([dg - ref_dg, db - ref_db]))) <= 1e-4 * g.m
+    assert np.max(np.abs(np.concatenate([dg - ref_dg, db - ref_db]))) <= c64_grad_tol(14, 10, g.m, scale)
 
 
 def test_gradient_then_state_is_plus_and_reusable(B):
@@ -152,10 +155,10 @@ def test_gradient_more_levels_than_one_coefficient_chunk(B, prec, n):
     ref_c, ref_dg, ref_db = oracle.adjoint_gradient(g, gamma, beta)
     c, dg, db = gpu_gradient(B, g, gamma, beta, prec)
     scale = max(1.0, np.max(np.abs(np.concatenate([ref_dg, ref_db]))))
-    tol = 1e-10 if prec == "c128" else 2e-4 * g.m
-    assert abs(c - ref_c) <= (1e-12 * abs(ref_c) if prec == "c128" else 1e-4 * g.m)
-    assert np.max(np.abs(dg - ref_dg)) <= tol * scale
-    assert np.max(np.abs(db - ref_db)) <= tol * scale
+    tol = 1e-10 * scale if prec == "c128" else c64_grad_tol(n, 70, g.m, scale)
+    assert abs(c - ref_c) <= (1e-12 * abs(ref_c) if prec == "c128" else 1e-5 * g.m)
+    assert np.max(np.abs(dg - ref_dg)) <= tol
+    assert np.max(np.abs(db - ref_db)) <= tol
 
 
 @pytest.mark.parametrize("prec", ["c128", "c64"])
@@ -206,5 +209,6 @@ def test_gradient_full_size_p1_closed_form(B, n, prec):
         assert abs(c - f(ga, be)) <= 1e-12 * f(ga, be)
         assert abs(dg[0] - ref_dg) <= 1e-7 * g.m and abs(db[0] - ref_db) <= 1e-7 * g.m
     else:
+        tol = c64_grad_tol(n, 1, g.m, max(abs(ref_dg), abs(ref_db))) + 1e-7 * g.m
         assert abs(c - f(ga, be)) <= 1e-5 * g.m
-        assert abs(dg[0] - ref_dg) <= 1e-4 * g.m and abs(db[0] - ref_db) <= 1e-4 * g.m
+        assert abs(dg[0] - ref_dg) <= tol and abs(db[0] - ref_db) <= tol

@@ -2,15 +2,7 @@
 
 Tolerances: cut values bit-exact; complex128 <C> within 1e-12 relative and the state within
 1e-12 in the 2-norm; complex64 <C> within 1e-5 * |E|, state fidelity >= 1 - 1e-5, and every
-amplitude within C64_AMP_K * u * sqrt(p (n + 2)) * max|psi_ref| of the oracle's (u = 2^-24).
-
-The per-amplitude bound: a level puts every amplitude through one phase product and n
-butterflies, each rounded once per component in FP32 (relative error <= u), and the rounding
-errors are carried on by norm-preserving maps, so after p levels the error of one amplitude is a
-sum of about p (n + 2) independent roundings of size <= u times the amplitudes they act on; their
-typical sum is u sqrt(p (n + 2)) max|psi|.  An FP32 emulation of the same arithmetic against the
-oracle gives at most 0.85 of that (n = 8..21, p up to 10); C64_AMP_K = 16 leaves a margin of about
-20, while an amplitude that is wrong by more than 2e-5 of the largest one still fails.
+amplitude within the rounding bound of tests/tolerances.py (c64_amp_tol).
 """
 import json
 import math
@@ -20,6 +12,7 @@ import numpy as np
 import pytest
 
 from paper_2312_03019_b300 import inputs as I
+from tests.tolerances import C64_AMP_K, U32, c64_amp_tol
 
 pytestmark = pytest.mark.gpu
 
@@ -51,14 +44,6 @@ def check_c128(g, c, nrm, psi, ref_psi, p=None):
     assert abs(c - ref_c) <= 1e-12 * max(1.0, abs(ref_c))
     assert abs(nrm - 1.0) < 1e-12
     assert np.linalg.norm(psi - ref_psi) <= 1e-12
-
-
-C64_AMP_K = 16.0
-
-
-def c64_amp_tol(n, p, ref_psi):
-    """Largest allowed |psi_z - psi_ref,z| of a complex64 run of p levels (see the module doc)."""
-    return C64_AMP_K * 2.0 ** -24 * math.sqrt(max(1, p) * (n + 2)) * float(np.max(np.abs(ref_psi)))
 
 
 def check_c64(g, c, nrm, psi, ref_psi, p):
@@ -433,7 +418,7 @@ def test_full_size_c64_against_c128(B, n):
     assert abs(n128 - 1) < 1e-12
     assert fid >= 1 - 1e-5, fid
     assert abs(c64 - c128) <= 1e-5 * g.m, (c64, c128)
-    tol = C64_AMP_K * 2.0 ** -24 * math.sqrt(len(gamma) * (g.n + 2)) * amax
+    tol = C64_AMP_K * U32 * math.sqrt(len(gamma) * (g.n + 2)) * amax
     assert worst <= tol, (worst, tol)
 
 

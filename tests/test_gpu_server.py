@@ -1,4 +1,5 @@
-"""Continuous-batching server (qaoa_server_*): every result equals the same request run alone,
+"""Continuous-batching server (qaoa_server_*): every result equals the same request run alone
+and matches the FP64 oracle (<C> by the gate-level circuit, gradients by the oracle's adjoint),
 admission by HBM footprint, queue limits, graphs on and off, shutdown with work in flight."""
 import time
 
@@ -6,6 +7,7 @@ import numpy as np
 import pytest
 
 from paper_2312_03019_b300 import inputs as I
+from tests.tolerances import c64_grad_tol
 
 pytestmark = pytest.mark.gpu
 
@@ -62,6 +64,38 @@ def mixed_requests(count, seed=3):
     return out
 
 
+_ORACLE = {}
+
+
+def oracle_result(g, gamma, beta, grad):
+    """(<C>, d gamma, d beta) of a request from the oracle, cached across the tests of this file."""
+    import oracle
+    key = (g.name, g.n, g.m, tuple(np.round(gamma, 15)), tuple(np.round(beta, 15)), grad)
+    if key not in _ORACLE:
+        if grad:
+            _ORACLE[key] = oracle.adjoint_gradient(g, gamma, beta)
+        else:
+            _ORACLE[key] = (oracle.expectation(g, oracle.qaoa_state(g, gamma, beta))[0], None, None)
+    return _ORACLE[key]
+
+
+def check_against_oracle(r, g, gamma, beta, grad, prec):
+    """A served result against the oracle: complex128 <C> within 1e-12 relative and derivatives
+    within 1e-10 of the largest; complex64 <C> within 1e-5 |E| and derivatives within the
+    rounding bound of tests/tolerances.py."""
+    c, dg, db = oracle_result(g, gamma, beta, grad)
+    if prec == "c128":
+        assert abs(r["expectation"] - c) <= 1e-12 * max(1.0, abs(c)), (g.name, r["expectation"], c)
+    else:
+        assert abs(r["expectation"] - c) <= 1e-5 * max(1, g.m), (g.name, r["expectation"], c)
+    if grad:
+        ref = np.concatenate([dg, db])
+        got = np.concatenate([r["d_gamma"], r["d_beta"]])
+        scale = float(np.max(np.abs(ref)))
+        tol = 1e-10 * max(1.0, scale) if prec == "c128" else c64_grad_tol(g.n, len(gamma), g.m, scale)
+        assert np.max(np.abs(got - ref)) <= tol, (g.name, np.max(np.abs(got - ref)), tol)
+
+
 @pytest.mark.parametrize("graphs", [True, False])
 def test_results_identical_alone_and_in_the_mix(B, graphs):
     reqs = mixed_requests(48)
@@ -74,6 +108,7 @@ def test_results_identical_alone_and_in_the_mix(B, graphs):
     assert stats["batches"] >= 1 and stats["batched_requests"] >= 1
     if graphs:
         assert stats["graph_launches"] >= 1
+    packed = streamed = 0
     for (g, ga, be, grad), t in zip(reqs, tickets):
         r = res[t]
         assert r["status"] == 0
@@ -81,6 +116,29 @@ def test_results_identical_alone_and_in_the_mix(B, graphs):
         assert r["expectation"] == c, (g.name, r["expectation"], c)  # bit-identical
         if grad:
             assert np.array_equal(r["d_gamma"], dg) and np.array_equal(r["d_beta"], db)
+        check_against_oracle(r, g, ga, be, grad, "c64")
+        packed += r["batched"]
+        streamed += g.n >= 15
+    assert packed >= 1 and streamed >= 10
+
+
+def test_c128_mix_against_the_oracle(B):
+    """complex128 server: packed small requests (n <= 13), streamed ones (n = 15..19), with and
+    without gradients, all against the oracle to 1e-12."""
+    reqs = []
+    for i, n in enumerate((8, 11, 13, 9, 15, 17, 19, 16, 12, 18)):
+        g = I.regular3(n, 30 + i) if n % 2 == 0 else I.gnp(n, 0.35, 30 + i)
+        ga, be = I.angles(1 + i % 4, seed=300 + i)
+        reqs.append((g, ga, be, i % 3 == 1))
+    sv = B.qaoa_server_create(2 << 30, "c128", max_inflight=8, max_batch=8, streams=4)
+    try:
+        tickets = [B.qaoa_submit(sv, g, ga, be, grad) for g, ga, be, grad in reqs]
+        res = wait_all(B, sv, tickets)
+    finally:
+        B.qaoa_server_destroy(sv)
+    for (g, ga, be, grad), t in zip(reqs, tickets):
+        assert res[t]["status"] == 0
+        check_against_oracle(res[t], g, ga, be, grad, "c128")
 
 
 def test_admission_under_a_small_arena(B):
@@ -150,6 +208,7 @@ def test_c128_server_gradient(B):
     r = wait_all(B, sv, [t])[t]
     B.qaoa_server_destroy(sv)
     assert r["expectation"] == c and np.array_equal(r["d_gamma"], dg) and np.array_equal(r["d_beta"], db)
+    check_against_oracle(r, g, ga, be, True, "c128")
 
 
 def test_deadline_expires_while_queued(B):
