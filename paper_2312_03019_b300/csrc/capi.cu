@@ -330,6 +330,7 @@ struct qaoa_state_s {
     void* d_gmix = nullptr;       // [3 * level] mixer entries
     double* d_gacc = nullptr;     // [2 * levels]
     double2* d_gpart = nullptr;   // [2 * tiles]
+    double* d_gpow = nullptr;     // complex64 sweep: [level][kMaxN + 1] powers of the butterflies' factor
     bool lazy = true;
     bool exp_valid = false;
     bool compl_ = false;  // buffer index z holds the amplitude of ~z (pending X on every qubit)
@@ -798,6 +799,7 @@ void release(qaoa_state s) {
     cudaFree(s->d_gmix);
     cudaFree(s->d_gacc);
     cudaFree(s->d_gpart);
+    cudaFree(s->d_gpow);
     if (s->h_result) cudaFreeHost(s->h_result);
     delete s;
 }
@@ -1018,6 +1020,20 @@ qaoa_status expectation_static_impl(const HostGraph& hg, const void* dev_state, 
 
 namespace {
 
+// Records in every RXD op of an adjoint-sweep plan how many of its level's qubits the ops before
+// it (in this and earlier passes) have already turned (sweep_done): the pair terms it measures
+// carry that many butterfly factors, which the complex64 sweep undoes.
+void annotate_sweep(Plan& plan, int p) {
+    std::vector<int> done(p, 0);
+    for (Pass& ps : plan.passes)
+        for (Op& op : ps.ops) {
+            if (op.kind != OP_RXD) continue;
+            const int level = sweep_level(op.arg);
+            op.arg = (op.arg & 0x1ffff) | (done[level] << 17);
+            done[level] += __builtin_popcount(op.mask);
+        }
+}
+
 qaoa_status grad_workspace(qaoa_state s, int p) {
     if (p <= s->grad_levels && s->d_gtab) return QAOA_OK;
     cudaFree(s->d_gtab);
@@ -1025,9 +1041,11 @@ qaoa_status grad_workspace(qaoa_state s, int p) {
     cudaFree(s->d_gacc);
     cudaFree(s->d_gpart);
     cudaFree(s->d_gwfix);
+    cudaFree(s->d_gpow);
     s->d_gtab = s->d_gmix = s->d_gwfix = nullptr;
     s->d_gacc = nullptr;
     s->d_gpart = nullptr;
+    s->d_gpow = nullptr;
     s->grad_levels = 0;
     const size_t eb = elem_bytes(s->prec);
     cudaError_t e = cudaMalloc(&s->d_gtab, (size_t)p * table_entries(s->g) * eb);
@@ -1035,6 +1053,7 @@ qaoa_status grad_workspace(qaoa_state s, int p) {
     if (e == cudaSuccess) e = cudaMalloc(&s->d_gmix, (size_t)3 * p * eb);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_gacc, (size_t)2 * p * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&s->d_gpart, (size_t)2 * grad_tiles(s->n) * sizeof(double2));
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_gpow, (size_t)p * (kMaxN + 1) * sizeof(double));
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(QAOA_ERR_OOM, std::string("gradient workspace allocation failed: ") + cudaGetErrorString(e));
@@ -1065,7 +1084,11 @@ qaoa_status forward_async(qaoa_state s, int p, const double* gamma, const double
 template <typename real>
 qaoa_status gradient_async(qaoa_state s, int p, const double* gamma, const double* beta, void* work) {
     qaoa_status st = forward_async<real>(s, p, gamma, beta);
-    if (st == QAOA_OK) st = set_parity_form<real>(s, false);  // the sweep reads the plain form
+    constexpr int Q = GradTraits<real>::Q, R = GradTraits<real>::R;
+    // the tiled complex64 sweep runs in the forward passes' parity form (and folds each level's
+    // butterfly factors, see rxd_parity); the one-CTA sweep and complex128 read the plain form
+    const bool parity_sweep = std::is_same<real, float>::value && s->n > Q;
+    if (st == QAOA_OK) st = set_parity_form<real>(s, parity_sweep);
     if (st != QAOA_OK) return st;
     using C2 = typename C2T<real>::type;
     // plain per-level tables (no folded factors) for the sweep
@@ -1083,7 +1106,13 @@ qaoa_status gradient_async(qaoa_state s, int p, const double* gamma, const doubl
         for (int k = 0; k < levels; ++k) {
             ca.gamma[k] = gamma[k0 + k];
             ca.beta[k] = beta[k0 + k];
+            // packed butterflies need |t| <= 1: RX(2b) = -i X RX(2b - pi) where |tan b| > 1; X on
+            // both states is an index complement, which no sweep term sees (C(~z) = C(z), and
+            // X^n commutes with every X_j), and the phase (-i)^n cancels in <lambda|.|psi>
+            ca.fold[k] = (parity_sweep && std::fabs(std::sin(beta[k0 + k])) > std::fabs(std::cos(beta[k0 + k]))) ? 1 : 0;
         }
+        ca.sweep = parity_sweep ? 1 : 0;
+        ca.gpow = s->d_gpow + (size_t)k0 * (kMaxN + 1);
         ca.phase = reinterpret_cast<C2*>(s->d_gtab) + (size_t)k0 * table_entries(s->g);
         ca.mix = reinterpret_cast<C2*>(s->d_gmix) + (size_t)3 * k0;
         dim3 grid((unsigned)std::max(1, (std::max(ca.E1, ca.m) + 255) / 256), (unsigned)levels);
@@ -1092,7 +1121,6 @@ qaoa_status gradient_async(qaoa_state s, int p, const double* gamma, const doubl
         s->launches++;
     }
     CUDA_TRY(cudaMemsetAsync(s->d_gacc, 0, (size_t)2 * p * sizeof(double), s->stream));
-    constexpr int Q = GradTraits<real>::Q, R = GradTraits<real>::R;
     if (s->n <= Q) {
         SmallGradJob j;
         std::memset(&j, 0, sizeof(j));
@@ -1119,6 +1147,7 @@ qaoa_status gradient_async(qaoa_state s, int p, const double* gamma, const doubl
         } catch (const std::exception& ex) {
             return fail(QAOA_ERR_UNSUPPORTED, ex.what());
         }
+        annotate_sweep(plan, p);
         const uint64_t gt = grad_tiles(s->n);
         const size_t smem = (size_t)(1u << Q) * sizeof(C2);
         qaoa_status ast = ensure_attributes<real>();
@@ -1132,11 +1161,12 @@ qaoa_status gradient_async(qaoa_state s, int p, const double* gamma, const doubl
             a.phase = s->d_gtab;
             a.mix = s->d_gmix;
             a.partials = s->d_gpart;
+            a.gpow = s->d_gpow;
             if (s->g.weighted && !fill_weighted(a, s->g, s->prec, s->d_gwfix, a.ops, a.nops))
                 return fail(QAOA_ERR_UNSUPPORTED, "too many phase levels in one adjoint pass");
             int lev[2] = {-1, -1};
             for (const Op& op : ps.ops)
-                if (op.kind == OP_RXD || op.kind == OP_GRADG) lev[(op.arg >> 16) & 1] = op.arg & 0xffff;
+                if (op.kind == OP_RXD || op.kind == OP_GRADG) lev[sweep_slot(op.arg)] = sweep_level(op.arg);
             NvtxRange range("qaoa adjoint pass");
             pick_grad_kernel<real>(a, s->g.weighted)<<<(unsigned)gt, 1u << (Q - R), smem, s->stream>>>(a);
             CUDA_TRY(cudaGetLastError());

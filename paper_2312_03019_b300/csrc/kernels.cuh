@@ -115,6 +115,7 @@ struct TileArgs {
     const void* phase;   // [level][E1] complex<real>
     const void* mix;     // [3 * level + i]: (cos b, sin b), (t, 0), (f, 0) as complex<real>
     double2* partials;   // [tile] (sum |psi|^2 C, sum |psi|^2); adjoint sweep: [2 tile + slot]
+    const double* gpow;  // adjoint sweep, complex64: [level][kMaxN + 1], entry s = (1 + t_level^2)^-s
     uint16_t* cutout;    // [2^n] cut values (OP_CUTVAL)
     unsigned* bounds_flag;  // debug builds: the index-check word (NULL: no reporting)
 };
@@ -149,6 +150,10 @@ struct CoeffArgs {
     int32_t fold_factors;       // 1: multiply the phase tables by the mixers' factors (tile passes)
     int32_t fold[kLayerChunk];  // 1: the tile passes apply level k as -i X RX(2 beta - pi)
     int32_t gre, gim;           // exact factor in {1, -i, -1, i} folded into the last phase table
+    // complex64 adjoint sweep: level k's table is exp(-i gamma_k c) times |f_k|^n (f_k the matched
+    // factor of the level's butterflies) and gpow[k][s] = f_k^(2 s), s = 0..kMaxN
+    int32_t sweep;
+    double* gpow;
     double gamma[kLayerChunk];
     double beta[kLayerChunk];
     void* phase;
@@ -156,6 +161,13 @@ struct CoeffArgs {
 };
 
 constexpr int kSmallThreadsGrad = 512;
+
+// Argument word of the adjoint sweep's RXD and GRADG ops: level in bits 0..15, accumulator slot in
+// bit 16, and for RXD the number of the level's qubits whose butterflies ran before the op in
+// bits 17..22 (the complex64 sweep's butterflies carry a real factor per qubit, see rxd_parity).
+__host__ __device__ constexpr int sweep_level(int32_t arg) { return arg & 0xffff; }
+__host__ __device__ constexpr int sweep_slot(int32_t arg) { return (arg >> 16) & 1; }
+__host__ __device__ constexpr int sweep_done(int32_t arg) { return (arg >> 17) & 63; }
 
 // ---------------------------------------------------------------------------------- helpers
 
@@ -309,7 +321,7 @@ __device__ void weighted_cta_setup(const TileArgs<Q>& a, uint64_t zb, WA* sK, WA
 
 // ---------------------------------------------------------------------------------- tile pass
 
-template <typename real, int Q, int R, bool kGP = false>
+template <typename real, int Q, int R, bool kGP = false, int kSw = 0>
 struct Tile {
     using C2 = typename C2T<real>::type;
     static constexpr int NT = 1 << (Q - R);
@@ -357,10 +369,23 @@ struct Tile {
     //     (l, l ^ 1) stays one aligned 16-byte vector.  8-byte accesses of layouts 0 and 1 hit 16
     //     distinct 8-byte slots per half warp; layout 2 moves pairs with 16-byte accesses, 8
     //     distinct 16-byte slots per quarter warp.
+    //   complex64 passes that use layouts 0 and 1 only (kSw = 1): bit 3 ^= l8, which is enough
+    //     for those two (a half warp covers l0..l3 in layout 0, where l8 is a register bit, and
+    //     l0..l2, l8 in layout 1, where l3 is one), and leaves the register bits of both layouts
+    //     apart from the thread bits but for bit 3: an address is one of two per-thread bases
+    //     plus a compile-time offset (see to_smem).
     //   complex128 (16 B, Q = 12): bits 0..4 ^= bits 4..8; 8 distinct slots per quarter warp in
     //     every layout.
     static __host__ __device__ constexpr uint32_t swz(uint32_t l) {
+        if (kPair && kSw == 1) return l ^ (((l >> 8) & 1u) << 3);
         return kPair ? (l ^ (((l >> 4) & 14u) ^ ((l >> 5) & 8u))) : (l ^ ((l >> 4) & 31u));
+    }
+    // kSw = 1, layouts 0 and 1: the byte offset of register slot x is P_b + off(x), P_b the
+    // thread's swizzled base with bit 3 flipped by b = x & 1 (l8 in layout 0, l3 in layout 1),
+    // off(x) the rest of x's bits (l9..l12 / l4..l7), disjoint from every thread bit.
+    template <int L, int x>
+    static __host__ __device__ constexpr uint32_t sw1_off() {
+        return L == 0 ? ((uint32_t)x << 8) * 8u : ((uint32_t)(x >> 1) << 4) * 8u;
     }
 
     // local bits of thread `tid` in layout L (register bits zero)
@@ -547,12 +572,24 @@ struct Tile {
     }
 
     // Shared-memory exchange: byte offset = (swizzled thread part) XOR (compile-time register part).
+    // An exchange from layout Lp writes each of the thread's amplitudes at the position its index
+    // maps to, which is exactly where the thread read them in the previous exchange (whose target
+    // layout was Lp); so one barrier, between the writes and the reads, is enough: no thread can
+    // overwrite a position another thread has still to read.  A pass's first exchange finds the
+    // tile unused (one tile per CTA).
     template <int L>
     static __device__ __forceinline__ void to_smem(const C2 (&v)[NE], unsigned char* tile, uint32_t tid,
                                                    unsigned* bf = nullptr) {
         constexpr uint32_t kBytes = (1u << Q) * (uint32_t)sizeof(C2);
         const uint32_t P = swz(tbits(L, tid)) * (uint32_t)sizeof(C2);
-        if constexpr (kPair && L == 2) {  // register bit 0 is local bit 0: store amplitude pairs
+        if constexpr (kPair && kSw == 1 && L != 2) {
+            const uint32_t Pb[2] = {P, P ^ 64u};
+            for_x<NE>([&](auto X) {
+                constexpr int x = decltype(X)::value;
+                const uint32_t o = Pb[x & 1] + sw1_off<L, x>();
+                if (QAOA_IN_BOUNDS(bf, o + 8u <= kBytes, 4u)) *reinterpret_cast<C2*>(tile + o) = from_reg<x>(v[x]);
+            });
+        } else if constexpr (kPair && L == 2) {  // register bit 0 is local bit 0: store amplitude pairs
             for_x<NE / 2>([&](auto H) {
                 constexpr int x = 2 * decltype(H)::value;
                 const C2 a = from_reg<x>(v[x]), b = from_reg<x + 1>(v[x + 1]);
@@ -575,7 +612,17 @@ struct Tile {
                                                      unsigned* bf = nullptr) {
         constexpr uint32_t kBytes = (1u << Q) * (uint32_t)sizeof(C2);
         const uint32_t P = swz(tbits(L, tid)) * (uint32_t)sizeof(C2);
-        if constexpr (kPair && L == 2) {
+        if constexpr (kPair && kSw == 1 && L != 2) {
+            const uint32_t Pb[2] = {P, P ^ 64u};
+            for_x<NE>([&](auto X) {
+                constexpr int x = decltype(X)::value;
+                const uint32_t o = Pb[x & 1] + sw1_off<L, x>();
+                if (QAOA_IN_BOUNDS(bf, o + 8u <= kBytes, 8u))
+                    v[x] = to_reg<x>(*reinterpret_cast<const C2*>(tile + o));
+                else
+                    v[x] = make_c2((real)0, (real)0);
+            });
+        } else if constexpr (kPair && L == 2) {
             for_x<NE / 2>([&](auto H) {
                 constexpr int x = 2 * decltype(H)::value;
                 const uint32_t o = P ^ (swz((uint32_t)x) * 8u);
@@ -793,6 +840,127 @@ struct Tile {
         return acc;
     }
 
+    // complex64 adjoint sweep in the parity form (kGP): RX(2 beta)^dagger on psi (v) and lambda
+    // (w) for the masked register bits as the butterflies a' = a + i t b, b' = b + i t a (one
+    // packed FMA per amplitude per state; `tn` = -sg t), which leave a real factor 1/f with
+    // f^2 = 1 / (1 + t^2) on every amplitude of both states per qubit.  Before the butterflies it
+    // sums the pair terms Im(conj(l_a) p_b + conj(l_b) p_a) of Im <lambda| X_j |psi> over the masked
+    // bits j: a pair term of level k is unchanged by the level's RX gates on either state (they
+    // commute with X_j), so measured before this op's butterflies it is the true term times
+    // (1/f^2)^s, s = the level's qubits done before the op; the caller applies f^(2 s).  With x
+    // the even-parity slot of a pair (the (re, im) form when P = 0) and y the other, the term is
+    // (E.x - E.y) - (F.x - F.y) with E = w[x] v[y] and F = w[y] v[x] componentwise; a thread with
+    // P = 1 has every form flipped and gets the negative, so the caller also multiplies by sg.
+    static __device__ __forceinline__ real rxd_parity(C2 (&v)[NE], C2 (&w)[NE], uint32_t mask, real tn) {
+        C2 E0 = make_c2((real)0, (real)0), F0 = E0, E1 = E0, F1 = E0;
+        for_x<R>([&](auto J) {
+            constexpr int j = decltype(J)::value;
+            if (!((mask >> j) & 1u)) return;
+            for_x<NE>([&](auto X) {
+                constexpr int x = decltype(X)::value;
+                if constexpr (!(x & (1 << j))) {
+                    constexpr int y = x | (1 << j);
+                    constexpr int xe = odd_parity(x) ? y : x, xo = odd_parity(x) ? x : y;
+                    if constexpr (j % 2 == 0) {
+                        E0 = ffma2(w[xe], v[xo], E0);
+                        F0 = ffma2(w[xo], v[xe], F0);
+                    } else {
+                        E1 = ffma2(w[xe], v[xo], E1);
+                        F1 = ffma2(w[xo], v[xe], F1);
+                    }
+                }
+            });
+        });
+        for_x<R>([&](auto J) {
+            constexpr int j = decltype(J)::value;
+            if (!((mask >> j) & 1u)) return;
+            const C2 cp = make_c2(tn, -tn), cm = make_c2(-tn, tn);
+            for_x<NE>([&](auto X) {
+                constexpr int x = decltype(X)::value;
+                if constexpr (!(x & (1 << j))) {
+                    constexpr int y = x | (1 << j);
+                    constexpr int xn = odd_parity(x) ? y : x, xs = odd_parity(x) ? x : y;
+                    const C2 n0 = v[xn], s0 = v[xs], m0 = w[xn], r0 = w[xs];
+                    v[xn] = ffma2(cp, s0, n0);
+                    v[xs] = ffma2(cm, n0, s0);
+                    w[xn] = ffma2(cp, r0, m0);
+                    w[xs] = ffma2(cm, m0, r0);
+                }
+            });
+        });
+        return ((E0.x - E0.y) - (F0.x - F0.y)) + ((E1.x - E1.y) - (F1.x - F1.y));
+    }
+
+    // complex64 sweep (kGP): sum_z C(z) Im(conj(lambda_z) psi_z) for the P = 0 orientation (the
+    // caller multiplies by sg): a (re, im) slot gives w.x v.y - w.y v.x, an (im, re) slot its
+    // negative.
+    template <int L, bool kW = false>
+    static __device__ __forceinline__ real grad_gamma_parity(const C2 (&v)[NE], const C2 (&w)[NE], const Ctx& c,
+                                                             uint32_t tid) {
+        const TileArgs<Q>& a = *c.a;
+        real acc_e = 0, acc_o = 0;
+        if constexpr (kW) {
+            WA s[R], P[NP];
+            const WA base = wsetup<L>(c, tid, 0, s, P);
+            for_x<NE>([&](auto X) {
+                constexpr int x = decltype(X)::value;
+                const real d = (real)(SWA)wat<x>(base, s, P) * (w[x].x * v[x].y - w[x].y * v[x].x);
+                if constexpr (odd_parity(x)) acc_o += d;
+                else acc_e += d;
+            });
+            return (real)((double)(acc_e - acc_o) * a.vscale);
+        } else {
+            int s[R];
+            const int base = cut_setup<L>(c, tid, s);
+            for_x<NE>([&](auto X) {
+                constexpr int x = decltype(X)::value;
+                int cidx = base + a.crtab[L][x];
+#pragma unroll
+                for (int j = 0; j < R; ++j)
+                    if ((x >> j) & 1) cidx += s[j];
+                const real d = (real)cidx * (w[x].x * v[x].y - w[x].y * v[x].x);
+                if constexpr (odd_parity(x)) acc_o += d;
+                else acc_e += d;
+            });
+            return acc_e - acc_o;
+        }
+    }
+
+    // complex64 sweep (kGP): exp(+i gamma C(z)) times the table's real factor on both states: the
+    // conjugate of the table entry applied in the slot's form (as in `phase`).
+    template <int L, bool kW = false>
+    static __device__ __forceinline__ void phase_dual_parity(C2 (&v)[NE], C2 (&w)[NE], const Ctx& c, uint32_t tid,
+                                                             int level) {
+        const TileArgs<Q>& a = *c.a;
+        const C2* __restrict__ T = reinterpret_cast<const C2*>(a.phase) + (size_t)level * a.E1;
+        if constexpr (kW) {
+            WA s[R], P[NP];
+            const WA base = wsetup<L>(c, tid, a.wslot[level], s, P);
+            for_x<NE>([&](auto X) {
+                constexpr int x = decltype(X)::value;
+                const C2 f = phase_tab(wat<x>(base, s, P), T);
+                const C2 fc = make_c2(f.x, -f.y);
+                v[x] = apply_phase<x>(v[x], fc, c.sg);
+                w[x] = apply_phase<x>(w[x], fc, c.sg);
+            });
+            return;
+        }
+        int s[R];
+        const int base = cut_setup<L>(c, tid, s);
+        for_x<NE>([&](auto X) {
+            constexpr int x = decltype(X)::value;
+            int cidx = base + a.crtab[L][x];
+#pragma unroll
+            for (int j = 0; j < R; ++j)
+                if ((x >> j) & 1) cidx += s[j];
+            (void)QAOA_IN_BOUNDS(a.bounds_flag, (unsigned)cidx < (unsigned)a.E1, 16u);
+            const C2 f = __ldg(T + min((unsigned)cidx, (unsigned)(a.E1 - 1)));
+            const C2 fc = make_c2(f.x, -f.y);
+            v[x] = apply_phase<x>(v[x], fc, c.sg);
+            w[x] = apply_phase<x>(w[x], fc, c.sg);
+        });
+    }
+
     // sum_z C(z) Im(conj(lambda_z) psi_z) over the thread's amplitudes
     template <int L, bool kW = false>
     static __device__ __forceinline__ real grad_gamma(const C2 (&v)[NE], const C2 (&w)[NE], const Ctx& c, uint32_t tid) {
@@ -972,6 +1140,13 @@ __host__ __device__ constexpr int recipe_layout2(uint64_t lo, uint64_t hi, int i
             L = (int)(((k < 10 ? lo >> (6 * k) : hi >> (6 * (k - 10))) >> 4) & 3u);
     return L;
 }
+// True when some op of a compiled program switches to register layout 2.
+__host__ __device__ constexpr bool recipe_uses_layout2(uint64_t lo, uint64_t hi, int nops) {
+    for (int i = 0; i < nops; ++i)
+        if (sets_layout(recipe_kind2(lo, hi, i)) && recipe_layout2(lo, hi, i) == 2) return true;
+    return false;
+}
+
 // Step i of a two-word program: in lo for i < 10, else in hi.
 __host__ __device__ constexpr uint64_t recipe_step_lo(int i, int kind, int layout) {
     return i < 10 ? recipe_step(i, kind, layout) : 0;
@@ -1103,7 +1278,10 @@ template <typename real, int Q, int R, bool kW, uint64_t kRecipe = 0, int kNops 
           uint64_t kRecipeHi = 0>
 __global__ void __launch_bounds__(1 << (Q - R), tile_min_blocks<real, kW>(kRecipe, kNops))
     tile_kernel(const __grid_constant__ TileArgs<Q> a) {
-    using T = Tile<real, Q, R, true>;
+    // compiled programs that stay in layouts 0 and 1 (the high-group passes) use the swizzle with
+    // immediate shared-memory offsets
+    constexpr int kSw = (kNops > 0 && !recipe_uses_layout2(kRecipe, kRecipeHi, kNops)) ? 1 : 0;
+    using T = Tile<real, Q, R, true, kSw>;
     using C2 = typename T::C2;
     using WA = typename T::WA;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1167,7 +1345,8 @@ __global__ void __launch_bounds__(1 << (Q - R), tile_min_blocks<real, kW>(kRecip
             } else if constexpr (kind == OP_LOAD) {
                 T::template load<Lc>(v, c, tid);
             } else if constexpr (kind == OP_XCHG) {
-                __syncthreads();
+                // no barrier before the writes: a thread writes exactly the tile positions it read
+                // in the previous exchange, or the tile is still unused (see to_smem)
                 T::template to_smem<Lp>(v, tile, tid, a.bounds_flag);
                 __syncthreads();
                 T::template from_smem<Lc>(v, tile, tid, a.bounds_flag);
@@ -1210,7 +1389,6 @@ __global__ void __launch_bounds__(1 << (Q - R), tile_min_blocks<real, kW>(kRecip
                 else T::template load<2>(v, c, tid);
                 break;
             case OP_XCHG:
-                __syncthreads();
                 if (L == 0) T::template to_smem<0>(v, tile, tid, a.bounds_flag);
                 else if (L == 1) T::template to_smem<1>(v, tile, tid, a.bounds_flag);
                 else T::template to_smem<2>(v, tile, tid, a.bounds_flag);
@@ -1279,7 +1457,11 @@ __global__ void __launch_bounds__(1 << (Q - R), tile_min_blocks<real, kW>(kRecip
 // (complex64 holds both states in 64 registers and runs two CTAs per SM; complex128 needs 128)
 template <typename real, int Q, int R, bool kW, uint64_t kRecipe = 0, int kNops = 0>
 __global__ void __launch_bounds__(1 << (Q - R), sizeof(real) == 4 ? 2 : 1) grad_kernel(const __grid_constant__ TileArgs<Q> a) {
-    using T = Tile<real, Q, R>;
+    // complex64: both states in the forward passes' parity form, packed butterflies with the real
+    // factors undone through a.gpow and the sweep's phase tables; complex128: plain form, exact
+    // RX(2 beta)^dagger butterflies
+    constexpr bool kPG = sizeof(real) == 4;
+    using T = Tile<real, Q, R, kPG>;
     using C2 = typename T::C2;
     using WA = typename T::WA;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1315,12 +1497,34 @@ __global__ void __launch_bounds__(1 << (Q - R), sizeof(real) == 4 ? 2 : 1) grad_
     c.sE = sE;
     c.wK = sKw;
     c.wE = sEw;
-    c.sg = (real)1;
+    c.sg = (kPG && (((__popcll(zb) + __popc(tid)) & 1) != 0)) ? (real)-1 : (real)1;  // P of the parity form
 
     C2 v[T::NE], w[T::NE];
     int L = 0;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};  // (pair terms, gamma terms) for slots 0 and 1
     const bool lam_init = a.nops > 1 && a.ops[1].kind == OP_LAMBDA;
+    // d/d beta pair terms of one RXD op (and its butterflies), as a true-scale FP64 sum
+    auto rxd_op = [&](const Op& op, C2(&vv)[T::NE], C2(&ww)[T::NE]) -> double {
+        const int level = sweep_level(op.arg);
+        if constexpr (kPG) {
+            const real t = reinterpret_cast<const C2*>(a.mix)[3 * level + 1].x;
+            const real d = T::rxd_parity(vv, ww, op.mask, -c.sg * t);
+            return (double)(c.sg * d) * a.gpow[level * (kMaxN + 1) + sweep_done(op.arg)];
+        } else {
+            const C2 cs = reinterpret_cast<const C2*>(a.mix)[3 * level];
+            return (double)T::rx_dual(vv, ww, op.mask, cs.x, cs.y);
+        }
+    };
+    // d/d gamma terms of one GRADG op (after all n butterflies of its level), true scale
+    auto gradg_op = [&](auto Lt, const Op& op, const C2(&vv)[T::NE], const C2(&ww)[T::NE]) -> double {
+        constexpr int Lx = decltype(Lt)::value;
+        if constexpr (kPG) {
+            const real g = T::template grad_gamma_parity<Lx, kW>(vv, ww, c, tid);
+            return (double)(c.sg * g) * a.gpow[sweep_level(op.arg) * (kMaxN + 1) + a.n];
+        } else {
+            return (double)T::template grad_gamma<Lx, kW>(vv, ww, c, tid);
+        }
+    };
 
 #define QAOA_BY_LAYOUT(F, ...)                     \
     do {                                           \
@@ -1339,7 +1543,7 @@ __global__ void __launch_bounds__(1 << (Q - R), sizeof(real) == 4 ? 2 : 1) grad_
                 T::template load_from<Lc>(v, c, tid, a.state);
                 T::template load_from<Lc>(w, c, tid, a.state2);
             } else if constexpr (kind == OP_XCHG) {
-                __syncthreads();
+                // psi first, at the positions this thread read lambda from last (see to_smem)
                 T::template to_smem<Lp>(v, tile, tid, a.bounds_flag);
                 __syncthreads();
                 T::template from_smem<Lc>(v, tile, tid, a.bounds_flag);
@@ -1349,16 +1553,16 @@ __global__ void __launch_bounds__(1 << (Q - R), sizeof(real) == 4 ? 2 : 1) grad_
                 T::template from_smem<Lc>(w, tile, tid, a.bounds_flag);
             } else if constexpr (kind == OP_RXD) {
                 const Op op = a.ops[i];
-                const C2 cs = reinterpret_cast<const C2*>(a.mix)[3 * (op.arg & 0xffff)];
-                const double d = (double)T::rx_dual(v, w, op.mask, cs.x, cs.y);
-                if (op.arg >> 16) acc[2] += d;
+                const double d = rxd_op(op, v, w);
+                if (sweep_slot(op.arg)) acc[2] += d;
                 else acc[0] += d;
             } else if constexpr (kind == OP_GRADG) {
-                const double d = (double)T::template grad_gamma<Lc, kW>(v, w, c, tid);
-                if (a.ops[i].arg >> 16) acc[3] += d;
+                const double d = gradg_op(std::integral_constant<int, Lc>{}, a.ops[i], v, w);
+                if (sweep_slot(a.ops[i].arg)) acc[3] += d;
                 else acc[1] += d;
             } else if constexpr (kind == OP_PHASED) {
-                T::template phase_dual<Lc, kW>(v, w, c, tid, a.ops[i].arg);
+                if constexpr (kPG) T::template phase_dual_parity<Lc, kW>(v, w, c, tid, a.ops[i].arg);
+                else T::template phase_dual<Lc, kW>(v, w, c, tid, a.ops[i].arg);
             } else if constexpr (kind == OP_STORE) {
                 T::template store_to<Lc>(v, c, tid, a.state);
                 T::template store_to<Lc>(w, c, tid, a.state2);
@@ -1380,7 +1584,6 @@ __global__ void __launch_bounds__(1 << (Q - R), sizeof(real) == 4 ? 2 : 1) grad_
                 break;
             case OP_XCHG: {
                 const int Lold = L;
-                __syncthreads();
                 QAOA_BY_LAYOUT(to_smem, v, tile, tid, a.bounds_flag);
                 __syncthreads();
                 L = op.layout;
@@ -1393,25 +1596,27 @@ __global__ void __launch_bounds__(1 << (Q - R), sizeof(real) == 4 ? 2 : 1) grad_
                 QAOA_BY_LAYOUT(from_smem, w, tile, tid, a.bounds_flag);
                 break;
             }
-            case OP_RXD: {
-                const int level = op.arg & 0xffff, slot = op.arg >> 16;
-                const C2 cs = reinterpret_cast<const C2*>(a.mix)[3 * level];
-                acc[2 * slot] += (double)T::rx_dual(v, w, op.mask, cs.x, cs.y);
+            case OP_RXD:
+                acc[2 * sweep_slot(op.arg)] += rxd_op(op, v, w);
                 break;
-            }
             case OP_GRADG: {
-                const int slot = op.arg >> 16;
-                real g = 0;
-                if (L == 0) g = T::template grad_gamma<0, kW>(v, w, c, tid);
-                else if (L == 1) g = T::template grad_gamma<1, kW>(v, w, c, tid);
-                else g = T::template grad_gamma<2, kW>(v, w, c, tid);
-                acc[2 * slot + 1] += (double)g;
+                double g = 0;
+                if (L == 0) g = gradg_op(std::integral_constant<int, 0>{}, op, v, w);
+                else if (L == 1) g = gradg_op(std::integral_constant<int, 1>{}, op, v, w);
+                else g = gradg_op(std::integral_constant<int, 2>{}, op, v, w);
+                acc[2 * sweep_slot(op.arg) + 1] += g;
                 break;
             }
             case OP_PHASED:
-                if (L == 0) T::template phase_dual<0, kW>(v, w, c, tid, op.arg);
-                else if (L == 1) T::template phase_dual<1, kW>(v, w, c, tid, op.arg);
-                else T::template phase_dual<2, kW>(v, w, c, tid, op.arg);
+                if constexpr (kPG) {
+                    if (L == 0) T::template phase_dual_parity<0, kW>(v, w, c, tid, op.arg);
+                    else if (L == 1) T::template phase_dual_parity<1, kW>(v, w, c, tid, op.arg);
+                    else T::template phase_dual_parity<2, kW>(v, w, c, tid, op.arg);
+                } else {
+                    if (L == 0) T::template phase_dual<0, kW>(v, w, c, tid, op.arg);
+                    else if (L == 1) T::template phase_dual<1, kW>(v, w, c, tid, op.arg);
+                    else T::template phase_dual<2, kW>(v, w, c, tid, op.arg);
+                }
                 break;
             case OP_STORE:
                 L = op.layout;
@@ -1713,6 +1918,14 @@ __global__ void coeff_kernel(const __grid_constant__ CoeffArgs a) {
     if (a.fold_factors) {
         if (k > 0) mult *= pow(mixer_factor<real>(a.beta[k - 1], a.fold[k - 1]), (double)a.n);
         if (last) mult *= pow(mixer_factor<real>(a.beta[k], a.fold[k]), (double)a.n);
+    }
+    if (a.sweep && k < a.levels) {
+        const double f = mixer_factor<real>(a.beta[k], a.fold[k]);
+        mult = pow(fabs(f), (double)a.n);
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            double q = 1.0;
+            for (int sdone = 0; sdone <= kMaxN; ++sdone, q *= f * f) a.gpow[(size_t)k * (kMaxN + 1) + sdone] = q;
+        }
     }
     if (a.weighted) coeff_weighted_rows<real>(a, k);
     if (k >= a.levels) return;  // levels == 0: only the endpoint and value rows

@@ -81,7 +81,7 @@ struct SReq {
 
 // Device block of a request that runs alone (offsets from the block start).
 struct Layout {
-    size_t state, work, phase, mix, partials, result, gtab, gmix, gacc, gpart, wfix, gwfix, total;
+    size_t state, work, phase, mix, partials, result, gtab, gmix, gacc, gpart, gpow, wfix, gwfix, total;
 };
 
 Layout single_layout(const HostGraph& g, int p, int prec, bool grad, uint64_t ntiles) {
@@ -106,6 +106,7 @@ Layout single_layout(const HostGraph& g, int p, int prec, bool grad, uint64_t nt
         L.gmix = take((size_t)3 * p * eb);
         L.gacc = take((size_t)2 * p * sizeof(double));
         L.gpart = take((size_t)2 * grad_tiles(n) * sizeof(double2));
+        L.gpow = take((size_t)p * (kMaxN + 1) * sizeof(double));
         if (g.weighted) L.gwfix = take(wfix_bytes(g, prec, p));
     }
     L.total = o;
@@ -313,6 +314,7 @@ qaoa_status dispatch_single(qaoa_server_s* sv, SReq&& r, size_t off, const Layou
         st->d_gmix = base + L.gmix;
         st->d_gacc = reinterpret_cast<double*>(base + L.gacc);
         st->d_gpart = reinterpret_cast<double2*>(base + L.gpart);
+        st->d_gpow = reinterpret_cast<double*>(base + L.gpow);
         if (r.g.weighted) st->d_gwfix = base + L.gwfix;
     }
     run.st = st;
@@ -343,6 +345,7 @@ qaoa_status dispatch_single(qaoa_server_s* sv, SReq&& r, size_t off, const Layou
         st->d_gtab = st->d_gmix = nullptr;
         st->d_gacc = nullptr;
         st->d_gpart = nullptr;
+        st->d_gpow = nullptr;
         st->d_wfix = st->d_gwfix = nullptr;
         delete st;
         return s;
@@ -496,6 +499,7 @@ bool scheduler_turn(qaoa_server_s* sv) {
         st->d_gtab = st->d_gmix = nullptr;
         st->d_gacc = nullptr;
         st->d_gpart = nullptr;
+        st->d_gpow = nullptr;
         st->d_wfix = st->d_gwfix = nullptr;
         delete st;
         sv->inflight--;
