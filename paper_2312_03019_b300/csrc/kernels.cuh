@@ -1032,8 +1032,35 @@ struct Tile {
     // not applied here; coeff_kernel folds them into the phase tables.  Register bits outside
     // the op's mask get t = 0, an exact identity, so the code has no data-dependent branches.
     // complex64: with N the (re, im) slot and S the (im, re) slot of a pair,
-    //   N' = (t, -t) * S + N   and   S' = (-t, t) * N + S   (two packed FMAs per pair).
-    template <bool kFull>
+    //   N' = (t, -t) * S + N   and   S' = (-t, t) * N + S
+    // as two packed FMAs (FFMA2), or, with kScalar, as the same four FMAs one lane at a time
+    // (bit-identical: FFMA2 rounds each lane as one FMA).  Which is faster depends on the pass
+    // (see recipe_scalar_fma).
+    template <bool kScalar>
+    static __device__ __forceinline__ void bfly(C2& n, C2& sw, const C2 cp, const C2 cm) {
+        const C2 n0 = n, s0 = sw;
+        if constexpr (kScalar) {
+            n = make_c2(fma(cp.x, s0.x, n0.x), fma(cp.y, s0.y, n0.y));
+            sw = make_c2(fma(cm.x, n0.x, s0.x), fma(cm.y, n0.y, s0.y));
+        } else {
+            n = ffma2(cp, s0, n0);
+            sw = ffma2(cm, n0, s0);
+        }
+    }
+    template <int x, bool kScalar>
+    static __device__ __forceinline__ void bfly_pair(C2 (&v)[NE], int j, real T, real nT) {
+        const int y = x | (1 << j);
+        if constexpr (kSwapOdd) {
+            const C2 cp = make_c2(T, nT), cm = make_c2(nT, T);
+            if constexpr (!odd_parity(x)) bfly<kScalar>(v[x], v[y], cp, cm);
+            else bfly<kScalar>(v[y], v[x], cp, cm);
+        } else {
+            const C2 p = v[x], q = v[y];
+            v[x] = make_c2(fma(T, q.y, p.x), fma(nT, q.x, p.y));
+            v[y] = make_c2(fma(T, p.y, q.x), fma(nT, p.x, q.y));
+        }
+    }
+    template <bool kFull, bool kScalar = false>
     static __device__ __forceinline__ void rx_bits(C2 (&v)[NE], uint32_t mask, real t) {
 #pragma unroll
         for (int j = 0; j < R; ++j) {
@@ -1041,65 +1068,29 @@ struct Tile {
             const real nT = -T;
             for_x<NE>([&](auto X) {
                 constexpr int x = decltype(X)::value;
-                if (!(x & (1 << j))) {
-                    const int y = x | (1 << j);
-                    if constexpr (kSwapOdd) {
-                        const C2 cp = make_c2(T, nT), cm = make_c2(nT, T);
-                        if constexpr (!odd_parity(x)) {
-                            const C2 n0 = v[x], s0 = v[y];
-                            v[x] = ffma2(cp, s0, n0);
-                            v[y] = ffma2(cm, n0, s0);
-                        } else {
-                            const C2 n0 = v[y], s0 = v[x];
-                            v[y] = ffma2(cp, s0, n0);
-                            v[x] = ffma2(cm, n0, s0);
-                        }
-                    } else {
-                        const C2 p = v[x], q = v[y];
-                        v[x] = make_c2(fma(T, q.y, p.x), fma(nT, q.x, p.y));
-                        v[y] = make_c2(fma(T, p.y, q.x), fma(nT, p.x, q.y));
-                    }
-                }
+                if (!(x & (1 << j))) bfly_pair<x, kScalar>(v, j, T, nT);
             });
         }
     }
 
     // RX on the register bits of a compile-time mask only (no butterflies for the other bits)
-    template <uint32_t kMask>
+    template <uint32_t kMask, bool kScalar = false>
     static __device__ __forceinline__ void rx_fixed(C2 (&v)[NE], real t) {
         for_x<R>([&](auto J) {
             constexpr int j = decltype(J)::value;
             if constexpr ((kMask >> j) & 1u) {
-                const real T = t, nT = -t;
                 for_x<NE>([&](auto X) {
                     constexpr int x = decltype(X)::value;
-                    if constexpr (!(x & (1 << j))) {
-                        constexpr int y = x | (1 << j);
-                        if constexpr (kSwapOdd) {
-                            const C2 cp = make_c2(T, nT), cm = make_c2(nT, T);
-                            if constexpr (!odd_parity(x)) {
-                                const C2 n0 = v[x], s0 = v[y];
-                                v[x] = ffma2(cp, s0, n0);
-                                v[y] = ffma2(cm, n0, s0);
-                            } else {
-                                const C2 n0 = v[y], s0 = v[x];
-                                v[y] = ffma2(cp, s0, n0);
-                                v[x] = ffma2(cm, n0, s0);
-                            }
-                        } else {
-                            const C2 p = v[x], q = v[y];
-                            v[x] = make_c2(fma(T, q.y, p.x), fma(nT, q.x, p.y));
-                            v[y] = make_c2(fma(T, p.y, q.x), fma(nT, p.x, q.y));
-                        }
-                    }
+                    if constexpr (!(x & (1 << j))) bfly_pair<x, kScalar>(v, j, t, -t);
                 });
             }
         });
     }
 
+    template <bool kScalar = false>
     static __device__ __forceinline__ void rx(C2 (&v)[NE], uint32_t mask, real t) {
-        if (mask == (1u << R) - 1u) rx_bits<true>(v, mask, t);
-        else rx_bits<false>(v, mask, t);
+        if (mask == (1u << R) - 1u) rx_bits<true, kScalar>(v, mask, t);
+        else rx_bits<false, kScalar>(v, mask, t);
     }
 
 };
@@ -1237,6 +1228,19 @@ __host__ __device__ constexpr uint64_t recipe_masks(int r) {
     return m;
 }
 
+// Complex64 recipes whose butterflies run as scalar FMAs: the first pass and the group-0 pass
+// (measured at n = 33: first pass 18.4 -> 16.6 ms, group-0 pass 23.4 -> 22.9 ms).  Packed FMAs
+// (FFMA2) need about 0.4-0.7 register moves each for a butterfly's old value (an FFMA2
+// accumulates in place), so they save fewer instructions than they seem to; the fused boundary
+// pass and the last pass are still faster packed (36.0 against 39.3 ms, 31.9 against 32.1 ms).
+template <typename real>
+__host__ __device__ constexpr bool recipe_scalar_fma(uint64_t recipe, int nops) {
+    if (sizeof(real) != 4 || nops == 0) return false;
+    for (int r : {0, 1})
+        if (recipe == base_recipe(r).code && nops == base_recipe(r).nops) return true;
+    return false;
+}
+
 #ifndef QAOA_TILE_MIN_BLOCKS
 #define QAOA_TILE_MIN_BLOCKS 2  // resident CTAs per SM the register budget is sized for
 #endif
@@ -1353,10 +1357,11 @@ __global__ void __launch_bounds__(1 << (Q - R), tile_min_blocks<real, kW>(kRecip
             } else if constexpr (kind == OP_RX) {
                 const Op op = a.ops[i];
                 constexpr uint32_t fm = i < 10 ? (uint32_t)((kMasks >> (6 * i)) & 63u) : 0u;
+                constexpr bool kScalar = recipe_scalar_fma<real>(kRecipe, kNops);
                 if constexpr ((fm & 32u) != 0)
-                    T::template rx_fixed<(fm & 31u)>(v, c.sg * mix[3 * op.arg + 1].x);
+                    T::template rx_fixed<(fm & 31u), kScalar>(v, c.sg * mix[3 * op.arg + 1].x);
                 else
-                    T::rx(v, op.mask, c.sg * mix[3 * op.arg + 1].x);
+                    T::template rx<kScalar>(v, op.mask, c.sg * mix[3 * op.arg + 1].x);
             } else if constexpr (kind == OP_PHASE) {
                 T::template phase<Lc, kW>(v, c, tid, a.ops[i].arg);
             } else if constexpr (kind == OP_EXPECT) {
