@@ -238,9 +238,11 @@ qaoa_status qaoa_expectation_static(const qaoa_graph *g, qaoa_prec prec, const v
  *     hbm_budget_bytes allocated at qaoa_server_create; at most max_inflight requests at once;
  *   - continuous batching: every scheduler turn packs all admitted small forward requests (whole
  *     state in one CTA: n <= 14 for complex64, n <= 13 for complex128) into one batched launch,
- *     one CTA per request, while larger requests run concurrently on a pool of `streams` CUDA
- *     streams; with use_graphs each launch sequence is recorded into a CUDA graph and replayed
- *     through an executable graph cached per request shape;
+ *     one CTA per request, and the admitted mid-size complex64 forward requests (15 <= n <= 22,
+ *     p <= 8, unit weights) of one (n, p) into packed launches (one launch per pass over every
+ *     tile of up to 32 requests), while larger requests run concurrently on a pool of `streams`
+ *     CUDA streams; with use_graphs each launch sequence is recorded into a CUDA graph and
+ *     replayed through an executable graph cached per request shape;
  *   - completion is detected with CUDA events; results land in pinned host memory.
  * Each result is computed by the same kernels and reduction order as a lone request, so it is
  * identical alone and in the mix. */
@@ -287,6 +289,8 @@ typedef struct {
     int64_t batches, batched_requests, single_requests, graph_launches;
     size_t arena_peak_bytes;
     int64_t timed_out;    /* requests whose deadline passed before dispatch (counted in failed) */
+    int64_t tiled_batches;          /* packed launches of mid-size (tiled) states */
+    int64_t tiled_batched_requests; /* requests that ran in them (also counted in batched_requests) */
 } qaoa_server_stats;
 
 typedef struct qaoa_server_s *qaoa_server;

@@ -114,7 +114,8 @@ class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
                 ("rejected_full", ctypes.c_int64), ("batches", ctypes.c_int64), ("batched_requests", ctypes.c_int64),
                 ("single_requests", ctypes.c_int64), ("graph_launches", ctypes.c_int64),
-                ("arena_peak_bytes", ctypes.c_size_t), ("timed_out", ctypes.c_int64)]
+                ("arena_peak_bytes", ctypes.c_size_t), ("timed_out", ctypes.c_int64),
+                ("tiled_batches", ctypes.c_int64), ("tiled_batched_requests", ctypes.c_int64)]
 
 
 _sig("qaoa_server_create", ctypes.c_int, [ctypes.POINTER(ServerConfig), ctypes.POINTER(_vp)])

@@ -411,39 +411,77 @@ TileFn<real> recipe_kernel(int r) {
     }
 }
 
-// The pass kernel for a program: a recipe instantiation when one matches (those with compiled-in
-// masks first, and only when the program's masks are exactly those), else the interpreting one.
+// The compiled recipe a program runs, or -1 for the interpreting instantiation: the first recipe
+// (those with compiled-in masks first, and only when the program's masks are exactly those) whose
+// ops and layouts equal the program's and which is compiled for this precision and weighting.
 // Edge weights enter only the phase, <C> and cut-value ops: a program without them (a plain mixer
 // pass) runs the unit-weight instance, whatever the graph.
+template <typename real>
+int pick_recipe(const TileArgs<PrecTraits<real>::Q>& a, bool weighted_graph) {
+    const bool weighted = weighted_graph && a.need_cut;
+    if (a.nops > 20) return -1;
+    uint64_t code = 0, hi = 0;
+    for (int i = 0; i < a.nops; ++i) {
+        code |= recipe_step_lo(i, a.ops[i].kind, a.ops[i].layout);
+        hi |= recipe_step_hi(i, a.ops[i].kind, a.ops[i].layout);
+    }
+    // the full-mask fused pass (6) spills: not used
+    const int order[] = {1, 5, 7, 0, 2, 3, 4, 8, 9, 10, 11, 12};
+    for (int r : order) {
+        const Recipe d = recipe_def(r);
+        if (d.nops != a.nops || d.code != code || d.hi != hi) continue;
+        bool masks_ok = true;
+        for (int i = 0; i < a.nops && i < 10; ++i) {
+            const uint32_t fm = (uint32_t)((recipe_masks<real>(r) >> (6 * i)) & 63u);
+            if ((fm & 32u) && a.ops[i].mask != (fm & 31u)) masks_ok = false;
+        }
+        if (!masks_ok) continue;
+        if (weighted ? recipe_kernel_w<real>(r) != nullptr : recipe_kernel<real>(r) != nullptr) return r;
+    }
+    return -1;
+}
+
+// The pass kernel for a program: its recipe instantiation, else the interpreting one.
 template <typename real>
 TileFn<real> pick_tile_kernel(const TileArgs<PrecTraits<real>::Q>& a, bool weighted_graph) {
     constexpr int Q = PrecTraits<real>::Q, R = PrecTraits<real>::R;
     const bool weighted = weighted_graph && a.need_cut;
-    if (a.nops <= 20) {
-        uint64_t code = 0, hi = 0;
-        for (int i = 0; i < a.nops; ++i) {
-            code |= recipe_step_lo(i, a.ops[i].kind, a.ops[i].layout);
-            hi |= recipe_step_hi(i, a.ops[i].kind, a.ops[i].layout);
-        }
-        // the full-mask fused pass (6) spills: not used
-        const int order[] = {1, 5, 7, 0, 2, 3, 4, 8, 9, 10, 11, 12};
-        for (int r : order) {
-            const Recipe d = recipe_def(r);
-            if (d.nops != a.nops || d.code != code || d.hi != hi) continue;
-            bool masks_ok = true;
-            for (int i = 0; i < a.nops && i < 10; ++i) {
-                const uint32_t fm = (uint32_t)((recipe_masks<real>(r) >> (6 * i)) & 63u);
-                if ((fm & 32u) && a.ops[i].mask != (fm & 31u)) masks_ok = false;
-            }
-            if (!masks_ok) continue;
-            if (!weighted) {
-                if (TileFn<real> f = recipe_kernel<real>(r)) return f;
-                continue;
-            }
-            if (TileFn<real> f = recipe_kernel_w<real>(r)) return f;
+    const int r = pick_recipe<real>(a, weighted_graph);
+    if (r >= 0) return weighted ? recipe_kernel_w<real>(r) : recipe_kernel<real>(r);
+    return weighted ? tile_kernel<real, Q, R, true> : tile_kernel<real, Q, R, false>;
+}
+
+// The packed (tile_batch_kernel) form of the kernel pick_tile_kernel gives a unit-weight
+// complex64 program, for the programs of the two-group plans (recipes 8..12 or the interpreting
+// instance); NULL for others, which then run alone.
+template <typename real>
+using TileBatchFn = void (*)(const TileArgs<PrecTraits<real>::Q>*);
+
+template <typename real, int r>
+constexpr TileBatchFn<real> batch_recipe_fn() {
+    return tile_batch_kernel<real, PrecTraits<real>::Q, PrecTraits<real>::R, false, recipe_def(r).code,
+                             recipe_def(r).nops, recipe_masks<real>(r), recipe_def(r).hi>;
+}
+
+template <typename real>
+TileBatchFn<real> batch_kernel_for(int r) {
+    if constexpr (std::is_same<real, float>::value) {
+        switch (r) {
+            case -1: return tile_batch_kernel<real, PrecTraits<real>::Q, PrecTraits<real>::R, false>;
+            case 8: return batch_recipe_fn<real, 8>();
+            case 9: return batch_recipe_fn<real, 9>();
+            case 10: return batch_recipe_fn<real, 10>();
+            case 11: return batch_recipe_fn<real, 11>();
+            case 12: return batch_recipe_fn<real, 12>();
+            default: return nullptr;
         }
     }
-    return weighted ? tile_kernel<real, Q, R, true> : tile_kernel<real, Q, R, false>;
+    return nullptr;
+}
+
+template <typename real>
+TileBatchFn<real> pick_tile_batch_kernel(const TileArgs<PrecTraits<real>::Q>& a) {
+    return batch_kernel_for<real>(pick_recipe<real>(a, false));
 }
 
 template <typename real>
@@ -503,6 +541,9 @@ qaoa_status ensure_attributes() {
         if (TileFn<real> f = recipe_kernel_w<real>(r))
             CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)((1u << Q) * sizeof(C2))));
     }
+    for (int r : {-1, 8, 9, 10, 11, 12})
+        if (TileBatchFn<real> f = batch_kernel_for<real>(r))
+            CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)((1u << Q) * sizeof(C2))));
     constexpr int GQ = GradTraits<real>::Q, GR = GradTraits<real>::R;
     CUDA_TRY(cudaFuncSetAttribute(grad_kernel<real, GQ, GR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)((1u << GQ) * sizeof(C2))));
@@ -613,9 +654,10 @@ qaoa_status run_plan(qaoa_state s, const Plan& plan) {
 template <typename real>
 qaoa_status set_parity_form(qaoa_state s, bool parity);
 
-template <typename real>
-qaoa_status apply_chunk(qaoa_state s, int levels, const double* gamma, const double* beta, bool expect) {
-    CoeffArgs ca;
+// Coefficient arguments of one chunk of levels of state s (phase tables and mixer entries into
+// s->d_phase / s->d_mix).  Returns whether the chunk leaves an odd number of folded levels, i.e.
+// toggles the pending complement.
+bool chunk_coeff_args(const qaoa_state_s* s, int levels, const double* gamma, const double* beta, CoeffArgs& ca) {
     std::memset(&ca, 0, sizeof(ca));
     ca.levels = levels;
     ca.E1 = table_entries(s->g);
@@ -636,10 +678,20 @@ qaoa_status apply_chunk(qaoa_state s, int levels, const double* gamma, const dou
     const int quarter = (int)(((int64_t)folded * s->n) % 4);  // (-i)^quarter
     ca.gre = quarter == 0 ? 1 : (quarter == 2 ? -1 : 0);
     ca.gim = quarter == 1 ? -1 : (quarter == 3 ? 1 : 0);
-    if (folded & 1) s->compl_ = !s->compl_;
     ca.phase = s->d_phase;
     ca.mix = s->d_mix;
-    dim3 grid((unsigned)std::max(1, (std::max(ca.E1, ca.m) + 255) / 256), (unsigned)levels);
+    return (folded & 1) != 0;
+}
+
+dim3 coeff_grid(const CoeffArgs& ca) {
+    return dim3((unsigned)std::max(1, (std::max(ca.E1, ca.m) + 255) / 256), (unsigned)std::max(1, ca.levels));
+}
+
+template <typename real>
+qaoa_status apply_chunk(qaoa_state s, int levels, const double* gamma, const double* beta, bool expect) {
+    CoeffArgs ca;
+    if (chunk_coeff_args(s, levels, gamma, beta, ca)) s->compl_ = !s->compl_;
+    dim3 grid = coeff_grid(ca);
     coeff_kernel<real><<<grid, 256, 0, s->stream>>>(ca);
     CUDA_TRY(cudaGetLastError());
     s->launches++;

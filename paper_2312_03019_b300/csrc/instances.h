@@ -1,6 +1,7 @@
-// instances.h -- the heavy kernel template instantiations (the pass kernels and the adjoint-sweep
-// kernels), each compiled in a translation unit of its own (tile_c64.cu, tile_c128.cu,
-// grad_kernels.cu, grad_recipes.cu, ...) so that the library builds in parallel.  capi.cu includes this file after
+// instances.h -- the heavy kernel template instantiations (the pass kernels, their packed forms and
+// the adjoint-sweep kernels), each compiled in a translation unit of its own (tile_c64.cu,
+// tile_c128.cu, batch_c64.cu, grad_kernels.cu, grad_recipes.cu, ...) so that the library builds
+// in parallel.  capi.cu includes this file after
 // kernels.cuh with QAOA_INSTANCE = "extern template" (declarations); each instance unit defines
 // QAOA_OWN_* for the set it owns and instantiates that set with QAOA_INSTANCE = "template".
 // Building this way needs -static-global-template-stub=false (external kernel stubs).
@@ -79,6 +80,24 @@
     QAOA_GRAD_RECIPE(real, Q, R, 2)                                                                    \
     }
 
+// packed mid-size requests of the server: the complex64 two-group programs (recipes 8..12) and the
+// interpreting program, unit weights
+#define QAOA_BATCH_ONE(real, Q, R, r)                                                                 \
+    QAOA_INSTANCE __global__ void tile_batch_kernel<real, Q, R, false, recipe_def(r).code, recipe_def(r).nops, \
+                                                    recipe_masks<real>(r), recipe_def(r).hi>(const TileArgs<Q>*);
+#define QAOA_BATCH_INSTANCES(real, Q, R)                                                              \
+    namespace qaoa {                                                                                   \
+    QAOA_INSTANCE __global__ void tile_batch_kernel<real, Q, R, false, 0, 0, 0, 0>(const TileArgs<Q>*);   \
+    QAOA_BATCH_ONE(real, Q, R, 8)                                                                      \
+    QAOA_BATCH_ONE(real, Q, R, 9)                                                                      \
+    QAOA_BATCH_ONE(real, Q, R, 10)                                                                     \
+    QAOA_BATCH_ONE(real, Q, R, 11)                                                                     \
+    QAOA_BATCH_ONE(real, Q, R, 12)                                                                     \
+    }
+
+#if !defined(QAOA_OWN_BATCH_C64)
+QAOA_BATCH_INSTANCES(float, 13, 5)
+#endif
 #if !defined(QAOA_OWN_TILE_C64)
 QAOA_TILE_INSTANCES(float, 13, 5)
 #endif

@@ -851,7 +851,13 @@ struct Tile {
     // the even-parity slot of a pair (the (re, im) form when P = 0) and y the other, the term is
     // (E.x - E.y) - (F.x - F.y) with E = w[x] v[y] and F = w[y] v[x] componentwise; a thread with
     // P = 1 has every form flipped and gets the negative, so the caller also multiplies by sg.
+    template <bool kScalar = false>
     static __device__ __forceinline__ real rxd_parity(C2 (&v)[NE], C2 (&w)[NE], uint32_t mask, real tn) {
+        // d += a * b componentwise, packed (FFMA2) or as two FMAs (bit-identical)
+        auto acc2 = [](C2 a, C2 b, C2 d) -> C2 {
+            if constexpr (kScalar) return make_c2(fma(a.x, b.x, d.x), fma(a.y, b.y, d.y));
+            else return ffma2(a, b, d);
+        };
         C2 E0 = make_c2((real)0, (real)0), F0 = E0, E1 = E0, F1 = E0;
         for_x<R>([&](auto J) {
             constexpr int j = decltype(J)::value;
@@ -862,11 +868,11 @@ struct Tile {
                     constexpr int y = x | (1 << j);
                     constexpr int xe = odd_parity(x) ? y : x, xo = odd_parity(x) ? x : y;
                     if constexpr (j % 2 == 0) {
-                        E0 = ffma2(w[xe], v[xo], E0);
-                        F0 = ffma2(w[xo], v[xe], F0);
+                        E0 = acc2(w[xe], v[xo], E0);
+                        F0 = acc2(w[xo], v[xe], F0);
                     } else {
-                        E1 = ffma2(w[xe], v[xo], E1);
-                        F1 = ffma2(w[xo], v[xe], F1);
+                        E1 = acc2(w[xe], v[xo], E1);
+                        F1 = acc2(w[xo], v[xe], F1);
                     }
                 }
             });
@@ -880,11 +886,8 @@ struct Tile {
                 if constexpr (!(x & (1 << j))) {
                     constexpr int y = x | (1 << j);
                     constexpr int xn = odd_parity(x) ? y : x, xs = odd_parity(x) ? x : y;
-                    const C2 n0 = v[xn], s0 = v[xs], m0 = w[xn], r0 = w[xs];
-                    v[xn] = ffma2(cp, s0, n0);
-                    v[xs] = ffma2(cm, n0, s0);
-                    w[xn] = ffma2(cp, r0, m0);
-                    w[xs] = ffma2(cm, m0, r0);
+                    bfly<kScalar>(v[xn], v[xs], cp, cm);
+                    bfly<kScalar>(w[xn], w[xs], cp, cm);
                 }
             });
         });
@@ -1278,10 +1281,9 @@ __host__ __device__ constexpr Recipe grad_recipe(int r) {
 }
 constexpr int kGradRecipes = 3;
 
-template <typename real, int Q, int R, bool kW, uint64_t kRecipe = 0, int kNops = 0, uint64_t kMasks = 0,
-          uint64_t kRecipeHi = 0>
-__global__ void __launch_bounds__(1 << (Q - R), tile_min_blocks<real, kW>(kRecipe, kNops))
-    tile_kernel(const __grid_constant__ TileArgs<Q> a) {
+// One pass over tile t of the state: the body of tile_kernel and tile_batch_kernel.
+template <typename real, int Q, int R, bool kW, uint64_t kRecipe, int kNops, uint64_t kMasks, uint64_t kRecipeHi>
+__device__ __forceinline__ void tile_body(const TileArgs<Q>& a, const uint64_t t) {
     // compiled programs that stay in layouts 0 and 1 (the high-group passes) use the swizzle with
     // immediate shared-memory offsets
     constexpr int kSw = (kNops > 0 && !recipe_uses_layout2(kRecipe, kRecipeHi, kNops)) ? 1 : 0;
@@ -1297,7 +1299,6 @@ __global__ void __launch_bounds__(1 << (Q - R), tile_min_blocks<real, kW>(kRecip
 
     unsigned char* tile = smem_raw;
     const uint32_t tid = threadIdx.x;
-    const uint64_t t = blockIdx.x;
     uint64_t zb = 0;  // outer index bits of tile t: runs of tile-id bits deposited in place
     for (int r = 0; r < a.nruns; ++r) zb |= ((t >> a.run_src[r]) & ((1ull << a.run_len[r]) - 1ull)) << a.run_dst[r];
 
@@ -1454,6 +1455,29 @@ __global__ void __launch_bounds__(1 << (Q - R), tile_min_blocks<real, kW>(kRecip
     }
 }
 
+template <typename real, int Q, int R, bool kW, uint64_t kRecipe = 0, int kNops = 0, uint64_t kMasks = 0,
+          uint64_t kRecipeHi = 0>
+__global__ void __launch_bounds__(1 << (Q - R), tile_min_blocks<real, kW>(kRecipe, kNops))
+    tile_kernel(const __grid_constant__ TileArgs<Q> a) {
+    tile_body<real, Q, R, kW, kRecipe, kNops, kMasks, kRecipeHi>(a, blockIdx.x);
+}
+
+// The same pass for blockIdx.y of several requests of one shape (the request server's packed
+// launches of mid-size states): request y's arguments are copied from args[y] into shared memory
+// first, so one launch covers every tile of every request.
+template <typename real, int Q, int R, bool kW, uint64_t kRecipe = 0, int kNops = 0, uint64_t kMasks = 0,
+          uint64_t kRecipeHi = 0>
+__global__ void __launch_bounds__(1 << (Q - R), tile_min_blocks<real, kW>(kRecipe, kNops))
+    tile_batch_kernel(const TileArgs<Q>* __restrict__ args) {
+    __shared__ __align__(16) TileArgs<Q> sa;
+    static_assert(sizeof(TileArgs<Q>) % 16 == 0, "TileArgs is copied in 16-byte words");
+    const uint4* src = reinterpret_cast<const uint4*>(args + blockIdx.y);
+    uint4* dst = reinterpret_cast<uint4*>(&sa);
+    for (uint32_t i = threadIdx.x; i < sizeof(TileArgs<Q>) / 16; i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+    tile_body<real, Q, R, kW, kRecipe, kNops, kMasks, kRecipeHi>(sa, blockIdx.x);
+}
+
 // ---------------------------------------------------------------------------------- adjoint sweep
 
 // One pass of the adjoint sweep over psi (a.state) and lambda (a.state2), same tiling as
@@ -1466,6 +1490,7 @@ __global__ void __launch_bounds__(1 << (Q - R), sizeof(real) == 4 ? 2 : 1) grad_
     // factors undone through a.gpow and the sweep's phase tables; complex128: plain form, exact
     // RX(2 beta)^dagger butterflies
     constexpr bool kPG = sizeof(real) == 4;
+    constexpr bool kSweepScalar = false;
     using T = Tile<real, Q, R, kPG>;
     using C2 = typename T::C2;
     using WA = typename T::WA;
@@ -1513,7 +1538,7 @@ __global__ void __launch_bounds__(1 << (Q - R), sizeof(real) == 4 ? 2 : 1) grad_
         const int level = sweep_level(op.arg);
         if constexpr (kPG) {
             const real t = reinterpret_cast<const C2*>(a.mix)[3 * level + 1].x;
-            const real d = T::rxd_parity(vv, ww, op.mask, -c.sg * t);
+            const real d = T::template rxd_parity<kSweepScalar>(vv, ww, op.mask, -c.sg * t);
             return (double)(c.sg * d) * a.gpow[level * (kMaxN + 1) + sweep_done(op.arg)];
         } else {
             const C2 cs = reinterpret_cast<const C2*>(a.mix)[3 * level];
@@ -1914,9 +1939,8 @@ __device__ void coeff_weighted_rows(const CoeffArgs& a, int k) {
 }
 
 template <typename real>
-__global__ void coeff_kernel(const __grid_constant__ CoeffArgs a) {
+__device__ __forceinline__ void coeff_body(const CoeffArgs& a, const int k) {
     using C2 = typename C2T<real>::type;
-    const int k = blockIdx.y;
     C2* T = reinterpret_cast<C2*>(a.phase) + (size_t)k * a.E1;
     const bool last = k == a.levels - 1;
     double mult = 1.0;
@@ -1961,6 +1985,18 @@ __global__ void coeff_kernel(const __grid_constant__ CoeffArgs a) {
             m[2] = make_c2((real)s, (real)0);
         }
     }
+}
+
+template <typename real>
+__global__ void coeff_kernel(const __grid_constant__ CoeffArgs a) {
+    coeff_body<real>(a, blockIdx.y);
+}
+
+// The coefficients of several requests in one launch (the server's packed mid-size states):
+// blockIdx.z picks the request, whose CoeffArgs are read from the device array.
+template <typename real>
+__global__ void coeff_batch_args_kernel(const CoeffArgs* __restrict__ args) {
+    coeff_body<real>(args[blockIdx.z], blockIdx.y);
 }
 
 // Batched coefficient tables for packed small states: CTA b builds job b's plain per-level
@@ -2022,8 +2058,8 @@ __global__ void complement_kernel(void* state, uint64_t dim, int complement, int
 
 // ---------------------------------------------------------------------------------- reductions / fill
 
-static __global__ void __launch_bounds__(1024) finalize_kernel(const double2* __restrict__ partials, uint64_t count,
-                                                        double2* __restrict__ out) {
+__device__ __forceinline__ void finalize_body(const double2* __restrict__ partials, uint64_t count,
+                                              double2* __restrict__ out) {
     __shared__ double sc[1024], sn[1024];
     double a = 0.0, b = 0.0;
     for (uint64_t i = threadIdx.x; i < count; i += 1024) {
@@ -2042,6 +2078,18 @@ static __global__ void __launch_bounds__(1024) finalize_kernel(const double2* __
         __syncthreads();
     }
     if (threadIdx.x == 0) *out = make_double2(sc[0], sn[0]);
+}
+
+static __global__ void __launch_bounds__(1024) finalize_kernel(const double2* __restrict__ partials, uint64_t count,
+                                                        double2* __restrict__ out) {
+    finalize_body(partials, count, out);
+}
+
+// finalize_kernel for blockIdx.x of several requests whose partials lie back to back, `count`
+// each (the same summation order, so each result equals the lone reduction bit for bit).
+static __global__ void __launch_bounds__(1024) finalize_batch_kernel(const double2* __restrict__ partials,
+                                                              uint64_t count, double2* __restrict__ out) {
+    finalize_body(partials + (size_t)blockIdx.x * count, count, out + blockIdx.x);
 }
 
 template <typename real>

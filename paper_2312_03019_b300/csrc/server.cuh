@@ -136,6 +136,37 @@ BatchLayout batch_layout(int maxB) {
     return L;
 }
 
+// Packed mid-size forward requests (tiled complex64 states that fit in two mixer groups): one
+// launch per pass covers every tile of up to kMidMaxB requests of one (n, p).
+constexpr int kMidMaxN = 22;
+constexpr int kMidMaxP = 8;
+constexpr int kMidMaxB = 32;
+constexpr int kMidStages = 4;
+
+// Head block of a packed mid-size launch (device) and its staging slot (pinned host), same layout:
+// [TileArgs, pass-major: pass i of request b at i * B + b][CoeffArgs x B][partials: B x tiles]
+// [results x B]; the first `upload` bytes go host -> device, the results come back.
+struct MidLayout {
+    size_t targs, cargs, partials, results, upload, total;
+};
+
+MidLayout mid_layout(int passes, int B, uint64_t tiles) {
+    MidLayout L{};
+    L.targs = 0;
+    L.cargs = Arena::round((size_t)passes * B * sizeof(TileArgs<PrecTraits<float>::Q>));
+    L.upload = L.cargs + Arena::round((size_t)B * sizeof(CoeffArgs));
+    L.partials = L.upload;
+    L.results = L.partials + Arena::round((size_t)B * tiles * sizeof(double2));
+    L.total = L.results + Arena::round((size_t)B * sizeof(double2));
+    return L;
+}
+
+// Pinned staging bytes per slot: descriptors of the largest packed launch, and its results.
+size_t mid_stage_bytes() {
+    const MidLayout L = mid_layout(kMidMaxP + 1, kMidMaxB, 1);
+    return L.upload + Arena::round((size_t)kMidMaxB * sizeof(double2));
+}
+
 struct Running {  // a request dispatched alone
     SReq r;
     size_t off = 0, bytes = 0;
@@ -149,6 +180,10 @@ struct Running {  // a request dispatched alone
 struct RunningBatch {
     std::vector<SReq> reqs;
     std::vector<size_t> offs;
+    std::vector<size_t> bytes;   // per request (mid-size packs; small packs use small_bytes)
+    std::vector<int> slots;      // per request pinned result slots held (mid-size packs)
+    bool mid = false;            // packed mid-size states (else small states, one CTA each)
+    size_t res_off = 0;          // mid-size packs: offset of the results in the staging slot
     size_t head_off = 0, head_bytes = 0;
     int stream = 0, staging = -1;
     cudaEvent_t ev = nullptr;
@@ -176,6 +211,9 @@ struct qaoa_server_s {
     unsigned char* pin_stage = nullptr;
     size_t stage_bytes = 0;
     std::vector<int> free_stage;
+    // pinned staging for packed mid-size launches (kMidStages slots of mid_stage_bytes())
+    unsigned char* pin_mid = nullptr;
+    std::vector<int> free_mid;
     std::vector<cudaEvent_t> event_pool;
     std::map<std::tuple<int, int, int, int>, GraphPool> graphs;  // (kind, n, p, m) -> executables
     // host-side bookkeeping
@@ -280,22 +318,16 @@ void release_graph(qaoa_server_s* sv, cudaGraphExec_t exec) {
             if (e.first == exec) e.second = false;
 }
 
-template <typename real>
-qaoa_status dispatch_single(qaoa_server_s* sv, SReq&& r, size_t off, const Layout& L, int slot) {
-    Running run;
-    run.off = off;
-    run.bytes = L.total;
-    run.slot = slot;
-    run.stream = pick_stream(sv);
-    char* base = sv->arena.base + off;
-    qaoa_state_s* st = new (std::nothrow) qaoa_state_s;
-    if (!st) return fail(QAOA_ERR_OOM, "host allocation failed");
+// A state handle over a request's block of the arena (the library's own per-state workspace
+// pointers aimed into the block; nothing allocated).
+void bind_request_state(qaoa_server_s* sv, qaoa_state_s* st, const SReq& r, char* base, const Layout& L,
+                        cudaStream_t stream) {
     st->dev = sv->dev;
     st->n = r.g.n;
     st->prec = sv->cfg.prec;
     st->dim = 1ull << r.g.n;
     st->buf = base + L.state;
-    st->stream = sv->streams[run.stream];
+    st->stream = stream;
     st->g = r.g;
     st->tc = tile_config_for(sv->cfg.prec);
     st->small = is_small(r.g.n, sv->cfg.prec);
@@ -308,6 +340,31 @@ qaoa_status dispatch_single(qaoa_server_s* sv, SReq&& r, size_t off, const Layou
     st->d_partials = reinterpret_cast<double2*>(base + L.partials);
     st->d_result = reinterpret_cast<double2*>(base + L.result);
     if (r.g.weighted) st->d_wfix = base + L.wfix;
+}
+
+// Drops the handle's pointers into the arena (they are not its own) before deleting it.
+void unbind_request_state(qaoa_state_s* st) {
+    st->d_phase = st->d_mix = nullptr;
+    st->d_partials = st->d_result = nullptr;
+    st->d_gtab = st->d_gmix = nullptr;
+    st->d_gacc = nullptr;
+    st->d_gpart = nullptr;
+    st->d_gpow = nullptr;
+    st->d_wfix = st->d_gwfix = nullptr;
+    delete st;
+}
+
+template <typename real>
+qaoa_status dispatch_single(qaoa_server_s* sv, SReq&& r, size_t off, const Layout& L, int slot) {
+    Running run;
+    run.off = off;
+    run.bytes = L.total;
+    run.slot = slot;
+    run.stream = pick_stream(sv);
+    char* base = sv->arena.base + off;
+    qaoa_state_s* st = new (std::nothrow) qaoa_state_s;
+    if (!st) return fail(QAOA_ERR_OOM, "host allocation failed");
+    bind_request_state(sv, st, r, base, L, sv->streams[run.stream]);
     if (r.grad) {
         st->grad_levels = r.p;
         st->d_gtab = base + L.gtab;
@@ -340,14 +397,7 @@ qaoa_status dispatch_single(qaoa_server_s* sv, SReq&& r, size_t off, const Layou
     if (s != QAOA_OK) {
         release_graph(sv, run.exec);
         if (run.ev) sv->event_pool.push_back(run.ev);
-        st->d_phase = st->d_mix = nullptr;
-        st->d_partials = st->d_result = nullptr;
-        st->d_gtab = st->d_gmix = nullptr;
-        st->d_gacc = nullptr;
-        st->d_gpart = nullptr;
-        st->d_gpow = nullptr;
-        st->d_wfix = st->d_gwfix = nullptr;
-        delete st;
+        unbind_request_state(st);
         return s;
     }
     sv->stream_load[run.stream]++;
@@ -442,6 +492,119 @@ qaoa_status dispatch_batch(qaoa_server_s* sv, std::vector<SReq>&& reqs, std::vec
     return QAOA_OK;
 }
 
+// Whether a request runs in a packed mid-size launch: a complex64 forward request with unit
+// weights whose state is tiled in two mixer groups (14 < n <= kMidMaxN) and p <= kMidMaxP.
+bool serve_mid(const qaoa_server_s* sv, const SReq& r) {
+    return sv->cfg.prec == QAOA_C64 && !r.grad && !r.g.weighted && !is_small(r.g.n, sv->cfg.prec) &&
+           r.g.n <= kMidMaxN && r.p <= kMidMaxP;
+}
+
+// Packed launch of mid-size forward requests of one (n, p): every request keeps its own arena
+// block (single_layout: state, phase tables, mixer entries), its pass arguments are the ones a
+// lone run builds (fill_program_with, chunk_coeff_args) and its passes run the same compiled
+// programs (pick_tile_batch_kernel), so each result equals the request run alone bit for bit.
+// One upload of all descriptors, one coefficient launch, one launch per pass over the tiles of
+// every request, one reduction launch, one download of the B results.  Returns
+// QAOA_ERR_UNSUPPORTED (nothing enqueued) when a pass program has no packed kernel.
+template <typename real>
+qaoa_status dispatch_mid_batch(qaoa_server_s* sv, std::vector<SReq>& reqs, const std::vector<size_t>& offs,
+                               const std::vector<size_t>& bytes, const std::vector<int>& slots, int staging) {
+    constexpr int Q = PrecTraits<real>::Q, R = PrecTraits<real>::R;
+    using C2 = typename C2T<real>::type;
+    const int B = (int)reqs.size();
+    const int n = reqs[0].g.n, p = reqs[0].p;
+    const TileConfig tc = tile_config_for(sv->cfg.prec);
+    const uint64_t tiles = 1ull << (n - Q);
+    Plan plan;
+    try {
+        plan = plan_levels(n, tc, p, true, true);
+    } catch (const std::exception& ex) {
+        return fail(QAOA_ERR_UNSUPPORTED, ex.what());
+    }
+    const int passes = (int)plan.passes.size();
+    if (passes > kMidMaxP + 1 || B > kMidMaxB) return fail(QAOA_ERR_UNSUPPORTED, "packed launch too large");
+    const MidLayout ML = mid_layout(passes, B, tiles);
+    unsigned char* stage = sv->pin_mid + (size_t)staging * mid_stage_bytes();
+    TileArgs<Q>* targs = reinterpret_cast<TileArgs<Q>*>(stage + ML.targs);
+    CoeffArgs* cargs = reinterpret_cast<CoeffArgs*>(stage + ML.cargs);
+    double2* res_host = reinterpret_cast<double2*>(stage + ML.upload);
+    RunningBatch rb;
+    rb.stream = pick_stream(sv);
+    cudaStream_t stream = sv->streams[rb.stream];
+    unsigned gx = 1;
+    for (int b = 0; b < B; ++b) {
+        const SReq& r = reqs[b];
+        const Layout L = single_layout(r.g, p, sv->cfg.prec, false, tiles);
+        qaoa_state_s st;
+        bind_request_state(sv, &st, r, sv->arena.base + offs[b], L, stream);
+        for (int i = 0; i < passes; ++i) {
+            TileArgs<Q>& a = targs[(size_t)i * B + b];
+            std::memset(&a, 0, sizeof(a));
+            fill_program_with(a, &st, plan.passes[i], st.groups, st.tc);
+        }
+        chunk_coeff_args(&st, p, r.gamma.data(), r.beta.data(), cargs[b]);
+        gx = std::max(gx, coeff_grid(cargs[b]).x);
+    }
+    std::vector<TileBatchFn<real>> kfn(passes);
+    for (int i = 0; i < passes; ++i) {
+        kfn[i] = pick_tile_batch_kernel<real>(targs[(size_t)i * B]);
+        if (!kfn[i]) return fail(QAOA_ERR_UNSUPPORTED, "no packed kernel for a pass program");
+    }
+    size_t head_off = 0;
+    if (!sv->arena.alloc(ML.total, head_off)) return fail(QAOA_ERR_AGAIN, "no arena room for a packed launch");
+    char* head = sv->arena.base + head_off;
+    // the pass arguments name the head block's partials only now that it has an address
+    for (int b = 0; b < B; ++b)
+        for (int i = 0; i < passes; ++i)
+            targs[(size_t)i * B + b].partials = reinterpret_cast<double2*>(head + ML.partials) + (size_t)b * tiles;
+    const TileArgs<Q>* d_targs = reinterpret_cast<const TileArgs<Q>*>(head + ML.targs);
+    double2* d_partials = reinterpret_cast<double2*>(head + ML.partials);
+    double2* d_results = reinterpret_cast<double2*>(head + ML.results);
+    const size_t smem = (size_t)(1u << Q) * sizeof(C2);
+    auto enqueue = [&]() -> qaoa_status {
+        CUDA_TRY(cudaMemcpyAsync(head, stage, ML.upload, cudaMemcpyHostToDevice, stream));
+        coeff_batch_args_kernel<real><<<dim3(gx, (unsigned)p, (unsigned)B), 256, 0, stream>>>(
+            reinterpret_cast<const CoeffArgs*>(head + ML.cargs));
+        CUDA_TRY(cudaGetLastError());
+        for (int i = 0; i < passes; ++i) {
+            kfn[i]<<<dim3((unsigned)tiles, (unsigned)B), 1u << (Q - R), smem, stream>>>(d_targs + (size_t)i * B);
+            CUDA_TRY(cudaGetLastError());
+        }
+        finalize_batch_kernel<<<(unsigned)B, 1024, 0, stream>>>(d_partials, tiles, d_results);
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(cudaMemcpyAsync(res_host, d_results, (size_t)B * sizeof(double2), cudaMemcpyDeviceToHost, stream));
+        return QAOA_OK;
+    };
+    qaoa_status s = run_maybe_graph(sv, std::make_tuple(3, n, p, B), stream, enqueue, &rb.exec);
+    if (s == QAOA_OK) {
+        rb.ev = take_event(sv);
+        if (!rb.ev) s = fail(QAOA_ERR_CUDA, "cudaEventCreate failed");
+        else if (cudaEventRecord(rb.ev, stream) != cudaSuccess) s = cuda_fail(cudaGetLastError(), "cudaEventRecord");
+    }
+    if (s != QAOA_OK) {
+        release_graph(sv, rb.exec);
+        sv->arena.release(head_off, ML.total);
+        return s;
+    }
+    sv->stream_load[rb.stream]++;
+    rb.mid = true;
+    rb.res_off = ML.upload;
+    rb.reqs = std::move(reqs);
+    rb.offs = offs;
+    rb.bytes = bytes;
+    rb.slots = slots;
+    rb.head_off = head_off;
+    rb.head_bytes = ML.total;
+    rb.staging = staging;
+    rb.t_start = sv->now();
+    bump(sv, &qaoa_server_stats::batches);
+    bump(sv, &qaoa_server_stats::batched_requests, B);
+    bump(sv, &qaoa_server_stats::tiled_batches);
+    bump(sv, &qaoa_server_stats::tiled_batched_requests, B);
+    sv->batches.push_back(std::move(rb));
+    return QAOA_OK;
+}
+
 void finish(qaoa_server_s* sv, const SReq& r, qaoa_result res) {
     std::lock_guard<std::mutex> lock(sv->mu);
     sv->done[r.ticket] = res;
@@ -493,15 +656,7 @@ bool scheduler_turn(qaoa_server_s* sv) {
         sv->stream_load[run.stream]--;
         sv->free_single.push_back(run.slot);
         sv->arena.release(run.off, run.bytes);
-        qaoa_state_s* st = run.st;
-        st->d_phase = st->d_mix = nullptr;
-        st->d_partials = st->d_result = nullptr;
-        st->d_gtab = st->d_gmix = nullptr;
-        st->d_gacc = nullptr;
-        st->d_gpart = nullptr;
-        st->d_gpow = nullptr;
-        st->d_wfix = st->d_gwfix = nullptr;
-        delete st;
+        unbind_request_state(run.st);
         sv->inflight--;
         sv->running[i] = std::move(sv->running.back());
         sv->running.pop_back();
@@ -517,6 +672,8 @@ bool scheduler_turn(qaoa_server_s* sv) {
         const double t = sv->now();
         const double2* res_host = reinterpret_cast<const double2*>(sv->pin_stage + (size_t)rb.staging * sv->stage_bytes +
                                                                    batch_layout(sv->cfg.max_batch).results);
+        if (rb.mid)
+            res_host = reinterpret_cast<const double2*>(sv->pin_mid + (size_t)rb.staging * mid_stage_bytes() + rb.res_off);
         for (size_t b = 0; b < rb.reqs.size(); ++b) {
             qaoa_result res = base_result(rb.reqs[b], rb.t_start, t);
             res.batched = 1;
@@ -527,13 +684,14 @@ bool scheduler_turn(qaoa_server_s* sv) {
                 res.norm = res_host[b].y;
             }
             finish(sv, rb.reqs[b], res);
-            sv->arena.release(rb.offs[b], small_bytes(rb.reqs[b].g.m, rb.reqs[b].p, sv->cfg.prec));
+            sv->arena.release(rb.offs[b], rb.mid ? rb.bytes[b] : small_bytes(rb.reqs[b].g.m, rb.reqs[b].p, sv->cfg.prec));
             sv->inflight--;
         }
+        for (int slot : rb.slots) sv->free_single.push_back(slot);
         release_graph(sv, rb.exec);
         sv->event_pool.push_back(rb.ev);
         sv->stream_load[rb.stream]--;
-        sv->free_stage.push_back(rb.staging);
+        (rb.mid ? sv->free_mid : sv->free_stage).push_back(rb.staging);
         sv->arena.release(rb.head_off, rb.head_bytes);
         sv->batches[i] = std::move(sv->batches.back());
         sv->batches.pop_back();
@@ -561,9 +719,35 @@ bool scheduler_turn(qaoa_server_s* sv) {
     size_t head_off = 0;
     bool have_head = false;
     const size_t head_bytes = batch_layout(sv->cfg.max_batch).total;
+    struct MidGroup {
+        std::vector<SReq> reqs;
+        std::vector<size_t> offs, bytes;
+        std::vector<int> slots;
+    };
+    std::vector<MidGroup> mids;  // admitted mid-size requests, grouped by (n, p)
+    const int mid_cap = std::min(sv->cfg.max_batch, kMidMaxB);
     while (!sv->pending.empty() && sv->inflight < sv->cfg.max_inflight) {
         SReq& r = sv->pending.front();
-        if (serve_small(sv, r)) {
+        if (serve_mid(sv, r)) {
+            if (sv->free_single.empty()) break;
+            const Layout L = single_layout(r.g, r.p, sv->cfg.prec, false, 1ull << (r.g.n - tile_config_for(sv->cfg.prec).Q));
+            size_t off = 0;
+            if (!sv->arena.alloc(L.total, off)) break;
+            MidGroup* grp = nullptr;
+            for (MidGroup& m : mids)
+                if (m.reqs[0].g.n == r.g.n && m.reqs[0].p == r.p && (int)m.reqs.size() < mid_cap) grp = &m;
+            if (!grp) {
+                mids.emplace_back();
+                grp = &mids.back();
+            }
+            grp->slots.push_back(sv->free_single.back());
+            sv->free_single.pop_back();
+            grp->offs.push_back(off);
+            grp->bytes.push_back(L.total);
+            grp->reqs.push_back(std::move(r));
+            sv->pending.pop_front();
+            sv->inflight++;
+        } else if (serve_small(sv, r)) {
             if ((int)small.size() >= sv->cfg.max_batch) break;
             if (!have_head) {
                 if (sv->free_stage.empty() || !sv->arena.alloc(head_bytes, head_off)) break;
@@ -607,17 +791,59 @@ bool scheduler_turn(qaoa_server_s* sv) {
         const qaoa_status s = dispatch_batch<real>(sv, std::move(small), std::move(small_offs), staging, head_off);
         if (s != QAOA_OK) {
             const double t = sv->now();
-            for (const SReq& r : keep) {
-                qaoa_result res = base_result(r, t, t);
+            for (size_t b = 0; b < keep.size(); ++b) {
+                qaoa_result res = base_result(keep[b], t, t);
                 res.status = s;
-                finish(sv, r, res);
+                finish(sv, keep[b], res);
+                sv->arena.release(small_offs[b], small_bytes(keep[b].g.m, keep[b].p, sv->cfg.prec));
                 sv->inflight--;
             }
+            sv->arena.release(head_off, head_bytes);
             sv->free_stage.push_back(staging);
         }
         progress = true;
     } else if (have_head) {
         sv->arena.release(head_off, head_bytes);
+    }
+    // mid-size groups: packed when two or more share (n, p) and a staging slot and arena room for
+    // the head are free, else each request runs alone in the block it was admitted with
+    for (MidGroup& m : mids) {
+        if (m.reqs.size() >= 2 && !sv->free_mid.empty()) {
+            const int staging = sv->free_mid.back();
+            sv->free_mid.pop_back();
+            std::vector<SReq> keep = m.reqs;
+            const qaoa_status s = dispatch_mid_batch<real>(sv, m.reqs, m.offs, m.bytes, m.slots, staging);
+            if (s == QAOA_OK) continue;
+            sv->free_mid.push_back(staging);
+            m.reqs = std::move(keep);
+            if (s != QAOA_ERR_AGAIN && s != QAOA_ERR_UNSUPPORTED) {  // a CUDA failure: report it
+                const double t = sv->now();
+                for (size_t b = 0; b < m.reqs.size(); ++b) {
+                    qaoa_result res = base_result(m.reqs[b], t, t);
+                    res.status = s;
+                    finish(sv, m.reqs[b], res);
+                    sv->arena.release(m.offs[b], m.bytes[b]);
+                    sv->free_single.push_back(m.slots[b]);
+                    sv->inflight--;
+                }
+                continue;
+            }
+        }
+        for (size_t b = 0; b < m.reqs.size(); ++b) {
+            const SReq& r0 = m.reqs[b];
+            const Layout L = single_layout(r0.g, r0.p, sv->cfg.prec, false, 1ull << (r0.g.n - tile_config_for(sv->cfg.prec).Q));
+            SReq req = std::move(m.reqs[b]);
+            const double t = sv->now();
+            const qaoa_status s = dispatch_single<real>(sv, std::move(req), m.offs[b], L, m.slots[b]);
+            if (s != QAOA_OK) {
+                qaoa_result res = base_result(req, t, t);
+                res.status = s;
+                sv->arena.release(m.offs[b], L.total);
+                sv->free_single.push_back(m.slots[b]);
+                sv->inflight--;
+                finish(sv, req, res);
+            }
+        }
     }
     return progress;
 }
@@ -657,6 +883,7 @@ void server_free(qaoa_server_s* sv) {
     if (sv->arena.base) cudaFree(sv->arena.base);
     if (sv->pin_single) cudaFreeHost(sv->pin_single);
     if (sv->pin_stage) cudaFreeHost(sv->pin_stage);
+    if (sv->pin_mid) cudaFreeHost(sv->pin_mid);
     delete sv;
 }
 
@@ -689,6 +916,7 @@ qaoa_status qaoa_server_create(const qaoa_server_config* cfg, qaoa_server* out) 
     const int stages = std::max(2, std::min(16, cfg->streams * 2));
     e = cudaMallocHost(&sv->pin_single, (size_t)slots * (2 + 2 * QAOA_SERVE_MAX_P) * sizeof(double));
     if (e == cudaSuccess) e = cudaMallocHost(&sv->pin_stage, (size_t)stages * sv->stage_bytes);
+    if (e == cudaSuccess && cfg->prec == QAOA_C64) e = cudaMallocHost(&sv->pin_mid, (size_t)kMidStages * mid_stage_bytes());
     for (int i = 0; i < cfg->streams && e == cudaSuccess; ++i) {
         cudaStream_t s = nullptr;
         e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
@@ -702,6 +930,7 @@ qaoa_status qaoa_server_create(const qaoa_server_config* cfg, qaoa_server* out) 
     }
     for (int i = slots - 1; i >= 0; --i) sv->free_single.push_back(i);
     for (int i = stages - 1; i >= 0; --i) sv->free_stage.push_back(i);
+    for (int i = kMidStages - 1; sv->pin_mid && i >= 0; --i) sv->free_mid.push_back(i);
     // kernel attributes are set here, outside any stream capture
     const qaoa_status st = cfg->prec == QAOA_C64 ? prepare_kernels<float>() : prepare_kernels<double>();
     if (st != QAOA_OK) {

@@ -93,6 +93,9 @@ try:
     for i, n in enumerate((8, 11, 14, 18, 22, 9, 16)):
         gamma, beta = I.angles(2, 40 + i)
         tickets.append(B.qaoa_submit(sv, graph(n), gamma, beta, want_grad=(i % 2 == 1)))
+    for i, n in enumerate((15, 15, 15, 20, 20, 22, 22)):  # packed mid-size launches
+        gamma, beta = I.angles(3, 80 + i)
+        tickets.append(B.qaoa_submit(sv, I.gnp(n, 0.3, 80 + i), gamma, beta))
     while tickets:
         tickets = [t for t in tickets if B.qaoa_poll(sv, t) is None]
 finally:

@@ -106,6 +106,7 @@ def test_results_identical_alone_and_in_the_mix(B, graphs):
     B.qaoa_server_destroy(sv)
     assert stats["completed"] == len(reqs) and stats["failed"] == 0
     assert stats["batches"] >= 1 and stats["batched_requests"] >= 1
+    assert stats["tiled_batches"] >= 1 and stats["tiled_batched_requests"] >= 2
     if graphs:
         assert stats["graph_launches"] >= 1
     packed = streamed = 0
@@ -120,6 +121,44 @@ def test_results_identical_alone_and_in_the_mix(B, graphs):
         packed += r["batched"]
         streamed += g.n >= 15
     assert packed >= 1 and streamed >= 10
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+def test_packed_mid_size_requests(B, graphs):
+    """Mid-size complex64 forward requests (tiled states, 15 <= n <= 22, p <= 8) of one (n, p)
+    run in packed launches, one launch per pass over the tiles of every request: 40 requests of
+    four shapes, different graphs; each result equals the request run alone bit for bit and the
+    oracle's <C> within 1e-5 |E|.  A request with p = 9 and a gradient request of the same size
+    run alone."""
+    reqs = []
+    for i in range(40):
+        n, p = ((15, 3), (18, 2), (20, 4), (22, 1))[i % 4]
+        g = I.regular3(n, 500 + i) if (n % 2 == 0 and i % 3) else I.gnp(n, 0.3, 500 + i)
+        ga, be = I.angles(p, seed=700 + i, beta_hi=np.pi)
+        reqs.append((g, ga, be, False))
+    g9 = I.gnp(18, 0.3, 9)
+    reqs.append((g9, *I.angles(9, seed=9), False))
+    reqs.append((I.regular3(18, 10), *I.angles(2, seed=10), True))
+    sv = B.qaoa_server_create(8 << 30, "c64", max_inflight=64, max_batch=64, streams=4, use_graphs=graphs)
+    try:
+        tickets = [B.qaoa_submit(sv, g, ga, be, grad) for g, ga, be, grad in reqs]
+        res = wait_all(B, sv, tickets)
+        stats = B.qaoa_server_stats_read(sv)
+    finally:
+        B.qaoa_server_destroy(sv)
+    assert stats["failed"] == 0 and stats["completed"] == len(reqs)
+    packed = 0
+    for (g, ga, be, grad), t in zip(reqs, tickets):
+        r = res[t]
+        assert r["status"] == 0
+        c, dg, db = alone(B, g, ga, be, grad)
+        assert r["expectation"] == c, (g.name, r["expectation"], c)
+        check_against_oracle(r, g, ga, be, grad, "c64")
+        packed += r["batched"]
+    assert not res[tickets[-2]]["batched"] and not res[tickets[-1]]["batched"]
+    # the scheduler starts while requests are still being submitted, so not all of them find a
+    # partner of the same shape in the same turn
+    assert packed == stats["tiled_batched_requests"] >= 8, stats
 
 
 def test_c128_mix_against_the_oracle(B):
