@@ -425,8 +425,8 @@ int pick_recipe(const TileArgs<PrecTraits<real>::Q>& a, bool weighted_graph) {
         code |= recipe_step_lo(i, a.ops[i].kind, a.ops[i].layout);
         hi |= recipe_step_hi(i, a.ops[i].kind, a.ops[i].layout);
     }
-    // the full-mask fused pass (6) spills: not used
-    const int order[] = {1, 5, 7, 0, 2, 3, 4, 8, 9, 10, 11, 12};
+    // full-mask instantiations first (5, 6, 7), then the runtime-mask ones
+    const int order[] = {1, 5, 6, 7, 0, 2, 3, 4, 8, 9, 10, 11, 12};
     for (int r : order) {
         const Recipe d = recipe_def(r);
         if (d.nops != a.nops || d.code != code || d.hi != hi) continue;
