@@ -217,7 +217,7 @@ void fill_geometry(TileArgs<Q>& a, const HostGraph& hg, const Geometry& geo, con
                 for (int j = 0; j < tc.R; ++j)
                     for (int m = j + 1; m < tc.R; ++m)
                         if ((a.locAdj[rl + j] >> (rl + m)) & 1u) c += ((x >> j) ^ (x >> m)) & 1;
-            a.crtab[L][x] = (uint8_t)c;
+            a.crtab[L][x] = c;
         }
     }
 }
@@ -545,15 +545,16 @@ qaoa_status ensure_attributes() {
         if (TileBatchFn<real> f = batch_kernel_for<real>(r))
             CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)((1u << Q) * sizeof(C2))));
     constexpr int GQ = GradTraits<real>::Q, GR = GradTraits<real>::R;
+    // the adjoint passes exchange psi and lambda through a tile each
     CUDA_TRY(cudaFuncSetAttribute(grad_kernel<real, GQ, GR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)((1u << GQ) * sizeof(C2))));
+                                  (int)(2 * (1u << GQ) * sizeof(C2))));
     CUDA_TRY(cudaFuncSetAttribute(grad_kernel<real, GQ, GR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)((1u << GQ) * sizeof(C2))));
+                                  (int)(2 * (1u << GQ) * sizeof(C2))));
     if constexpr (std::is_same<real, float>::value)
         for (int r = 0; r < kGradRecipes; ++r)
             for (bool w : {false, true})
                 CUDA_TRY(cudaFuncSetAttribute(grad_recipe_kernel<real>(r, w), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)((1u << GQ) * sizeof(C2))));
+                                              (int)(2 * (1u << GQ) * sizeof(C2))));
     CUDA_TRY(cudaFuncSetAttribute(small_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024));
     CUDA_TRY(cudaFuncSetAttribute(small_batch_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024));
     CUDA_TRY(cudaFuncSetAttribute(small_grad_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1201,7 +1202,7 @@ qaoa_status gradient_async(qaoa_state s, int p, const double* gamma, const doubl
         }
         annotate_sweep(plan, p);
         const uint64_t gt = grad_tiles(s->n);
-        const size_t smem = (size_t)(1u << Q) * sizeof(C2);
+        const size_t smem = (size_t)2 * (1u << Q) * sizeof(C2);  // psi's and lambda's exchange tiles
         qaoa_status ast = ensure_attributes<real>();
         if (ast != QAOA_OK) return ast;
         TileArgs<Q> a;

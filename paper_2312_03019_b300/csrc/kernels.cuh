@@ -98,7 +98,9 @@ struct TileArgs {
     uint32_t locUpper[Q];   // tile-internal upper neighbours of local bit u (local bit order)
     uint32_t locAdj[Q];     // all tile-internal neighbours of local bit u
     uint64_t outAdj[Q];     // neighbours of local bit u outside the tile (global positions)
-    uint8_t crtab[3][32];   // C_R(x) per register layout
+    int32_t crtab[3][32];   // C_R(x) per register layout (32-bit words: each is an operand of
+                            // the cut-index add as it is, 28.9 against 29.3 ms per fused pass
+                            // at n = 33 with bytes)
     // edge-weighted graphs (pass kernels instantiated with kW)
     const void* wfix;              // rows of m fixed-point words: [0] endpoints u | v << 8,
                                    // [1] value weights, [2 + k] angles of level k
@@ -1154,7 +1156,7 @@ __host__ __device__ constexpr int recipe_cut_setup(uint64_t lo, uint64_t hi, int
     for (int i = 0; i < nops; ++i) {
         const int k = recipe_kind2(lo, hi, i);
         if (k == OP_XCHG) xchg = true;
-        if (k == OP_PHASE || k == OP_EXPECT || k == OP_CUTVAL) {
+        if (k == OP_PHASE || k == OP_EXPECT || k == OP_CUTVAL || k == OP_LAMBDA || k == OP_GRADG || k == OP_PHASED) {
             if (!xchg) return 2;
             cut = true;
         }
@@ -1271,14 +1273,14 @@ __host__ __device__ constexpr bool recipe_scalar_fma(uint64_t recipe, int nops) 
 
 // Resident CTAs per SM a pass kernel's register budget is sized for.  Two (128 registers a
 // thread) by default; three (85) for the complex64 recipes that measured faster with 24 warps
-// per SM despite a few spilled registers (first, group-0 and last pass; the fused boundary pass,
-// with two RX sets and the phase live at once, is faster at two).
+// per SM (the first pass and the group-0 pass; at n = 33 the last pass takes 27.1 ms at two
+// CTAs against 30.7 ms at three, the first pass 21.5 ms at two against 17.0 ms at three).
 template <typename real, bool kW = false>
 __host__ __device__ constexpr int tile_min_blocks(uint64_t recipe, int nops) {
     if (kW) return QAOA_TILE_MIN_BLOCKS;  // the weighted split needs more registers
-    // (the first-pass, group-0 and last-pass programs, with runtime or compiled-in masks)
+    // (the first-pass and group-0 programs, with runtime or compiled-in masks)
     if (sizeof(real) == 4 && nops > 0)
-        for (int r : {0, 1, 3})
+        for (int r : {0, 1})
             if (recipe == base_recipe(r).code && nops == base_recipe(r).nops) return 3;
     return QAOA_TILE_MIN_BLOCKS;
 }
@@ -1540,34 +1542,48 @@ __global__ void __launch_bounds__(1 << (Q - R), sizeof(real) == 4 ? 2 : 1) grad_
     using C2 = typename T::C2;
     using WA = typename T::WA;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int sE[Q];
-    __shared__ int sK;
+    // the CTA's cut terms, placed as in tile_body (kSetup: see recipe_cut_setup)
+    constexpr int kSetup = (!kW && kNops > 0) ? recipe_cut_setup(kRecipe, 0, kNops) : -1;
+    constexpr int kCopies = kSetup == 2 ? T::NT / 32 : 1;
+    __shared__ int sE_all[kCopies][Q];
+    __shared__ int sK_all[kCopies];
 
     __shared__ WA sKw[kW ? kWSlots : 1];
     __shared__ WA sEw[kW ? kWSlots : 1][Q];
 
+    // psi and lambda exchange through one tile each
     unsigned char* tile = smem_raw;
+    unsigned char* tile2 = smem_raw + (1u << Q) * sizeof(C2);
     const uint32_t tid = threadIdx.x;
     const uint64_t t = blockIdx.x;
     uint64_t zb = 0;
     for (int r = 0; r < a.nruns; ++r) zb |= ((t >> a.run_src[r]) & ((1ull << a.run_len[r]) - 1ull)) << a.run_dst[r];
-    if constexpr (kW) {
-        weighted_cta_setup<WA, Q>(a, zb, sKw, sEw, tid, T::NT);
-        if (tid == 0) sK = 0;
-    } else if (tid < 32) {
+    const uint32_t wcopy = kSetup == 2 ? tid / 32 : 0;
+    int* const sE = sE_all[wcopy];
+    auto cut_terms = [&]() {
+        const uint32_t lane = tid & 31u;
         int acc = 0;
-        for (int v = (int)tid; v < a.n; v += 32) {
+        for (int v = (int)lane; v < a.n; v += 32) {
             const uint64_t bI = 0ull - ((zb >> v) & 1ull);
             acc += __popcll(a.gmask[v] & (bI ^ zb));
         }
         acc = warp_sum_int(acc);
-        if (tid == 0) sK = acc;
-        if (tid < (uint32_t)Q) sE[tid] = __popcll(a.outAdj[tid]) - 2 * __popcll(a.outAdj[tid] & zb);
+        if (lane == 0) sK_all[wcopy] = acc;
+        if (lane < (uint32_t)Q) sE[lane] = __popcll(a.outAdj[lane]) - 2 * __popcll(a.outAdj[lane] & zb);
+    };
+    if constexpr (kW) {
+        weighted_cta_setup<WA, Q>(a, zb, sKw, sEw, tid, T::NT);
+        __syncthreads();
+    } else if constexpr (kSetup == 2) {
+        cut_terms();
+        __syncwarp();
+    } else if constexpr (kSetup < 0) {
+        if (tid < 32) cut_terms();
+        __syncthreads();
     }
-    __syncthreads();
     typename T::Ctx c;
     c.zb = zb;
-    c.K = kW ? 0 : sK;
+    c.K = (!kW && (kSetup == 2 || kSetup < 0)) ? sK_all[wcopy] : 0;
     c.a = &a;
     c.sE = sE;
     c.wK = sKw;
@@ -1618,30 +1634,35 @@ __global__ void __launch_bounds__(1 << (Q - R), sizeof(real) == 4 ? 2 : 1) grad_
                 T::template load_from<Lc>(v, c, tid, a.state);
                 T::template load_from<Lc>(w, c, tid, a.state2);
             } else if constexpr (kind == OP_XCHG) {
-                // psi first, at the positions this thread read lambda from last (see to_smem)
+                // one barrier: a thread writes exactly the positions it read in the previous
+                // exchange (see to_smem)
                 T::template to_smem<Lp>(v, tile, tid, a.bounds_flag);
+                T::template to_smem<Lp>(w, tile2, tid, a.bounds_flag);
                 __syncthreads();
                 T::template from_smem<Lc>(v, tile, tid, a.bounds_flag);
-                __syncthreads();
-                T::template to_smem<Lp>(w, tile, tid, a.bounds_flag);
-                __syncthreads();
-                T::template from_smem<Lc>(w, tile, tid, a.bounds_flag);
+                T::template from_smem<Lc>(w, tile2, tid, a.bounds_flag);
             } else if constexpr (kind == OP_RXD) {
                 const Op op = a.ops[i];
                 const double d = rxd_op(op, v, w);
                 if (sweep_slot(op.arg)) acc[2] += d;
                 else acc[0] += d;
             } else if constexpr (kind == OP_GRADG) {
+                if constexpr (kSetup == 1) c.K = sK_all[0];
                 const double d = gradg_op(std::integral_constant<int, Lc>{}, a.ops[i], v, w);
                 if (sweep_slot(a.ops[i].arg)) acc[3] += d;
                 else acc[1] += d;
             } else if constexpr (kind == OP_PHASED) {
+                if constexpr (kSetup == 1) c.K = sK_all[0];
                 if constexpr (kPG) T::template phase_dual_parity<Lc, kW>(v, w, c, tid, a.ops[i].arg);
                 else T::template phase_dual<Lc, kW>(v, w, c, tid, a.ops[i].arg);
             } else if constexpr (kind == OP_STORE) {
                 T::template store_to<Lc>(v, c, tid, a.state);
                 T::template store_to<Lc>(w, c, tid, a.state2);
             }
+            // after the loads, warp 0 computes the cut terms; the next exchange's barrier
+            // publishes them (as in tile_body, the branch also ends the load block)
+            if constexpr ((kSetup == 1 || kSetup == 0) && i == 0)
+                if (a.need_cut && tid < 32) cut_terms();
         });
     }
     for (int i = 0; kNops == 0 && i < a.nops; ++i) {
@@ -1657,20 +1678,14 @@ __global__ void __launch_bounds__(1 << (Q - R), sizeof(real) == 4 ? 2 : 1) grad_
                 else if (L == 1) T::template lambda_init<1, kW>(v, w, c, tid);
                 else T::template lambda_init<2, kW>(v, w, c, tid);
                 break;
-            case OP_XCHG: {
-                const int Lold = L;
+            case OP_XCHG:
                 QAOA_BY_LAYOUT(to_smem, v, tile, tid, a.bounds_flag);
+                QAOA_BY_LAYOUT(to_smem, w, tile2, tid, a.bounds_flag);
                 __syncthreads();
                 L = op.layout;
                 QAOA_BY_LAYOUT(from_smem, v, tile, tid, a.bounds_flag);
-                __syncthreads();
-                L = Lold;
-                QAOA_BY_LAYOUT(to_smem, w, tile, tid, a.bounds_flag);
-                __syncthreads();
-                L = op.layout;
-                QAOA_BY_LAYOUT(from_smem, w, tile, tid, a.bounds_flag);
+                QAOA_BY_LAYOUT(from_smem, w, tile2, tid, a.bounds_flag);
                 break;
-            }
             case OP_RXD:
                 acc[2 * sweep_slot(op.arg)] += rxd_op(op, v, w);
                 break;
