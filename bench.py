@@ -42,11 +42,10 @@ UNIT = "layers/s"
 # categories: [0] the mixer-only pass (group 0 at n <= 33), [1] the fused boundary pass with the cost phase,
 # [2] the last pass with <C>), complex64, unit weights, per amplitude, from one ncu capture of
 # the same kernel build at n = 28 (the full-size state is too large for a multi-metric capture),
-# against 16 B per amplitude algorithmic (4.2950 GB per launch at n = 28): 4.2319, 4.2313 and
-# 4.3465 GB.  A pass's last writes are still in L2 when it ends; the last pass of a step also
-# writes back what the passes before it left there.  A pass reads and writes every amplitude
-# once, so the traffic scales with 2^n.
-NCU_TRAFFIC_BY_KIND = (4.2319e9 / 2 ** 28, 4.2313e9 / 2 ** 28, 4.3465e9 / 2 ** 28)
+# against 16 B per amplitude algorithmic (4.2950 GB per launch at n = 28): 4.2362, 4.2352 and
+# 4.2360 GB.  A pass's last writes are still in L2 when it ends.  A pass reads and writes every
+# amplitude once, so the traffic scales with 2^n.
+NCU_TRAFFIC_BY_KIND = (4.2362e9 / 2 ** 28, 4.2352e9 / 2 ** 28, 4.2360e9 / 2 ** 28)
 NOMINAL_HBM_GBS = 7700.0  # B300 HBM3e, nominal (the fractions are also given against it)
 PASS_KINDS = ("tile_kernel, mixer-only pass (read+write; the group-0 pass at n <= 33)",
               "tile_kernel, fused boundary pass with the cost phase (read+write)",

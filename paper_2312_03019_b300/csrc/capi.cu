@@ -487,19 +487,23 @@ TileBatchFn<real> pick_tile_batch_kernel(const TileArgs<PrecTraits<real>::Q>& a)
 template <typename real>
 using GradFn = void (*)(TileArgs<GradTraits<real>::Q>);
 
-// The straight-line adjoint-pass instantiation of sweep program r (complex64).
-template <int r, bool kW>
+// The straight-line adjoint-pass instantiation of sweep program r (complex64) with the RXD masks
+// of variant v compiled in (grad_masks; v = 0: runtime masks).
+template <int r, bool kW, int v = 0>
 constexpr GradFn<float> grad_recipe_fn() {
     return grad_kernel<float, GradTraits<float>::Q, GradTraits<float>::R, kW, grad_recipe(r).code,
-                       grad_recipe(r).nops>;
+                       grad_recipe(r).nops, grad_masks(r, v)>;
+}
+template <bool kW>
+GradFn<float> grad_recipe_fn_for(int r, int v) {
+    if (r == 0) return v == 1 ? grad_recipe_fn<0, kW, 1>() : v == 0 ? grad_recipe_fn<0, kW>() : nullptr;
+    if (r == 1) return v == 1 ? grad_recipe_fn<1, kW, 1>() : v == 2 ? grad_recipe_fn<1, kW, 2>() : grad_recipe_fn<1, kW>();
+    return v == 0 ? grad_recipe_fn<2, kW>() : nullptr;
 }
 template <typename real>
-GradFn<real> grad_recipe_kernel(int r, bool weighted) {
-    if constexpr (std::is_same<real, float>::value) {
-        if (weighted)
-            return r == 0 ? grad_recipe_fn<0, true>() : r == 1 ? grad_recipe_fn<1, true>() : grad_recipe_fn<2, true>();
-        return r == 0 ? grad_recipe_fn<0, false>() : r == 1 ? grad_recipe_fn<1, false>() : grad_recipe_fn<2, false>();
-    }
+GradFn<real> grad_recipe_kernel(int r, bool weighted, int v = 0) {
+    if constexpr (std::is_same<real, float>::value)
+        return weighted ? grad_recipe_fn_for<true>(r, v) : grad_recipe_fn_for<false>(r, v);
     return nullptr;
 }
 
@@ -511,9 +515,21 @@ GradFn<real> pick_grad_kernel(const TileArgs<GradTraits<real>::Q>& a, bool weigh
     if (std::is_same<real, float>::value && a.nops <= 10) {
         uint64_t code = 0;
         for (int i = 0; i < a.nops; ++i) code |= recipe_step(i, a.ops[i].kind, a.ops[i].layout);
-        for (int r = 0; r < kGradRecipes; ++r)
-            if (grad_recipe(r).nops == a.nops && grad_recipe(r).code == code)
-                return grad_recipe_kernel<real>(r, weighted);
+        for (int r = 0; r < kGradRecipes; ++r) {
+            if (grad_recipe(r).nops != a.nops || grad_recipe(r).code != code) continue;
+            // the mask variants whose compiled-in masks are this pass's, then the runtime one
+            for (int v = kGradMaskVariants - 1; v >= 0; --v) {
+                const uint64_t m = grad_masks(r, v);
+                if (v > 0 && m == 0) continue;
+                bool ok = true;
+                for (int i = 0; i < a.nops && i < 10; ++i) {
+                    const uint32_t fm = (uint32_t)((m >> (6 * i)) & 63u);
+                    if ((fm & 32u) && a.ops[i].mask != (fm & 31u)) ok = false;
+                }
+                if (!ok) continue;
+                if (GradFn<real> f = grad_recipe_kernel<real>(r, weighted, v)) return f;
+            }
+        }
     }
     return weighted ? grad_kernel<real, Q, R, true> : grad_kernel<real, Q, R, false>;
 }
@@ -552,9 +568,11 @@ qaoa_status ensure_attributes() {
                                   (int)(2 * (1u << GQ) * sizeof(C2))));
     if constexpr (std::is_same<real, float>::value)
         for (int r = 0; r < kGradRecipes; ++r)
-            for (bool w : {false, true})
-                CUDA_TRY(cudaFuncSetAttribute(grad_recipe_kernel<real>(r, w), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)(2 * (1u << GQ) * sizeof(C2))));
+            for (int v = 0; v < kGradMaskVariants; ++v)
+                for (bool w : {false, true})
+                    if (GradFn<real> f = grad_recipe_kernel<real>(r, w, v))
+                        CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                      (int)(2 * (1u << GQ) * sizeof(C2))));
     CUDA_TRY(cudaFuncSetAttribute(small_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024));
     CUDA_TRY(cudaFuncSetAttribute(small_batch_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024));
     CUDA_TRY(cudaFuncSetAttribute(small_grad_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,

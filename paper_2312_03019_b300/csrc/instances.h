@@ -1,6 +1,6 @@
 // instances.h -- the heavy kernel template instantiations (the pass kernels, their packed forms and
 // the adjoint-sweep kernels), each compiled in a translation unit of its own (tile_c64.cu,
-// tile_c128.cu, batch_c64.cu, grad_kernels.cu, grad_recipes.cu, ...) so that the library builds
+// tile_c128.cu, batch_c64.cu, grad_kernels.cu, grad_recipes.cu, grad_recipes_m.cu, ...) so that the library builds
 // in parallel.  capi.cu includes this file after
 // kernels.cuh with QAOA_INSTANCE = "extern template" (declarations); each instance unit defines
 // QAOA_OWN_* for the set it owns and instantiates that set with QAOA_INSTANCE = "template".
@@ -68,16 +68,25 @@
 
 // complex64 adjoint-sweep passes specialised to the compiled sweep programs (unit and edge weights; the
 // complex128 ones spill at 255 registers and stay on the interpreting instance)
-#define QAOA_GRAD_RECIPE(real, Q, R, r)                                                               \
-    QAOA_INSTANCE __global__ void grad_kernel<real, Q, R, false, grad_recipe(r).code, grad_recipe(r).nops>( \
-        const __grid_constant__ TileArgs<Q>);                                                             \
-    QAOA_INSTANCE __global__ void grad_kernel<real, Q, R, true, grad_recipe(r).code, grad_recipe(r).nops>(  \
-        const __grid_constant__ TileArgs<Q>);
+#define QAOA_GRAD_RECIPE_V(real, Q, R, r, v)                                                             \
+    QAOA_INSTANCE __global__ void grad_kernel<real, Q, R, false, grad_recipe(r).code, grad_recipe(r).nops,     \
+                                              grad_masks(r, v)>(const __grid_constant__ TileArgs<Q>);          \
+    QAOA_INSTANCE __global__ void grad_kernel<real, Q, R, true, grad_recipe(r).code, grad_recipe(r).nops,      \
+                                              grad_masks(r, v)>(const __grid_constant__ TileArgs<Q>);
+#define QAOA_GRAD_RECIPE(real, Q, R, r) QAOA_GRAD_RECIPE_V(real, Q, R, r, 0)
 #define QAOA_GRAD_RECIPE_INSTANCES(real, Q, R)                                                        \
     namespace qaoa {                                                                                   \
     QAOA_GRAD_RECIPE(real, Q, R, 0)                                                                    \
     QAOA_GRAD_RECIPE(real, Q, R, 1)                                                                    \
     QAOA_GRAD_RECIPE(real, Q, R, 2)                                                                    \
+    }
+
+// the sweep programs with compiled-in RXD masks (grad_masks: variants 1 and 2)
+#define QAOA_GRAD_RECIPE_M_INSTANCES(real, Q, R)                                                      \
+    namespace qaoa {                                                                                   \
+    QAOA_GRAD_RECIPE_V(real, Q, R, 0, 1)                                                               \
+    QAOA_GRAD_RECIPE_V(real, Q, R, 1, 1)                                                               \
+    QAOA_GRAD_RECIPE_V(real, Q, R, 1, 2)                                                               \
     }
 
 // packed mid-size requests of the server: the complex64 two-group programs (recipes 8..12) and the
@@ -120,4 +129,7 @@ QAOA_RECIPE_2G_INSTANCES(float, 13, 5)
 #endif
 #if !defined(QAOA_OWN_GRAD_RECIPES)
 QAOA_GRAD_RECIPE_INSTANCES(float, 12, 4)
+#endif
+#if !defined(QAOA_OWN_GRAD_RECIPES_M)
+QAOA_GRAD_RECIPE_M_INSTANCES(float, 12, 4)
 #endif

@@ -853,8 +853,14 @@ struct Tile {
     // the even-parity slot of a pair (the (re, im) form when P = 0) and y the other, the term is
     // (E.x - E.y) - (F.x - F.y) with E = w[x] v[y] and F = w[y] v[x] componentwise; a thread with
     // P = 1 has every form flipped and gets the negative, so the caller also multiplies by sg.
-    template <bool kScalar = false>
+    // kFixed: 0 for a runtime mask, else 32 | the register mask compiled in (no per-bit branches)
+    template <bool kScalar = false, uint32_t kFixed = 0>
     static __device__ __forceinline__ real rxd_parity(C2 (&v)[NE], C2 (&w)[NE], uint32_t mask, real tn) {
+        auto on = [&](auto J) {
+            constexpr int j = decltype(J)::value;
+            if constexpr ((kFixed & 32u) != 0) return ((kFixed >> j) & 1u) != 0;
+            else return ((mask >> j) & 1u) != 0;
+        };
         // d += a * b componentwise, packed (FFMA2) or as two FMAs (bit-identical)
         auto acc2 = [](C2 a, C2 b, C2 d) -> C2 {
             if constexpr (kScalar) return make_c2(fma(a.x, b.x, d.x), fma(a.y, b.y, d.y));
@@ -863,7 +869,7 @@ struct Tile {
         C2 E0 = make_c2((real)0, (real)0), F0 = E0, E1 = E0, F1 = E0;
         for_x<R>([&](auto J) {
             constexpr int j = decltype(J)::value;
-            if (!((mask >> j) & 1u)) return;
+            if (!on(J)) return;
             for_x<NE>([&](auto X) {
                 constexpr int x = decltype(X)::value;
                 if constexpr (!(x & (1 << j))) {
@@ -881,7 +887,7 @@ struct Tile {
         });
         for_x<R>([&](auto J) {
             constexpr int j = decltype(J)::value;
-            if (!((mask >> j) & 1u)) return;
+            if (!on(J)) return;
             const C2 cp = make_c2(tn, -tn), cm = make_c2(-tn, tn);
             for_x<NE>([&](auto X) {
                 constexpr int x = decltype(X)::value;
@@ -1303,6 +1309,24 @@ __host__ __device__ constexpr Recipe grad_recipe(int r) {
                            6};
 }
 constexpr int kGradRecipes = 3;
+// Compiled-in register masks of the sweep programs' RXD ops (6 bits per op, as recipe_masks):
+// variant 1 has every RXD op full (the group-0 pass always; the fused pass of 8-bit high groups),
+// variant 2 is the fused pass of 6-bit high groups, as at n = 24 (layout 1 holds two of the
+// group's bits).  Variant 0: runtime masks.
+constexpr int kGradMaskVariants = 3;
+__host__ __device__ constexpr uint64_t grad_masks(int r, int var) {
+    uint64_t m = 0;
+    if (var == 0 || r == 2 || (r == 0 && var == 2)) return 0;
+    const Recipe d = grad_recipe(r);
+    int k = 0;
+    for (int i = 0; i < d.nops; ++i)
+        if (recipe_kind(d.code, i) == OP_RXD) {
+            const uint32_t mk = (var == 2 && (k == 1 || k == 2)) ? 0xCu : 0xFu;
+            m |= fixed_mask(i, mk);
+            ++k;
+        }
+    return m;
+}
 
 // One pass over tile t of the state: the body of tile_kernel and tile_batch_kernel.
 template <typename real, int Q, int R, bool kW, uint64_t kRecipe, int kNops, uint64_t kMasks, uint64_t kRecipeHi>
@@ -1531,7 +1555,7 @@ __global__ void __launch_bounds__(1 << (Q - R), tile_min_blocks<real, kW>(kRecip
 // tile_kernel.  Per CTA it writes, for accumulator slots 0 and 1, (sum of RXD pair terms,
 // sum of GRADG terms) to partials[2 t + slot].
 // (complex64 holds both states in 64 registers and runs two CTAs per SM; complex128 needs 128)
-template <typename real, int Q, int R, bool kW, uint64_t kRecipe = 0, int kNops = 0>
+template <typename real, int Q, int R, bool kW, uint64_t kRecipe = 0, int kNops = 0, uint64_t kMasks = 0>
 __global__ void __launch_bounds__(1 << (Q - R), sizeof(real) == 4 ? 2 : 1) grad_kernel(const __grid_constant__ TileArgs<Q> a) {
     // complex64: both states in the forward passes' parity form, packed butterflies with the real
     // factors undone through a.gpow and the sweep's phase tables; complex128: plain form, exact
@@ -1595,11 +1619,11 @@ __global__ void __launch_bounds__(1 << (Q - R), sizeof(real) == 4 ? 2 : 1) grad_
     double acc[4] = {0.0, 0.0, 0.0, 0.0};  // (pair terms, gamma terms) for slots 0 and 1
     const bool lam_init = a.nops > 1 && a.ops[1].kind == OP_LAMBDA;
     // d/d beta pair terms of one RXD op (and its butterflies), as a true-scale FP64 sum
-    auto rxd_op = [&](const Op& op, C2(&vv)[T::NE], C2(&ww)[T::NE]) -> double {
+    auto rxd_op = [&](auto FM, const Op& op, C2(&vv)[T::NE], C2(&ww)[T::NE]) -> double {
         const int level = sweep_level(op.arg);
         if constexpr (kPG) {
             const real t = reinterpret_cast<const C2*>(a.mix)[3 * level + 1].x;
-            const real d = T::template rxd_parity<kSweepScalar>(vv, ww, op.mask, -c.sg * t);
+            const real d = T::template rxd_parity<kSweepScalar, decltype(FM)::value>(vv, ww, op.mask, -c.sg * t);
             return (double)(c.sg * d) * a.gpow[level * (kMaxN + 1) + sweep_done(op.arg)];
         } else {
             const C2 cs = reinterpret_cast<const C2*>(a.mix)[3 * level];
@@ -1643,7 +1667,8 @@ __global__ void __launch_bounds__(1 << (Q - R), sizeof(real) == 4 ? 2 : 1) grad_
                 T::template from_smem<Lc>(w, tile2, tid, a.bounds_flag);
             } else if constexpr (kind == OP_RXD) {
                 const Op op = a.ops[i];
-                const double d = rxd_op(op, v, w);
+                constexpr uint32_t fm = i < 10 ? (uint32_t)((kMasks >> (6 * i)) & 63u) : 0u;
+                const double d = rxd_op(std::integral_constant<uint32_t, fm>{}, op, v, w);
                 if (sweep_slot(op.arg)) acc[2] += d;
                 else acc[0] += d;
             } else if constexpr (kind == OP_GRADG) {
@@ -1687,7 +1712,7 @@ __global__ void __launch_bounds__(1 << (Q - R), sizeof(real) == 4 ? 2 : 1) grad_
                 QAOA_BY_LAYOUT(from_smem, w, tile2, tid, a.bounds_flag);
                 break;
             case OP_RXD:
-                acc[2 * sweep_slot(op.arg)] += rxd_op(op, v, w);
+                acc[2 * sweep_slot(op.arg)] += rxd_op(std::integral_constant<uint32_t, 0>{}, op, v, w);
                 break;
             case OP_GRADG: {
                 double g = 0;
