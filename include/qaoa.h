@@ -18,9 +18,12 @@
  *
  * Memory: a state of 2^n amplitudes lives in a device buffer the CALLER allocates and owns
  * (complex64 = 2 x float32 interleaved, complex128 = 2 x float64 interleaved, index z).  The
- * library borrows it; it allocates only small workspace of its own (phase tables, per-tile
- * partial sums) at qaoa_state_init and frees it at qaoa_state_free.  Host arrays passed in
- * are copied before the call returns; the caller may free them afterwards.
+ * library borrows it; it takes only small workspace of its own (phase tables, per-tile
+ * partial sums) at qaoa_state_init and gives it back at qaoa_state_free.  That workspace comes
+ * from a stream-ordered memory pool the library keeps per device (cudaMallocFromPoolAsync on the
+ * state's stream), which holds on to up to 256 MiB of freed blocks for later states, so creating
+ * and freeing states in a loop costs no cudaMalloc or cudaFree once the pool is warm.  Host
+ * arrays passed in are copied before the call returns; the caller may free them afterwards.
  *
  * Errors: every entry point returns a qaoa_status; negative values are errors and
  * qaoa_last_error() returns a message for the calling thread.  Nothing aborts and no C++
@@ -124,8 +127,9 @@ qaoa_status qaoa_expectation(qaoa_state s, double *out_c, double *out_norm);
  * least qaoa_state_bytes(n, prec) bytes (16-byte aligned, not the state buffer), which it
  * overwrites.  Sums are reduced in FP64 in a fixed order.  Afterwards the state is |+>^n
  * (deferred).  Writes <C> to *out_c (may be NULL) and the 2p derivatives to d_gamma[0..p-1] and
- * d_beta[0..p-1]; synchronises the stream.  Allocates gradient workspace on first use (p phase
- * tables, 2 doubles per tile).  QAOA_ERR_INVALID on p < 1, non-finite angles or a bad buffer. */
+ * d_beta[0..p-1]; synchronises the stream.  Takes gradient workspace from the library's pool on
+ * first use (p phase tables, 2 doubles per tile), kept until qaoa_state_free.  QAOA_ERR_INVALID
+ * on p < 1, non-finite angles or a bad buffer; QAOA_ERR_OOM if the workspace cannot be had. */
 qaoa_status qaoa_gradient(qaoa_state s, int32_t p, const double *gamma, const double *beta,
                           void *dev_work, size_t work_bytes, double *out_c, double *d_gamma,
                           double *d_beta);
@@ -134,7 +138,8 @@ qaoa_status qaoa_gradient(qaoa_state s, int32_t p, const double *gamma, const do
  * |+>^n first.  Synchronises the stream.  Parity hook. */
 qaoa_status qaoa_state_copy_out(qaoa_state s, void *host_dst, size_t bytes);
 
-/* Releases the handle and its workspace after the stream's pending work; never frees the
+/* Gives the handle's workspace back to the library's pool (stream-ordered, on the state's
+ * stream), waits for the stream's pending work and releases the handle; never frees the
  * caller's buffer.  NULL is accepted. */
 qaoa_status qaoa_state_free(qaoa_state s);
 
@@ -241,8 +246,12 @@ qaoa_status qaoa_expectation_static(const qaoa_graph *g, qaoa_prec prec, const v
  *     one CTA per request, and the admitted mid-size complex64 forward requests (15 <= n <= 22,
  *     p <= 8, unit weights) of one (n, p) into packed launches (one launch per pass over every
  *     tile of up to 32 requests), while larger requests run concurrently on a pool of `streams`
- *     CUDA streams; with use_graphs each launch sequence is recorded into a CUDA graph and
- *     replayed through an executable graph cached per request shape;
+ *     CUDA streams; with two or more streams, requests whose state fills the GPU on its own
+ *     (64 MiB or more: n >= 23 complex64, n >= 22 complex128) run one after another on stream 0
+ *     at the lowest stream priority, and everything else on streams 1.. at the highest, so short
+ *     requests overtake the long passes instead of queueing behind them; with use_graphs each
+ *     launch sequence is recorded into a CUDA graph and replayed through an executable graph
+ *     cached per request shape;
  *   - completion is detected with CUDA events; results land in pinned host memory.
  * Each result is computed by the same kernels and reduction order as a lone request, so it is
  * identical alone and in the mix. */

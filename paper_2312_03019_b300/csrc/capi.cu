@@ -322,8 +322,10 @@ struct qaoa_state_s {
     void* d_gwfix = nullptr;      // weighted graphs: the adjoint sweep's rows (2 + levels) x m
     double2* d_partials = nullptr;
     double2* d_result = nullptr;
-    double2* h_result = nullptr;
+    double2 h_result[1] = {};     // <C> and norm read back (pageable: the read synchronises anyway)
     uint64_t partial_count = 0;
+    void* ws = nullptr;           // the block d_phase .. d_result are carved from (library pool)
+    void* gws = nullptr;          // the block of the adjoint sweep's workspace (library pool)
     // adjoint sweep workspace (allocated on the first qaoa_gradient call, grown as needed)
     int grad_levels = 0;
     void* d_gtab = nullptr;       // plain phase tables, [level][E1]
@@ -852,26 +854,61 @@ qaoa_status expectation_impl(qaoa_state s, double* out_c, double* out_norm) {
     return QAOA_OK;
 }
 
+// Per-state workspace comes from one stream-ordered memory pool per device, owned by the
+// library: a state takes one block at qaoa_state_init (and one more at its first gradient) and
+// gives it back at qaoa_state_free, on its own stream.  Freed blocks stay in the pool (up to
+// kPoolKeepBytes per device) for the next state, so creating and freeing a state costs no
+// cudaMalloc, cudaFree or device-wide synchronisation once the pool is warm.
+constexpr uint64_t kPoolKeepBytes = 256ull << 20;
+
+cudaError_t pool_create(int dev, cudaMemPool_t* out) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaError_t e = cudaMemPoolCreate(out, &props);
+    if (e != cudaSuccess) return e;
+    uint64_t keep = kPoolKeepBytes;
+    return cudaMemPoolSetAttribute(*out, cudaMemPoolAttrReleaseThreshold, &keep);
+}
+
+// One block of `bytes` on `stream` from the pool of device `dev`.  A pool whose context is gone
+// (after cudaDeviceReset) fails with an error other than out-of-memory: it is then created anew
+// once.
+cudaError_t ws_alloc(int dev, cudaStream_t stream, size_t bytes, void** out) {
+    static std::mutex mu;
+    static std::vector<cudaMemPool_t> pools;
+    std::lock_guard<std::mutex> lk(mu);
+    if ((int)pools.size() <= dev) pools.resize(dev + 1, nullptr);
+    cudaError_t e = cudaSuccess;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        if (!pools[dev]) {
+            e = pool_create(dev, &pools[dev]);
+            if (e != cudaSuccess) {
+                pools[dev] = nullptr;
+                return e;
+            }
+        }
+        e = cudaMallocFromPoolAsync(out, bytes, pools[dev], stream);
+        if (e == cudaSuccess || e == cudaErrorMemoryAllocation) return e;
+        cudaGetLastError();
+        pools[dev] = nullptr;
+    }
+    return e;
+}
+
+size_t ws_round(size_t x) { return (x + 255) & ~(size_t)255; }
+
 void release(qaoa_state s) {
     if (!s) return;
     cudaSetDevice(s->dev);
-    if (s->stream) cudaStreamSynchronize(s->stream);
     for (auto& e : s->events) {
         if (e.a) cudaEventDestroy(e.a);
         if (e.b) cudaEventDestroy(e.b);
     }
-    cudaFree(s->d_phase);
-    cudaFree(s->d_mix);
-    cudaFree(s->d_wfix);
-    cudaFree(s->d_gwfix);
-    cudaFree(s->d_partials);
-    cudaFree(s->d_result);
-    cudaFree(s->d_gtab);
-    cudaFree(s->d_gmix);
-    cudaFree(s->d_gacc);
-    cudaFree(s->d_gpart);
-    cudaFree(s->d_gpow);
-    if (s->h_result) cudaFreeHost(s->h_result);
+    if (s->ws) cudaFreeAsync(s->ws, s->stream);
+    if (s->gws) cudaFreeAsync(s->gws, s->stream);
+    cudaStreamSynchronize(s->stream);
     delete s;
 }
 
@@ -1107,28 +1144,38 @@ void annotate_sweep(Plan& plan, int p) {
 
 qaoa_status grad_workspace(qaoa_state s, int p) {
     if (p <= s->grad_levels && s->d_gtab) return QAOA_OK;
-    cudaFree(s->d_gtab);
-    cudaFree(s->d_gmix);
-    cudaFree(s->d_gacc);
-    cudaFree(s->d_gpart);
-    cudaFree(s->d_gwfix);
-    cudaFree(s->d_gpow);
+    if (s->gws) cudaFreeAsync(s->gws, s->stream);
+    s->gws = nullptr;
     s->d_gtab = s->d_gmix = s->d_gwfix = nullptr;
     s->d_gacc = nullptr;
     s->d_gpart = nullptr;
     s->d_gpow = nullptr;
     s->grad_levels = 0;
     const size_t eb = elem_bytes(s->prec);
-    cudaError_t e = cudaMalloc(&s->d_gtab, (size_t)p * table_entries(s->g) * eb);
-    if (e == cudaSuccess && s->g.weighted) e = cudaMalloc(&s->d_gwfix, wfix_bytes(s->g, s->prec, p));
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_gmix, (size_t)3 * p * eb);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_gacc, (size_t)2 * p * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_gpart, (size_t)2 * grad_tiles(s->n) * sizeof(double2));
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_gpow, (size_t)p * (kMaxN + 1) * sizeof(double));
+    const size_t b_tab = ws_round((size_t)p * table_entries(s->g) * eb);
+    const size_t b_wfix = s->g.weighted ? ws_round(wfix_bytes(s->g, s->prec, p)) : 0;
+    const size_t b_mix = ws_round((size_t)3 * p * eb);
+    const size_t b_acc = ws_round((size_t)2 * p * sizeof(double));
+    const size_t b_part = ws_round((size_t)2 * grad_tiles(s->n) * sizeof(double2));
+    const size_t b_pow = ws_round((size_t)p * (kMaxN + 1) * sizeof(double));
+    const cudaError_t e = ws_alloc(s->dev, s->stream, b_tab + b_wfix + b_mix + b_acc + b_part + b_pow, &s->gws);
     if (e != cudaSuccess) {
         cudaGetLastError();
+        s->gws = nullptr;
         return fail(QAOA_ERR_OOM, std::string("gradient workspace allocation failed: ") + cudaGetErrorString(e));
     }
+    char* b = static_cast<char*>(s->gws);
+    s->d_gtab = b;
+    b += b_tab;
+    if (b_wfix) s->d_gwfix = b;
+    b += b_wfix;
+    s->d_gmix = b;
+    b += b_mix;
+    s->d_gacc = reinterpret_cast<double*>(b);
+    b += b_acc;
+    s->d_gpart = reinterpret_cast<double2*>(b);
+    b += b_part;
+    s->d_gpow = reinterpret_cast<double*>(b);
     s->grad_levels = p;
     return QAOA_OK;
 }
@@ -1312,17 +1359,27 @@ qaoa_status qaoa_state_init(const qaoa_graph* g, qaoa_prec prec, void* dev_buf, 
         s->ntiles = 1ull << (hg.n - s->tc.Q);
     }
     const size_t eb = elem_bytes(prec);
-    cudaError_t e = cudaMalloc(&s->d_phase, (size_t)kLayerChunk * table_entries(hg) * eb);
-    if (e == cudaSuccess && hg.weighted) e = cudaMalloc(&s->d_wfix, wfix_bytes(hg, prec, kLayerChunk));
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_mix, (size_t)3 * kLayerChunk * eb);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_partials, (size_t)s->ntiles * sizeof(double2));
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_result, sizeof(double2));
-    if (e == cudaSuccess) e = cudaMallocHost(&s->h_result, sizeof(double2));
+    const size_t b_phase = ws_round((size_t)kLayerChunk * table_entries(hg) * eb);
+    const size_t b_wfix = hg.weighted ? ws_round(wfix_bytes(hg, prec, kLayerChunk)) : 0;
+    const size_t b_mix = ws_round((size_t)3 * kLayerChunk * eb);
+    const size_t b_part = ws_round((size_t)s->ntiles * sizeof(double2));
+    const cudaError_t e = ws_alloc(s->dev, s->stream, b_phase + b_wfix + b_mix + b_part + sizeof(double2), &s->ws);
     if (e != cudaSuccess) {
-        release(s);
+        s->ws = nullptr;
         cudaGetLastError();
+        release(s);
         return fail(QAOA_ERR_OOM, std::string("workspace allocation failed: ") + cudaGetErrorString(e));
     }
+    char* b = static_cast<char*>(s->ws);
+    s->d_phase = b;
+    b += b_phase;
+    if (b_wfix) s->d_wfix = b;
+    b += b_wfix;
+    s->d_mix = b;
+    b += b_mix;
+    s->d_partials = reinterpret_cast<double2*>(b);
+    b += b_part;
+    s->d_result = reinterpret_cast<double2*>(b);
     s->lazy = true;
     s->exp_valid = false;
     if (hg.weighted) {  // endpoint and value rows, read by <C> of a state with no level applied

@@ -5,7 +5,8 @@
 // has completed, (2) admits queued requests in arrival order while the arena has room for their
 // footprint and fewer than max_inflight run, (3) packs every admitted small forward request into
 // one launch (coefficient tables for all of them, then one CTA per request), and (4) dispatches
-// every other admitted request on the least loaded stream of the pool.  With use_graphs, each
+// every other admitted request on a stream of the pool: requests that fill the GPU on their own
+// in order on a low-priority lane, the rest on the least loaded high-priority stream.  With use_graphs, each
 // dispatch's launch sequence is recorded by stream capture and replayed through an executable
 // graph kept per shape (a small pool per shape, since one executable graph cannot run
 // concurrently with itself; executables are updated in place with cudaGraphExecUpdate).
@@ -261,9 +262,23 @@ cudaEvent_t take_event(qaoa_server_s* sv) {
     return e;
 }
 
-int pick_stream(qaoa_server_s* sv) {
-    int best = 0;
-    for (int i = 1; i < (int)sv->streams.size(); ++i)
+// A request whose state is at least kLaneBytes fills the GPU on its own (n >= 23 complex64:
+// 1024 tiles per pass); two of them running at once only split the memory bandwidth and evict
+// each other's state from L2.  With two or more streams, such requests run one after another on
+// stream 0, the low-priority lane, and every other request and pack goes to the least loaded of
+// the high-priority streams 1.., whose CTAs the block scheduler places ahead of the big passes'.
+constexpr uint64_t kLaneBytes = 64ull << 20;
+
+bool fills_gpu(const qaoa_server_s* sv, const SReq& r) {
+    return ((1ull << r.g.n) * elem_bytes(sv->cfg.prec)) >= kLaneBytes;
+}
+
+int pick_stream(qaoa_server_s* sv, bool big) {
+    const int S = (int)sv->streams.size();
+    if (S < 2) return 0;
+    if (big) return 0;
+    int best = 1;
+    for (int i = 2; i < S; ++i)
         if (sv->stream_load[i] < sv->stream_load[best]) best = i;
     return best;
 }
@@ -360,7 +375,7 @@ qaoa_status dispatch_single(qaoa_server_s* sv, SReq&& r, size_t off, const Layou
     run.off = off;
     run.bytes = L.total;
     run.slot = slot;
-    run.stream = pick_stream(sv);
+    run.stream = pick_stream(sv, fills_gpu(sv, r));
     char* base = sv->arena.base + off;
     qaoa_state_s* st = new (std::nothrow) qaoa_state_s;
     if (!st) return fail(QAOA_ERR_OOM, "host allocation failed");
@@ -457,7 +472,7 @@ qaoa_status dispatch_batch(qaoa_server_s* sv, std::vector<SReq>&& reqs, std::vec
         nmax = std::max(nmax, r.g.n);
     }
     RunningBatch rb;
-    rb.stream = pick_stream(sv);
+    rb.stream = pick_stream(sv, false);
     cudaStream_t stream = sv->streams[rb.stream];
     auto enqueue = [&]() -> qaoa_status {
         CUDA_TRY(cudaMemcpyAsync(head, stage, BL.upload, cudaMemcpyHostToDevice, stream));
@@ -529,7 +544,7 @@ qaoa_status dispatch_mid_batch(qaoa_server_s* sv, std::vector<SReq>& reqs, const
     CoeffArgs* cargs = reinterpret_cast<CoeffArgs*>(stage + ML.cargs);
     double2* res_host = reinterpret_cast<double2*>(stage + ML.upload);
     RunningBatch rb;
-    rb.stream = pick_stream(sv);
+    rb.stream = pick_stream(sv, false);
     cudaStream_t stream = sv->streams[rb.stream];
     unsigned gx = 1;
     for (int b = 0; b < B; ++b) {
@@ -917,9 +932,12 @@ qaoa_status qaoa_server_create(const qaoa_server_config* cfg, qaoa_server* out) 
     e = cudaMallocHost(&sv->pin_single, (size_t)slots * (2 + 2 * QAOA_SERVE_MAX_P) * sizeof(double));
     if (e == cudaSuccess) e = cudaMallocHost(&sv->pin_stage, (size_t)stages * sv->stage_bytes);
     if (e == cudaSuccess && cfg->prec == QAOA_C64) e = cudaMallocHost(&sv->pin_mid, (size_t)kMidStages * mid_stage_bytes());
+    int prio_low = 0, prio_high = 0;  // stream 0 (the lane of GPU-filling requests) runs at the lowest
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
     for (int i = 0; i < cfg->streams && e == cudaSuccess; ++i) {
         cudaStream_t s = nullptr;
-        e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        const int prio = cfg->streams < 2 ? 0 : (i == 0 ? prio_low : prio_high);
+        e = cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, prio);
         sv->streams.push_back(s);
         sv->stream_load.push_back(0);
     }
