@@ -75,6 +75,9 @@ def parse_args():
                     help="time the CPU oracle on the host's cores (all threads and one) at the small configurations")
     ap.add_argument("--grad", action="store_true",
                     help="gradient mode: d<C>/d(gamma, beta) by qaoa_gradient on G(24, 0.5), p = 10")
+    ap.add_argument("--grad-n", type=int, default=24,
+                    help="--grad: vertices of the G(n, 0.5) graph (default 24, the gradient workload)")
+    ap.add_argument("--grad-p", type=int, default=10, help="--grad: levels (default 10)")
     ap.add_argument("--serve", action="store_true",
                     help="serving mode: an open-loop Poisson request stream through qaoa_submit/qaoa_poll")
     ap.add_argument("--serve-requests", type=int, default=4096)
@@ -721,15 +724,19 @@ def oracle_level_seconds_graph(g, gamma, beta):
     return time.perf_counter() - t0, g
 
 
-def grad_block(B, prec="c64", weighted=False, steps=10, warmup=3, accuracy=True):
+def grad_block(B, prec="c64", weighted=False, steps=10, warmup=3, accuracy=True, n=24, p=10):
     """Adjoint gradients per second on G(24, 0.5), seed 0, p = 10 (20 parameters), through
     qaoa_gradient (forward levels, lambda = C psi, reverse sweep; host-synchronous per call),
     beside the forward evaluation of the same circuit and the 4p forward evaluations central
-    differences would need."""
+    differences would need.  Other sizes: G(n, 0.5), seed 0, with p seeded levels."""
     import numpy as np
     import torch
 
-    g, gamma, beta = I.workload_gnp24_p10()
+    if (n, p) == (24, 10):
+        g, gamma, beta = I.workload_gnp24_p10()
+    else:
+        g = I.gnp(n, 0.5, 0)
+        gamma, beta = I.angles(p, 0)
     if weighted:  # the same graph with seeded U[0.1, 2] edge weights (Algorithm 2 path)
         g = I.random_weights(g, seed=0, lo=0.1, hi=2.0)
     s = B.QAOAState(g, prec)
@@ -759,7 +766,7 @@ def grad_block(B, prec="c64", weighted=False, steps=10, warmup=3, accuracy=True)
     p = len(gamma)
     rec = {"metric": "QAOA adjoint gradients/s", "value": 1.0 / t_grad, "unit": "gradients/s",
            "higher_is_better": True, "steps": K, "warmup": warm, "dtype": "f32" if prec == "c64" else "f64",
-           "config": {"workload": f"G(24, 0.5) seed 0{' with edge weights U[0.1, 2]' if weighted else ''}, "
+           "config": {"workload": f"G({n}, 0.5) seed 0{' with edge weights U[0.1, 2]' if weighted else ''}, "
                                   f"|E|={g.m}, p={p} seeded levels ({2 * p} parameters), "
                                   f"{'complex64' if prec == 'c64' else 'complex128'}, host-timed calls"},
            "ms_per_gradient": t_grad * 1e3, "ms_per_forward": t_fwd * 1e3,
@@ -792,7 +799,8 @@ def run_grad(args):
     bld.build()
     from paper_2312_03019_b300 import binding as B
 
-    rec = grad_block(B, args.prec, args.weighted, args.steps, args.warmup, not args.no_accuracy)
+    rec = grad_block(B, args.prec, args.weighted, args.steps, args.warmup, not args.no_accuracy, args.grad_n,
+                     args.grad_p)
     rec.update({"n_gpus": 1, "mode": "grad", "data": "synthetic"})
     print(json.dumps(rec), flush=True)
     return 0

@@ -499,7 +499,13 @@ constexpr GradFn<float> grad_recipe_fn() {
 template <bool kW>
 GradFn<float> grad_recipe_fn_for(int r, int v) {
     if (r == 0) return v == 1 ? grad_recipe_fn<0, kW, 1>() : v == 0 ? grad_recipe_fn<0, kW>() : nullptr;
-    if (r == 1) return v == 1 ? grad_recipe_fn<1, kW, 1>() : v == 2 ? grad_recipe_fn<1, kW, 2>() : grad_recipe_fn<1, kW>();
+    if (r == 1)
+        return v == 1   ? grad_recipe_fn<1, kW, 1>()
+               : v == 2 ? grad_recipe_fn<1, kW, 2>()
+               : v == 3 ? grad_recipe_fn<1, kW, 3>()
+                        : grad_recipe_fn<1, kW>();
+    if (r == 3) return v == 1 ? grad_recipe_fn<3, kW, 1>() : v == 0 ? grad_recipe_fn<3, kW>() : nullptr;
+    if (r == 4) return v == 1 ? grad_recipe_fn<4, kW, 1>() : v == 0 ? grad_recipe_fn<4, kW>() : nullptr;
     return v == 0 ? grad_recipe_fn<2, kW>() : nullptr;
 }
 template <typename real>

@@ -1293,7 +1293,9 @@ __host__ __device__ constexpr int tile_min_blocks(uint64_t recipe, int nops) {
 
 // Adjoint-sweep pass programs compiled as straight-line grad_kernel instantiations: 0 the
 // group-0 pass and 1 the fused boundary pass of sweeps with three or more groups (n >= 21),
-// 2 the high-group pass of two-group sweeps; other programs run the interpreting instance.
+// 2 the high-group pass of two-group sweeps, 3 the first pass (lambda = C psi) and 4 the last
+// pass (no store) of sweeps with three groups whose high groups fit two register layouts
+// (n = 22..28); other programs run the interpreting instance.
 __host__ __device__ constexpr Recipe grad_recipe(int r) {
     return r == 0 ? Recipe{recipe_step(0, OP_LOAD, 1) | recipe_step(1, OP_RXD, 0) | recipe_step(2, OP_XCHG, 2) |
                                recipe_step(3, OP_RXD, 0) | recipe_step(4, OP_XCHG, 0) | recipe_step(5, OP_RXD, 0) |
@@ -1304,24 +1306,32 @@ __host__ __device__ constexpr Recipe grad_recipe(int r) {
                                recipe_step(6, OP_RXD, 0) | recipe_step(7, OP_XCHG, 0) | recipe_step(8, OP_RXD, 0) |
                                recipe_step(9, OP_STORE, 0),
                            10}
-                  : Recipe{recipe_step(0, OP_LOAD, 0) | recipe_step(1, OP_RXD, 0) | recipe_step(2, OP_GRADG, 0) |
+         : r == 2 ? Recipe{recipe_step(0, OP_LOAD, 0) | recipe_step(1, OP_RXD, 0) | recipe_step(2, OP_GRADG, 0) |
                                recipe_step(3, OP_PHASED, 0) | recipe_step(4, OP_RXD, 0) | recipe_step(5, OP_STORE, 0),
-                           6};
+                           6}
+         : r == 3 ? Recipe{recipe_step(0, OP_LOAD, 1) | recipe_step(1, OP_LAMBDA, 0) | recipe_step(2, OP_RXD, 0) |
+                               recipe_step(3, OP_XCHG, 0) | recipe_step(4, OP_RXD, 0) | recipe_step(5, OP_STORE, 0),
+                           6}
+                  : Recipe{recipe_step(0, OP_LOAD, 1) | recipe_step(1, OP_RXD, 0) | recipe_step(2, OP_XCHG, 0) |
+                               recipe_step(3, OP_RXD, 0) | recipe_step(4, OP_GRADG, 0),
+                           5};
 }
-constexpr int kGradRecipes = 3;
+constexpr int kGradRecipes = 5;
 // Compiled-in register masks of the sweep programs' RXD ops (6 bits per op, as recipe_masks):
-// variant 1 has every RXD op full (the group-0 pass always; the fused pass of 8-bit high groups),
-// variant 2 is the fused pass of 6-bit high groups, as at n = 24 (layout 1 holds two of the
-// group's bits).  Variant 0: runtime masks.
-constexpr int kGradMaskVariants = 3;
+// variant 1 has every RXD op full (the group-0 pass always; the fused, first and last passes of
+// 8-bit high groups), variant 2 is the fused pass of 6-bit high groups, as at n = 24 (layout 1
+// holds two of the group's bits), variant 3 that of 7-bit high groups (n = 25..27; three bits
+// in layout 1).  Variant 0: runtime masks.
+constexpr int kGradMaskVariants = 4;
 __host__ __device__ constexpr uint64_t grad_masks(int r, int var) {
     uint64_t m = 0;
-    if (var == 0 || r == 2 || (r == 0 && var == 2)) return 0;
+    if (var == 0 || r == 2 || (r != 1 && var != 1)) return 0;
     const Recipe d = grad_recipe(r);
     int k = 0;
     for (int i = 0; i < d.nops; ++i)
         if (recipe_kind(d.code, i) == OP_RXD) {
-            const uint32_t mk = (var == 2 && (k == 1 || k == 2)) ? 0xCu : 0xFu;
+            const bool mid = r == 1 && (k == 1 || k == 2);
+            const uint32_t mk = (mid && var == 2) ? 0xCu : (mid && var == 3) ? 0xEu : 0xFu;
             m |= fixed_mask(i, mk);
             ++k;
         }
@@ -1656,7 +1666,11 @@ __global__ void __launch_bounds__(1 << (Q - R), sizeof(real) == 4 ? 2 : 1) grad_
             constexpr int Lp = i == 0 ? 0 : recipe_layout(kRecipe, i - 1);
             if constexpr (kind == OP_LOAD) {
                 T::template load_from<Lc>(v, c, tid, a.state);
-                T::template load_from<Lc>(w, c, tid, a.state2);
+                // the sweep's first pass makes lambda from psi instead of loading it
+                if constexpr (!(kNops > 1 && recipe_kind(kRecipe, 1) == OP_LAMBDA))
+                    T::template load_from<Lc>(w, c, tid, a.state2);
+            } else if constexpr (kind == OP_LAMBDA) {
+                T::template lambda_init<Lc, kW>(v, w, c, tid);
             } else if constexpr (kind == OP_XCHG) {
                 // one barrier: a thread writes exactly the positions it read in the previous
                 // exchange (see to_smem)
