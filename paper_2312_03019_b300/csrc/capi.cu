@@ -295,6 +295,18 @@ TileConfig grad_tile_config(int prec) {
 
 uint64_t grad_tiles(int n) { return n > 12 ? 1ull << (n - 12) : 1ull; }
 
+// Adjoint passes whose per-tile partials are reduced together (grad_reduce_batch_kernel): as many
+// as 32 MiB of partials hold, at most kGradBatchMax and at most the 3p + 1 passes a sweep of p
+// levels can have (non-decreasing in p, so workspace sized for p serves any smaller p).
+int grad_chunk(int n, int p) {
+    const uint64_t per_pass = 2 * grad_tiles(n) * sizeof(double2);
+    const uint64_t fit = std::max<uint64_t>(1, (32ull << 20) / per_pass);
+    return (int)std::min<uint64_t>({fit, (uint64_t)kGradBatchMax, (uint64_t)(3 * p + 1)});
+}
+size_t grad_partials_bytes(int n, int p) { return (size_t)grad_chunk(n, p) * 2 * grad_tiles(n) * sizeof(double2); }
+// Per-level sums [2p], the batch sums [4 kGradBatchMax] and the batch ticket.
+size_t grad_acc_bytes(int p) { return ((size_t)2 * p + 4 * kGradBatchMax + 1) * sizeof(double); }
+
 struct EventPair {
     cudaEvent_t a = nullptr, b = nullptr;
     // 1 read+write mixer-only pass, 2 synthesising pass, 3 read+write pass with a cost phase,
@@ -331,7 +343,7 @@ struct qaoa_state_s {
     void* d_gtab = nullptr;       // plain phase tables, [level][E1]
     void* d_gmix = nullptr;       // [3 * level] mixer entries
     double* d_gacc = nullptr;     // [2 * levels]
-    double2* d_gpart = nullptr;   // [2 * tiles]
+    double2* d_gpart = nullptr;   // [grad_chunk passes][2 * tiles]
     double* d_gpow = nullptr;     // complex64 sweep: [level][kMaxN + 1] powers of the butterflies' factor
     bool lazy = true;
     bool exp_valid = false;
@@ -1161,8 +1173,8 @@ qaoa_status grad_workspace(qaoa_state s, int p) {
     const size_t b_tab = ws_round((size_t)p * table_entries(s->g) * eb);
     const size_t b_wfix = s->g.weighted ? ws_round(wfix_bytes(s->g, s->prec, p)) : 0;
     const size_t b_mix = ws_round((size_t)3 * p * eb);
-    const size_t b_acc = ws_round((size_t)2 * p * sizeof(double));
-    const size_t b_part = ws_round((size_t)2 * grad_tiles(s->n) * sizeof(double2));
+    const size_t b_acc = ws_round(grad_acc_bytes(p));
+    const size_t b_part = ws_round(grad_partials_bytes(s->n, p));
     const size_t b_pow = ws_round((size_t)p * (kMaxN + 1) * sizeof(double));
     const cudaError_t e = ws_alloc(s->dev, s->stream, b_tab + b_wfix + b_mix + b_acc + b_part + b_pow, &s->gws);
     if (e != cudaSuccess) {
@@ -1244,7 +1256,7 @@ qaoa_status gradient_async(qaoa_state s, int p, const double* gamma, const doubl
         CUDA_TRY(cudaGetLastError());
         s->launches++;
     }
-    CUDA_TRY(cudaMemsetAsync(s->d_gacc, 0, (size_t)2 * p * sizeof(double), s->stream));
+    CUDA_TRY(cudaMemsetAsync(s->d_gacc, 0, grad_acc_bytes(p), s->stream));
     if (s->n <= Q) {
         SmallGradJob j;
         std::memset(&j, 0, sizeof(j));
@@ -1276,15 +1288,20 @@ qaoa_status gradient_async(qaoa_state s, int p, const double* gamma, const doubl
         const size_t smem = (size_t)2 * (1u << Q) * sizeof(C2);  // psi's and lambda's exchange tiles
         qaoa_status ast = ensure_attributes<real>();
         if (ast != QAOA_OK) return ast;
+        // the passes' partials are reduced in batches of up to `chunk` passes, one launch each
+        const int chunk = grad_chunk(s->n, p);
+        GradBatch gb;
+        gb.npass = 0;
         TileArgs<Q> a;
-        for (const Pass& ps : plan.passes) {
+        for (size_t ip = 0; ip < plan.passes.size(); ++ip) {
+            const Pass& ps = plan.passes[ip];
             std::memset(&a, 0, sizeof(a));
             fill_program_with(a, s, ps, plan.groups, gtc);
             a.need_cut = 1;
             a.state2 = work;
             a.phase = s->d_gtab;
             a.mix = s->d_gmix;
-            a.partials = s->d_gpart;
+            a.partials = s->d_gpart + (size_t)gb.npass * 2 * gt;
             a.gpow = s->d_gpow;
             if (s->g.weighted && !fill_weighted(a, s->g, s->prec, s->d_gwfix, a.ops, a.nops))
                 return fail(QAOA_ERR_UNSUPPORTED, "too many phase levels in one adjoint pass");
@@ -1294,9 +1311,20 @@ qaoa_status gradient_async(qaoa_state s, int p, const double* gamma, const doubl
             NvtxRange range("qaoa adjoint pass");
             pick_grad_kernel<real>(a, s->g.weighted)<<<(unsigned)gt, 1u << (Q - R), smem, s->stream>>>(a);
             CUDA_TRY(cudaGetLastError());
-            grad_reduce_kernel<<<1, 1024, 0, s->stream>>>(s->d_gpart, gt, lev[0], lev[1], p, s->d_gacc);
-            CUDA_TRY(cudaGetLastError());
-            s->launches += 2;
+            s->launches++;
+            gb.lev[gb.npass][0] = lev[0];
+            gb.lev[gb.npass][1] = lev[1];
+            ++gb.npass;
+            if (gb.npass == chunk || ip + 1 == plan.passes.size()) {
+                if (gb.npass == 1)
+                    grad_reduce_kernel<<<1, 1024, 0, s->stream>>>(s->d_gpart, gt, lev[0], lev[1], p, s->d_gacc);
+                else
+                    grad_reduce_batch_kernel<<<(unsigned)gb.npass, 1024, 0, s->stream>>>(s->d_gpart, gt, gb, p,
+                                                                                       s->d_gacc);
+                CUDA_TRY(cudaGetLastError());
+                s->launches++;
+                gb.npass = 0;
+            }
         }
     }
     // the sweep consumed the state: it is |+>^n again

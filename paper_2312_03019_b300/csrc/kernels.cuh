@@ -14,7 +14,8 @@
 //                  pass recipe as straight-line code (kRecipe, kNops, kMasks).
 //   grad_kernel    one pass of the adjoint sweep over psi and lambda = C psi (inverse mixer with
 //                  the d/d beta pair sums, the d/d gamma sums, the conjugate phase), with
-//   grad_reduce_kernel  the fixed-order sum of its per-tile partials per level.
+//   grad_reduce_kernel  the fixed-order sum of its per-tile partials per level
+//                  (grad_reduce_batch_kernel: the same for a batch of passes in one launch).
 //   small_kernel / small_batch_kernel / small_grad_kernel / coeff_batch_kernel
 //                  a whole state of n <= Q_small qubits in shared memory, all levels in one
 //                  launch: one CTA per state, many states per launch for the server.
@@ -1776,6 +1777,66 @@ __global__ void __launch_bounds__(1 << (Q - R), sizeof(real) == 4 ? 2 : 1) grad_
             a.partials[2 * t] = make_double2(r[0], r[1]);
             a.partials[2 * t + 1] = make_double2(r[2], r[3]);
         }
+    }
+}
+
+// A batch of adjoint passes whose per-tile partials are reduced by one launch: pass i of the
+// batch wrote its partials at partials + 2 tiles i, and its slots belong to levels lev[i][0..1].
+constexpr int kGradBatchMax = 64;
+struct GradBatch {
+    int npass;
+    int lev[kGradBatchMax][2];
+};
+
+// The per-level sums of a batch of passes: CTA i sums pass i's partials exactly as
+// grad_reduce_kernel does and leaves the four sums in acc[2p + 4i ..]; the CTA that finishes last
+// (a ticket counter at acc[2p + 4 kGradBatchMax], zero on entry and left zero) adds them to the
+// per-level sums in pass order, so the result is bit-identical to one grad_reduce_kernel launch
+// after each pass.  No CTA waits for another.
+static __global__ void __launch_bounds__(1024) grad_reduce_batch_kernel(const double2* __restrict__ partials,
+                                                                 uint64_t tiles, const __grid_constant__ GradBatch b,
+                                                                 int p, double* __restrict__ acc) {
+    __shared__ double sm[4][1024];
+    __shared__ bool last;
+    const double2* pp = partials + (size_t)blockIdx.x * 2 * tiles;
+    double r[4] = {0.0, 0.0, 0.0, 0.0};
+    for (uint64_t i = threadIdx.x; i < tiles; i += 1024) {
+        const double2 a = pp[2 * i], c = pp[2 * i + 1];
+        r[0] += a.x;
+        r[1] += a.y;
+        r[2] += c.x;
+        r[3] += c.y;
+    }
+    for (int k = 0; k < 4; ++k) sm[k][threadIdx.x] = r[k];
+    __syncthreads();
+    for (int s = 512; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s)
+            for (int k = 0; k < 4; ++k) sm[k][threadIdx.x] += sm[k][threadIdx.x + s];
+        __syncthreads();
+    }
+    double* sums = acc + 2 * p;
+    unsigned long long* ticket = reinterpret_cast<unsigned long long*>(acc + 2 * p + 4 * kGradBatchMax);
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 4; ++k) sums[4 * blockIdx.x + k] = sm[k][0];
+        __threadfence();
+        last = atomicAdd(ticket, 1ull) == (unsigned long long)gridDim.x - 1ull;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        for (int i = 0; i < b.npass; ++i) {
+            const double s0 = __ldcg(sums + 4 * i), s1 = __ldcg(sums + 4 * i + 1);
+            const double s2 = __ldcg(sums + 4 * i + 2), s3 = __ldcg(sums + 4 * i + 3);
+            if (b.lev[i][0] >= 0) {
+                acc[b.lev[i][0]] += s0;
+                acc[p + b.lev[i][0]] += s1;
+            }
+            if (b.lev[i][1] >= 0) {
+                acc[b.lev[i][1]] += s2;
+                acc[p + b.lev[i][1]] += s3;
+            }
+        }
+        *ticket = 0ull;
     }
 }
 

@@ -105,8 +105,8 @@ Layout single_layout(const HostGraph& g, int p, int prec, bool grad, uint64_t nt
     if (grad) {
         L.gtab = take((size_t)p * E1 * eb);
         L.gmix = take((size_t)3 * p * eb);
-        L.gacc = take((size_t)2 * p * sizeof(double));
-        L.gpart = take((size_t)2 * grad_tiles(n) * sizeof(double2));
+        L.gacc = take(grad_acc_bytes(p));
+        L.gpart = take(grad_partials_bytes(n, p));
         L.gpow = take((size_t)p * (kMaxN + 1) * sizeof(double));
         if (g.weighted) L.gwfix = take(wfix_bytes(g, prec, p));
     }
