@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <set>
@@ -527,31 +528,95 @@ GradFn<real> grad_recipe_kernel(int r, bool weighted, int v = 0) {
     return nullptr;
 }
 
+// The persistent prefetching form of compiled sweep program r with mask variant v (complex64,
+// unit weights; grad_pf_kernel), or nullptr.
+using GradPfFn = void (*)(TileArgs<GradTraits<float>::Q>, uint64_t);
+template <int r, int v>
+constexpr GradPfFn grad_pf_fn() {
+    return grad_pf_kernel<GradTraits<float>::Q, GradTraits<float>::R, grad_recipe(r).code, grad_recipe(r).nops,
+                          grad_masks(r, v)>;
+}
+GradPfFn grad_pf_for(int r, int v) {
+    switch (r * 8 + v) {
+        case 0 * 8 + 1: return grad_pf_fn<0, 1>();
+        case 1 * 8 + 0: return grad_pf_fn<1, 0>();
+        case 1 * 8 + 1: return grad_pf_fn<1, 1>();
+        case 1 * 8 + 2: return grad_pf_fn<1, 2>();
+        case 1 * 8 + 3: return grad_pf_fn<1, 3>();
+        case 3 * 8 + 0: return grad_pf_fn<3, 0>();
+        case 3 * 8 + 1: return grad_pf_fn<3, 1>();
+        case 4 * 8 + 0: return grad_pf_fn<4, 0>();
+        case 4 * 8 + 1: return grad_pf_fn<4, 1>();
+        default: return nullptr;
+    }
+}
+
+// The compiled sweep program (r, v) a pass's program matches: the mask variants whose
+// compiled-in masks are this pass's first, then the runtime one.  False: none (interpreting).
+template <typename real>
+bool match_grad_recipe(const TileArgs<GradTraits<real>::Q>& a, bool weighted, int* r_out, int* v_out) {
+    if (!std::is_same<real, float>::value || a.nops > 10) return false;
+    uint64_t code = 0;
+    for (int i = 0; i < a.nops; ++i) code |= recipe_step(i, a.ops[i].kind, a.ops[i].layout);
+    for (int r = 0; r < kGradRecipes; ++r) {
+        if (grad_recipe(r).nops != a.nops || grad_recipe(r).code != code) continue;
+        for (int v = kGradMaskVariants - 1; v >= 0; --v) {
+            const uint64_t m = grad_masks(r, v);
+            if (v > 0 && m == 0) continue;
+            bool ok = true;
+            for (int i = 0; i < a.nops && i < 10; ++i) {
+                const uint32_t fm = (uint32_t)((m >> (6 * i)) & 63u);
+                if ((fm & 32u) && a.ops[i].mask != (fm & 31u)) ok = false;
+            }
+            if (!ok || !grad_recipe_kernel<real>(r, weighted, v)) continue;
+            *r_out = r;
+            *v_out = v;
+            return true;
+        }
+    }
+    return false;
+}
+
 // The adjoint-pass kernel for a program: a compiled sweep program when one matches (complex64,
 // unit or edge weights), else the interpreting instantiation.
 template <typename real>
 GradFn<real> pick_grad_kernel(const TileArgs<GradTraits<real>::Q>& a, bool weighted) {
     constexpr int Q = GradTraits<real>::Q, R = GradTraits<real>::R;
-    if (std::is_same<real, float>::value && a.nops <= 10) {
-        uint64_t code = 0;
-        for (int i = 0; i < a.nops; ++i) code |= recipe_step(i, a.ops[i].kind, a.ops[i].layout);
-        for (int r = 0; r < kGradRecipes; ++r) {
-            if (grad_recipe(r).nops != a.nops || grad_recipe(r).code != code) continue;
-            // the mask variants whose compiled-in masks are this pass's, then the runtime one
-            for (int v = kGradMaskVariants - 1; v >= 0; --v) {
-                const uint64_t m = grad_masks(r, v);
-                if (v > 0 && m == 0) continue;
-                bool ok = true;
-                for (int i = 0; i < a.nops && i < 10; ++i) {
-                    const uint32_t fm = (uint32_t)((m >> (6 * i)) & 63u);
-                    if ((fm & 32u) && a.ops[i].mask != (fm & 31u)) ok = false;
-                }
-                if (!ok) continue;
-                if (GradFn<real> f = grad_recipe_kernel<real>(r, weighted, v)) return f;
-            }
-        }
-    }
+    int r = 0, v = 0;
+    if (match_grad_recipe<real>(a, weighted, &r, &v))
+        if (GradFn<real> f = grad_recipe_kernel<real>(r, weighted, v)) return f;
     return weighted ? grad_kernel<real, Q, R, true> : grad_kernel<real, Q, R, false>;
+}
+
+// The persistent prefetching kernel for a pass, when its program has one (complex64, unit
+// weights, a compiled program with an exchange), else nullptr.
+template <typename real>
+GradPfFn pick_grad_pf_kernel(const TileArgs<GradTraits<real>::Q>& a, bool weighted) {
+    int r = 0, v = 0;
+    if (weighted || !match_grad_recipe<real>(a, false, &r, &v)) return nullptr;
+    return grad_pf_for(r, v);
+}
+
+// CTAs of a persistent kernel that fit the current device at once (cached per device and kernel).
+template <typename F>
+unsigned resident_ctas(F f, int threads, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, unsigned> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    const auto key = std::make_pair(dev, reinterpret_cast<const void*>(f));
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, threads, smem) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    const unsigned n = (unsigned)std::max(0, per_sm * sms);
+    cache[key] = n;
+    return n;
 }
 
 // Dynamic shared-memory limits of every kernel, set once per device (the attribute belongs to
@@ -588,11 +653,15 @@ qaoa_status ensure_attributes() {
                                   (int)(2 * (1u << GQ) * sizeof(C2))));
     if constexpr (std::is_same<real, float>::value)
         for (int r = 0; r < kGradRecipes; ++r)
-            for (int v = 0; v < kGradMaskVariants; ++v)
+            for (int v = 0; v < kGradMaskVariants; ++v) {
                 for (bool w : {false, true})
                     if (GradFn<real> f = grad_recipe_kernel<real>(r, w, v))
                         CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                       (int)(2 * (1u << GQ) * sizeof(C2))));
+                if (GradPfFn f = grad_pf_for(r, v))
+                    CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)(2 * (1u << GQ) * sizeof(C2))));
+            }
     CUDA_TRY(cudaFuncSetAttribute(small_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024));
     CUDA_TRY(cudaFuncSetAttribute(small_batch_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024));
     CUDA_TRY(cudaFuncSetAttribute(small_grad_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1309,15 +1378,25 @@ qaoa_status gradient_async(qaoa_state s, int p, const double* gamma, const doubl
             for (const Op& op : ps.ops)
                 if (op.kind == OP_RXD || op.kind == OP_GRADG) lev[sweep_slot(op.arg)] = sweep_level(op.arg);
             NvtxRange range("qaoa adjoint pass");
-            pick_grad_kernel<real>(a, s->g.weighted)<<<(unsigned)gt, 1u << (Q - R), smem, s->stream>>>(a);
+            // the persistent prefetching form where the program has one: one partial pair per CTA
+            uint64_t count = gt;
+            GradPfFn pf = pick_grad_pf_kernel<real>(a, s->g.weighted);
+            const unsigned G = pf ? resident_ctas(pf, 1 << (Q - R), smem) : 0u;
+            if (pf && G > 0) {
+                count = std::min<uint64_t>(gt, G);
+                pf<<<(unsigned)count, 1u << (Q - R), smem, s->stream>>>(a, gt);
+            } else {
+                pick_grad_kernel<real>(a, s->g.weighted)<<<(unsigned)gt, 1u << (Q - R), smem, s->stream>>>(a);
+            }
             CUDA_TRY(cudaGetLastError());
             s->launches++;
             gb.lev[gb.npass][0] = lev[0];
             gb.lev[gb.npass][1] = lev[1];
+            gb.cnt[gb.npass] = (uint32_t)count;
             ++gb.npass;
             if (gb.npass == chunk || ip + 1 == plan.passes.size()) {
                 if (gb.npass == 1)
-                    grad_reduce_kernel<<<1, 1024, 0, s->stream>>>(s->d_gpart, gt, lev[0], lev[1], p, s->d_gacc);
+                    grad_reduce_kernel<<<1, 1024, 0, s->stream>>>(s->d_gpart, count, lev[0], lev[1], p, s->d_gacc);
                 else
                     grad_reduce_batch_kernel<<<(unsigned)gb.npass, 1024, 0, s->stream>>>(s->d_gpart, gt, gb, p,
                                                                                        s->d_gacc);

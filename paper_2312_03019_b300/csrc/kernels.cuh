@@ -647,6 +647,32 @@ struct Tile {
         }
     }
 
+    // Issues one 8-byte cp.async per amplitude of the thread in layout L (the elements load_from
+    // reads) into that element's place in a shared-memory tile (where from_smem, in any layout,
+    // reads it).  The values are copied raw, so this serves the forms that keep amplitudes as
+    // stored (kGP).  Completed by cp.async.wait_all in the caller, then a CTA barrier.
+    template <int L>
+    static __device__ __forceinline__ void prefetch_to(unsigned char* tile, const Ctx& c, uint32_t tid,
+                                                       const void* base, unsigned* bf = nullptr) {
+        static_assert(kPair && kGP && kSw == 0, "raw 8-byte copies in the default swizzle");
+        constexpr uint32_t kBytes = (1u << Q) * (uint32_t)sizeof(C2);
+        const TileArgs<Q>& a = *c.a;
+        const C2* g = reinterpret_cast<const C2*>(base) + c.zb + toff<L>(a, tid);
+        int64_t d[R];
+#pragma unroll
+        for (int j = 0; j < R; ++j) d[j] = a.rstep[L][j];
+        const uint32_t P = swz(tbits(L, tid)) * (uint32_t)sizeof(C2);
+        const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(tile);
+        for_x<NE>([&](auto X) {
+            constexpr int x = decltype(X)::value;
+            const uint32_t o = P ^ (swz((uint32_t)x << rlo(L)) * (uint32_t)sizeof(C2));
+            if (QAOA_IN_BOUNDS(bf, ((uint64_t)(g - reinterpret_cast<const C2*>(base)) >> a.n) == 0 && o + 8u <= kBytes,
+                               1u))
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s0 + o), "l"(g) : "memory");
+            if constexpr (x + 1 < NE) g += d[ctz_next(x)];
+        });
+    }
+
     // base(tau) and slopes s_j of the on-the-fly cut count in layout L
     template <int L>
     static __device__ __forceinline__ int cut_setup(const Ctx& c, uint32_t tid, int (&s)[R]) {
@@ -1780,12 +1806,173 @@ __global__ void __launch_bounds__(1 << (Q - R), sizeof(real) == 4 ? 2 : 1) grad_
     }
 }
 
-// A batch of adjoint passes whose per-tile partials are reduced by one launch: pass i of the
-// batch wrote its partials at partials + 2 tiles i, and its slots belong to levels lev[i][0..1].
+// Index of the last exchange of a compiled program (-1: none).
+__host__ __device__ constexpr int recipe_last_xchg(uint64_t r, int nops) {
+    int last = -1;
+    for (int i = 0; i < nops; ++i)
+        if (recipe_kind(r, i) == OP_XCHG) last = i;
+    return last;
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// The compiled complex64 sweep programs (unit weights) as a persistent, prefetching kernel: CTA b
+// runs tiles b, b + G, b + 2G, ... (G = gridDim.x, at most the CTAs that fit the GPU at once).
+// The next tile's psi and lambda are copied into the CTA's two exchange tiles by cp.async as
+// soon as the program's last exchange has read them, so the copy overlaps the rest of the
+// current tile (its last butterflies and its stores); the program's LOAD then reads shared
+// memory.  The FP64 sums of a thread run over all of its tiles and each CTA writes one partial
+// pair per slot: partials[2 b + slot] for b < G (the host reduces G entries per pass).  The
+// order is fixed for a given grid, so results are deterministic; they equal grad_kernel's up to
+// the order of the per-tile sums.
+template <int Q, int R, uint64_t kRecipe, int kNops, uint64_t kMasks>
+__global__ void __launch_bounds__(1 << (Q - R), 2)
+    grad_pf_kernel(const __grid_constant__ TileArgs<Q> a, uint64_t tiles) {
+    using real = float;
+    using T = Tile<real, Q, R, true>;
+    using C2 = typename T::C2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int kSetup = recipe_cut_setup(kRecipe, 0, kNops);
+    static_assert(kSetup == 0 || kSetup == 1 || kSetup == 2, "compiled sweep program");
+    // cut terms: one copy per warp (kSetup 2), else two copies used by alternate tiles, so that
+    // warp 0 can write a tile's terms while slower warps still read the previous tile's
+    constexpr int kCopies = kSetup == 2 ? T::NT / 32 : 2;
+    __shared__ int sE_all[kCopies][Q];
+    __shared__ int sK_all[kCopies];
+    constexpr bool kLam = kNops > 1 && recipe_kind(kRecipe, 1) == OP_LAMBDA;
+    constexpr int kLastX = recipe_last_xchg(kRecipe, kNops);
+    static_assert(kLastX > 0, "the prefetch follows the program's last exchange");
+    constexpr int kL0 = recipe_layout(kRecipe, 0);
+
+    unsigned char* tile = smem_raw;
+    unsigned char* tile2 = smem_raw + (1u << Q) * sizeof(C2);
+    const uint32_t tid = threadIdx.x;
+    auto zb_of = [&](uint64_t t) {
+        uint64_t z = 0;
+        for (int r = 0; r < a.nruns; ++r) z |= ((t >> a.run_src[r]) & ((1ull << a.run_len[r]) - 1ull)) << a.run_dst[r];
+        return z;
+    };
+    typename T::Ctx c;
+    c.a = &a;
+    c.wK = nullptr;
+    c.wE = nullptr;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};  // (pair terms, gamma terms) for slots 0 and 1
+
+    auto prefetch = [&](uint64_t t) {
+        typename T::Ctx cn = c;
+        cn.zb = zb_of(t);
+        T::template prefetch_to<kL0>(tile, cn, tid, a.state, a.bounds_flag);
+        if constexpr (!kLam) T::template prefetch_to<kL0>(tile2, cn, tid, a.state2, a.bounds_flag);
+        cp_async_commit();
+    };
+    if ((uint64_t)blockIdx.x < tiles) prefetch(blockIdx.x);
+
+    int it = 0;
+    for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x, ++it) {
+        const uint64_t zb = zb_of(t);
+        const uint32_t copy = kSetup == 2 ? tid / 32 : (uint32_t)(it & 1);
+        int* const sE = sE_all[copy];
+        auto cut_terms = [&]() {
+            const uint32_t lane = tid & 31u;
+            int s = 0;
+            for (int v = (int)lane; v < a.n; v += 32) {
+                const uint64_t bI = 0ull - ((zb >> v) & 1ull);
+                s += __popcll(a.gmask[v] & (bI ^ zb));
+            }
+            s = warp_sum_int(s);
+            if (lane == 0) sK_all[copy] = s;
+            if (lane < (uint32_t)Q) sE[lane] = __popcll(a.outAdj[lane]) - 2 * __popcll(a.outAdj[lane] & zb);
+        };
+        c.zb = zb;
+        c.sE = sE;
+        c.sg = (((__popcll(zb) + __popc(tid)) & 1) != 0) ? (real)-1 : (real)1;  // P of the parity form
+        cp_async_wait_all();
+        __syncthreads();  // every thread's copies of tile t have landed
+        if constexpr (kSetup == 2) {
+            cut_terms();
+            __syncwarp();
+            c.K = sK_all[copy];
+        } else {
+            c.K = 0;
+        }
+        C2 v[T::NE], w[T::NE];
+        T::template for_x<kNops>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            constexpr int kind = recipe_kind(kRecipe, i);
+            constexpr int Lc = recipe_layout(kRecipe, i);
+            constexpr int Lp = i == 0 ? 0 : recipe_layout(kRecipe, i - 1);
+            if constexpr (kind == OP_LOAD) {
+                T::template from_smem<Lc>(v, tile, tid, a.bounds_flag);
+                if constexpr (!kLam) T::template from_smem<Lc>(w, tile2, tid, a.bounds_flag);
+            } else if constexpr (kind == OP_LAMBDA) {
+                T::template lambda_init<Lc, false>(v, w, c, tid);
+            } else if constexpr (kind == OP_XCHG) {
+                T::template to_smem<Lp>(v, tile, tid, a.bounds_flag);
+                T::template to_smem<Lp>(w, tile2, tid, a.bounds_flag);
+                __syncthreads();
+                T::template from_smem<Lc>(v, tile, tid, a.bounds_flag);
+                T::template from_smem<Lc>(w, tile2, tid, a.bounds_flag);
+                if constexpr (i == kLastX) {
+                    __syncthreads();  // the tiles are read: the next tile may land in them
+                    if (t + gridDim.x < tiles) prefetch(t + gridDim.x);
+                }
+            } else if constexpr (kind == OP_RXD) {
+                const Op op = a.ops[i];
+                constexpr uint32_t fm = i < 10 ? (uint32_t)((kMasks >> (6 * i)) & 63u) : 0u;
+                const int level = sweep_level(op.arg);
+                const real tt = reinterpret_cast<const C2*>(a.mix)[3 * level + 1].x;
+                const real d = T::template rxd_parity<false, fm>(v, w, op.mask, -c.sg * tt);
+                const double dd = (double)(c.sg * d) * a.gpow[level * (kMaxN + 1) + sweep_done(op.arg)];
+                if (sweep_slot(op.arg)) acc[2] += dd;
+                else acc[0] += dd;
+            } else if constexpr (kind == OP_GRADG) {
+                if constexpr (kSetup == 1) c.K = sK_all[copy];
+                const real g = T::template grad_gamma_parity<Lc, false>(v, w, c, tid);
+                const double dd = (double)(c.sg * g) * a.gpow[sweep_level(a.ops[i].arg) * (kMaxN + 1) + a.n];
+                if (sweep_slot(a.ops[i].arg)) acc[3] += dd;
+                else acc[1] += dd;
+            } else if constexpr (kind == OP_PHASED) {
+                if constexpr (kSetup == 1) c.K = sK_all[copy];
+                T::template phase_dual_parity<Lc, false>(v, w, c, tid, a.ops[i].arg);
+            } else if constexpr (kind == OP_STORE) {
+                T::template store_to<Lc>(v, c, tid, a.state);
+                T::template store_to<Lc>(w, c, tid, a.state2);
+            }
+            // warp 0 computes the cut terms after its loads; the next exchange's barrier
+            // publishes them
+            if constexpr (kSetup == 1 && i == 0)
+                if (a.need_cut && tid < 32) cut_terms();
+        });
+    }
+    // one partial pair per slot and CTA, summed in FP64 by warp 0 through the (now idle) tile
+    double* red = reinterpret_cast<double*>(tile);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) red[k * T::NT + tid] = acc[k];
+    __syncthreads();
+    if (tid < 32) {
+        double r[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+        for (int i = 0; i < T::NT / 32; ++i)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) r[k] += red[k * T::NT + tid + 32 * i];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) r[k] = warp_sum_double(r[k]);
+        if (tid == 0 && (uint64_t)blockIdx.x < tiles) {
+            a.partials[2 * blockIdx.x] = make_double2(r[0], r[1]);
+            a.partials[2 * blockIdx.x + 1] = make_double2(r[2], r[3]);
+        }
+    }
+}
+
+// A batch of adjoint passes whose partials are reduced by one launch: pass i of the batch wrote
+// cnt[i] partial pairs at partials + 2 tiles i, and its slots belong to levels lev[i][0..1].
 constexpr int kGradBatchMax = 64;
 struct GradBatch {
     int npass;
     int lev[kGradBatchMax][2];
+    uint32_t cnt[kGradBatchMax];  // partial pairs pass i wrote (its tiles, or its CTAs)
 };
 
 // The per-level sums of a batch of passes: CTA i sums pass i's partials exactly as
@@ -1800,7 +1987,7 @@ static __global__ void __launch_bounds__(1024) grad_reduce_batch_kernel(const do
     __shared__ bool last;
     const double2* pp = partials + (size_t)blockIdx.x * 2 * tiles;
     double r[4] = {0.0, 0.0, 0.0, 0.0};
-    for (uint64_t i = threadIdx.x; i < tiles; i += 1024) {
+    for (uint64_t i = threadIdx.x; i < b.cnt[blockIdx.x]; i += 1024) {
         const double2 a = pp[2 * i], c = pp[2 * i + 1];
         r[0] += a.x;
         r[1] += a.y;
