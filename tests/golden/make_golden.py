@@ -1,9 +1,10 @@
 """Writes stored expected values for the large parity cases, computed by the CPU oracle only.
 
 Run from the repository root:  python tests/golden/make_golden.py [names...]
-The gate-level oracle (Algorithm 1 in complex128) needs minutes at n = 24..26, too long to
+The gate-level oracle (Algorithm 1 in complex128) needs minutes at n = 24..28, too long to
 rerun in every test session, so its <C>, norm and a seeded sample of amplitudes are stored as
-JSON here.  Nothing in this script touches the CUDA path.
+JSON here, and for the gradient cases (grad_*) the oracle's FP64 adjoint gradient d<C>/d gamma_k,
+d<C>/d beta_k.  Nothing in this script touches the CUDA path.
 """
 import json
 import os
@@ -24,6 +25,15 @@ CASES = {
     "gnp26_p4": I.workload_gnp26_p4,
     "gnp24_p10": I.workload_gnp24_p10,
     "regular3_n22_p6": lambda: (I.regular3(22, 0), *I.angles(6, 0)),
+}
+
+# adjoint gradients at the sizes whose sweeps use each compiled sweep program (high groups of
+# 6, 7 and 8 bits)
+GRAD_CASES = {
+    "grad_regular3_n24_p3": lambda: (I.regular3(24, 0), *I.angles(3, 24)),
+    "grad_regular3_n25_p3": lambda: (I.regular3(25, 0), *I.angles(3, 25)),
+    "grad_regular3_n27_p2": lambda: (I.regular3(27, 0), *I.angles(2, 27)),
+    "grad_regular3_n28_p2": lambda: (I.regular3(28, 0), *I.angles(2, 28)),
 }
 
 
@@ -55,6 +65,22 @@ def make(name):
     print(name, c, nrm, f"{time.time() - t0:.1f}s", flush=True)
 
 
+def make_grad(name):
+    g, gamma, beta = GRAD_CASES[name]()
+    t0 = time.time()
+    c, dg, db = oracle.adjoint_gradient(g, gamma, beta)
+    rec = {
+        "what": f"oracle FP64 adjoint gradient (Algorithm 1, complex128) on {g.name}, p={len(gamma)}",
+        "graph": g.name, "n": g.n, "m": g.m, "edges": g.edges.tolist(),
+        "gamma": gamma.tolist(), "beta": beta.tolist(),
+        "expectation": c, "d_gamma": [float(x) for x in dg], "d_beta": [float(x) for x in db],
+        "oracle_seconds": time.time() - t0, "oracle_threads": oracle.threads(),
+    }
+    with open(os.path.join(HERE, f"{name}.json"), "w") as f:
+        json.dump(rec, f, indent=1)
+    print(name, c, f"{time.time() - t0:.1f}s", flush=True)
+
+
 if __name__ == "__main__":
-    for nm in (sys.argv[1:] or list(CASES)):
-        make(nm)
+    for nm in (sys.argv[1:] or list(CASES) + list(GRAD_CASES)):
+        (make_grad if nm in GRAD_CASES else make)(nm)

@@ -1,5 +1,8 @@
 """GPU adjoint gradient d<C>/d(gamma_k, beta_k) (qaoa_gradient) against the FP64 CPU oracle adjoint
 and against central finite differences (h = 1e-4) evaluated in complex128 on the GPU."""
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -212,3 +215,34 @@ def test_gradient_full_size_p1_closed_form(B, n, prec):
         tol = c64_grad_tol(n, 1, g.m, max(abs(ref_dg), abs(ref_db))) + 1e-7 * g.m
         assert abs(c - f(ga, be)) <= 1e-5 * g.m
         assert abs(dg[0] - ref_dg) <= tol and abs(db[0] - ref_db) <= tol
+
+
+GRAD_GOLDEN = ["grad_regular3_n24_p3", "grad_regular3_n25_p3", "grad_regular3_n27_p2", "grad_regular3_n28_p2"]
+
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+@pytest.mark.parametrize("name", GRAD_GOLDEN)
+def test_gradient_stored_oracle_adjoint(B, name, prec):
+    """The adjoint gradient at n = 24..28, where the sweep runs its compiled programs (the
+    persistent prefetching form in complex64: the first, group-0, fused and last passes, with
+    the masks of 6-, 7- and 8-bit high groups), against the oracle's FP64 adjoint stored by
+    tests/golden/make_golden.py (which calls only the oracle)."""
+    path = os.path.join(os.path.dirname(__file__), "golden", f"{name}.json")
+    rec = json.load(open(path))
+    g = I.Graph(rec["n"], np.array(rec["edges"], dtype=np.int32))
+    gamma, beta = np.array(rec["gamma"]), np.array(rec["beta"])
+    ref_dg, ref_db = np.array(rec["d_gamma"]), np.array(rec["d_beta"])
+    c, dg, db = gpu_gradient(B, g, gamma, beta, prec)
+    import torch
+    torch.cuda.empty_cache()
+    big = np.max(np.abs(np.concatenate([ref_dg, ref_db])))
+    if prec == "c128":
+        scale = max(1.0, big)
+        assert abs(c - rec["expectation"]) <= 1e-12 * max(1.0, abs(rec["expectation"]))
+        assert np.max(np.abs(dg - ref_dg)) <= 1e-10 * scale
+        assert np.max(np.abs(db - ref_db)) <= 1e-10 * scale
+    else:
+        tol = c64_grad_tol(g.n, len(gamma), g.m, big)
+        assert abs(c - rec["expectation"]) <= 1e-5 * g.m
+        assert np.max(np.abs(dg - ref_dg)) <= tol
+        assert np.max(np.abs(db - ref_db)) <= tol
