@@ -519,7 +519,8 @@ GradFn<float> grad_recipe_fn_for(int r, int v) {
                         : grad_recipe_fn<1, kW>();
     if (r == 3) return v == 1 ? grad_recipe_fn<3, kW, 1>() : v == 0 ? grad_recipe_fn<3, kW>() : nullptr;
     if (r == 4) return v == 1 ? grad_recipe_fn<4, kW, 1>() : v == 0 ? grad_recipe_fn<4, kW>() : nullptr;
-    return v == 0 ? grad_recipe_fn<2, kW>() : nullptr;
+    if (r == 2) return v == 0 ? grad_recipe_fn<2, kW>() : nullptr;
+    return nullptr;  // programs 5..8: persistent form only
 }
 template <typename real>
 GradFn<real> grad_recipe_kernel(int r, bool weighted, int v = 0) {
@@ -534,7 +535,7 @@ using GradPfFn = void (*)(TileArgs<GradTraits<float>::Q>, uint64_t);
 template <int r, int v>
 constexpr GradPfFn grad_pf_fn() {
     return grad_pf_kernel<GradTraits<float>::Q, GradTraits<float>::R, grad_recipe(r).code, grad_recipe(r).nops,
-                          grad_masks(r, v)>;
+                          grad_masks(r, v), grad_recipe(r).hi>;
 }
 GradPfFn grad_pf_for(int r, int v) {
     switch (r * 8 + v) {
@@ -547,19 +548,28 @@ GradPfFn grad_pf_for(int r, int v) {
         case 3 * 8 + 1: return grad_pf_fn<3, 1>();
         case 4 * 8 + 0: return grad_pf_fn<4, 0>();
         case 4 * 8 + 1: return grad_pf_fn<4, 1>();
+        case 5 * 8 + 0: return grad_pf_fn<5, 0>();
+        case 6 * 8 + 0: return grad_pf_fn<6, 0>();
+        case 7 * 8 + 0: return grad_pf_fn<7, 0>();
+        case 8 * 8 + 0: return grad_pf_fn<8, 0>();
         default: return nullptr;
     }
 }
 
-// The compiled sweep program (r, v) a pass's program matches: the mask variants whose
-// compiled-in masks are this pass's first, then the runtime one.  False: none (interpreting).
-template <typename real>
-bool match_grad_recipe(const TileArgs<GradTraits<real>::Q>& a, bool weighted, int* r_out, int* v_out) {
-    if (!std::is_same<real, float>::value || a.nops > 10) return false;
-    uint64_t code = 0;
-    for (int i = 0; i < a.nops; ++i) code |= recipe_step(i, a.ops[i].kind, a.ops[i].layout);
+// The compiled sweep program (r, v) a pass's program matches, among those `exists(r, v)`
+// accepts: the mask variants whose compiled-in masks are this pass's first, then the runtime
+// one.  False: none (interpreting).
+template <typename real, typename Exists>
+bool match_grad_recipe(const TileArgs<GradTraits<real>::Q>& a, Exists&& exists, int* r_out, int* v_out) {
+    if (!std::is_same<real, float>::value || a.nops > 20) return false;
+    uint64_t lo = 0, hi = 0;
+    for (int i = 0; i < a.nops; ++i) {
+        lo |= recipe_step_lo(i, a.ops[i].kind, a.ops[i].layout);
+        hi |= recipe_step_hi(i, a.ops[i].kind, a.ops[i].layout);
+    }
     for (int r = 0; r < kGradRecipes; ++r) {
-        if (grad_recipe(r).nops != a.nops || grad_recipe(r).code != code) continue;
+        const Recipe d = grad_recipe(r);
+        if (d.nops != a.nops || d.code != lo || d.hi != hi) continue;
         for (int v = kGradMaskVariants - 1; v >= 0; --v) {
             const uint64_t m = grad_masks(r, v);
             if (v > 0 && m == 0) continue;
@@ -568,7 +578,7 @@ bool match_grad_recipe(const TileArgs<GradTraits<real>::Q>& a, bool weighted, in
                 const uint32_t fm = (uint32_t)((m >> (6 * i)) & 63u);
                 if ((fm & 32u) && a.ops[i].mask != (fm & 31u)) ok = false;
             }
-            if (!ok || !grad_recipe_kernel<real>(r, weighted, v)) continue;
+            if (!ok || !exists(r, v)) continue;
             *r_out = r;
             *v_out = v;
             return true;
@@ -583,7 +593,8 @@ template <typename real>
 GradFn<real> pick_grad_kernel(const TileArgs<GradTraits<real>::Q>& a, bool weighted) {
     constexpr int Q = GradTraits<real>::Q, R = GradTraits<real>::R;
     int r = 0, v = 0;
-    if (match_grad_recipe<real>(a, weighted, &r, &v))
+    auto exists = [&](int rr, int vv) { return grad_recipe_kernel<real>(rr, weighted, vv) != nullptr; };
+    if (match_grad_recipe<real>(a, exists, &r, &v))
         if (GradFn<real> f = grad_recipe_kernel<real>(r, weighted, v)) return f;
     return weighted ? grad_kernel<real, Q, R, true> : grad_kernel<real, Q, R, false>;
 }
@@ -593,7 +604,8 @@ GradFn<real> pick_grad_kernel(const TileArgs<GradTraits<real>::Q>& a, bool weigh
 template <typename real>
 GradPfFn pick_grad_pf_kernel(const TileArgs<GradTraits<real>::Q>& a, bool weighted) {
     int r = 0, v = 0;
-    if (weighted || !match_grad_recipe<real>(a, false, &r, &v)) return nullptr;
+    auto exists = [](int rr, int vv) { return grad_pf_for(rr, vv) != nullptr; };
+    if (weighted || !match_grad_recipe<real>(a, exists, &r, &v)) return nullptr;
     return grad_pf_for(r, v);
 }
 

@@ -103,7 +103,8 @@
 // the persistent prefetching sweep programs (grad_pf_kernel), complex64 unit weights
 #define QAOA_GRAD_PF_ONE(Q, R, r, v)                                                                  \
     QAOA_INSTANCE __global__ void grad_pf_kernel<Q, R, grad_recipe(r).code, grad_recipe(r).nops,           \
-                                                 grad_masks(r, v)>(const __grid_constant__ TileArgs<Q>, uint64_t);
+                                                 grad_masks(r, v), grad_recipe(r).hi>(                         \
+        const __grid_constant__ TileArgs<Q>, uint64_t);
 #define QAOA_GRAD_PF_INSTANCES(Q, R)                                                                  \
     namespace qaoa {                                                                                   \
     QAOA_GRAD_PF_ONE(Q, R, 0, 1)                                                                       \
@@ -115,6 +116,10 @@
     QAOA_GRAD_PF_ONE(Q, R, 3, 1)                                                                       \
     QAOA_GRAD_PF_ONE(Q, R, 4, 0)                                                                       \
     QAOA_GRAD_PF_ONE(Q, R, 4, 1)                                                                       \
+    QAOA_GRAD_PF_ONE(Q, R, 5, 0)                                                                       \
+    QAOA_GRAD_PF_ONE(Q, R, 6, 0)                                                                       \
+    QAOA_GRAD_PF_ONE(Q, R, 7, 0)                                                                       \
+    QAOA_GRAD_PF_ONE(Q, R, 8, 0)                                                                       \
     }
 
 // packed mid-size requests of the server: the complex64 two-group programs (recipes 8..12) and the

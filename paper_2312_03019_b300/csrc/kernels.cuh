@@ -1321,8 +1321,22 @@ __host__ __device__ constexpr int tile_min_blocks(uint64_t recipe, int nops) {
 // Adjoint-sweep pass programs compiled as straight-line grad_kernel instantiations: 0 the
 // group-0 pass and 1 the fused boundary pass of sweeps with three or more groups (n >= 21),
 // 2 the high-group pass of two-group sweeps, 3 the first pass (lambda = C psi) and 4 the last
-// pass (no store) of sweeps with three groups whose high groups fit two register layouts
-// (n = 22..28); other programs run the interpreting instance.
+// pass (no store) of sweeps whose high groups fit two register layouts (n = 22..28, 31..34),
+// 5 the plain high-group pass of four-group sweeps (n = 31..34), 6 / 7 / 8 the first, last and
+// fused boundary passes of 9-bit high groups, which need three layouts per level (n = 29, 30;
+// 8 is a two-word program of 14 ops).  0..4 also run as grad_kernel instantiations, all of them
+// in the persistent form (grad_pf_kernel); other programs run the interpreting instance.
+__host__ __device__ constexpr Recipe grad_recipe_fused3() {
+    constexpr int kSteps[14][2] = {{OP_LOAD, 0},  {OP_RXD, 0},   {OP_XCHG, 2}, {OP_RXD, 0}, {OP_XCHG, 1},
+                                   {OP_RXD, 0},   {OP_GRADG, 0}, {OP_PHASED, 0}, {OP_RXD, 0}, {OP_XCHG, 2},
+                                   {OP_RXD, 0},   {OP_XCHG, 0},  {OP_RXD, 0},  {OP_STORE, 0}};
+    Recipe d{0, 14, 0};
+    for (int i = 0; i < 14; ++i) {
+        d.code |= recipe_step_lo(i, kSteps[i][0], kSteps[i][1]);
+        d.hi |= recipe_step_hi(i, kSteps[i][0], kSteps[i][1]);
+    }
+    return d;
+}
 __host__ __device__ constexpr Recipe grad_recipe(int r) {
     return r == 0 ? Recipe{recipe_step(0, OP_LOAD, 1) | recipe_step(1, OP_RXD, 0) | recipe_step(2, OP_XCHG, 2) |
                                recipe_step(3, OP_RXD, 0) | recipe_step(4, OP_XCHG, 0) | recipe_step(5, OP_RXD, 0) |
@@ -1339,11 +1353,23 @@ __host__ __device__ constexpr Recipe grad_recipe(int r) {
          : r == 3 ? Recipe{recipe_step(0, OP_LOAD, 1) | recipe_step(1, OP_LAMBDA, 0) | recipe_step(2, OP_RXD, 0) |
                                recipe_step(3, OP_XCHG, 0) | recipe_step(4, OP_RXD, 0) | recipe_step(5, OP_STORE, 0),
                            6}
-                  : Recipe{recipe_step(0, OP_LOAD, 1) | recipe_step(1, OP_RXD, 0) | recipe_step(2, OP_XCHG, 0) |
+         : r == 4 ? Recipe{recipe_step(0, OP_LOAD, 1) | recipe_step(1, OP_RXD, 0) | recipe_step(2, OP_XCHG, 0) |
                                recipe_step(3, OP_RXD, 0) | recipe_step(4, OP_GRADG, 0),
-                           5};
+                           5}
+         : r == 5 ? Recipe{recipe_step(0, OP_LOAD, 1) | recipe_step(1, OP_RXD, 0) | recipe_step(2, OP_XCHG, 0) |
+                               recipe_step(3, OP_RXD, 0) | recipe_step(4, OP_STORE, 0),
+                           5}
+         : r == 6 ? Recipe{recipe_step(0, OP_LOAD, 1) | recipe_step(1, OP_LAMBDA, 0) | recipe_step(2, OP_RXD, 0) |
+                               recipe_step(3, OP_XCHG, 2) | recipe_step(4, OP_RXD, 0) | recipe_step(5, OP_XCHG, 0) |
+                               recipe_step(6, OP_RXD, 0) | recipe_step(7, OP_STORE, 0),
+                           8}
+         : r == 7 ? Recipe{recipe_step(0, OP_LOAD, 1) | recipe_step(1, OP_RXD, 0) | recipe_step(2, OP_XCHG, 2) |
+                               recipe_step(3, OP_RXD, 0) | recipe_step(4, OP_XCHG, 0) | recipe_step(5, OP_RXD, 0) |
+                               recipe_step(6, OP_GRADG, 0),
+                           7}
+                  : grad_recipe_fused3();
 }
-constexpr int kGradRecipes = 5;
+constexpr int kGradRecipes = 9;
 // Compiled-in register masks of the sweep programs' RXD ops (6 bits per op, as recipe_masks):
 // variant 1 has every RXD op full (the group-0 pass always; the fused, first and last passes of
 // 8-bit high groups), variant 2 is the fused pass of 6-bit high groups, as at n = 24 (layout 1
@@ -1352,7 +1378,7 @@ constexpr int kGradRecipes = 5;
 constexpr int kGradMaskVariants = 4;
 __host__ __device__ constexpr uint64_t grad_masks(int r, int var) {
     uint64_t m = 0;
-    if (var == 0 || r == 2 || (r != 1 && var != 1)) return 0;
+    if (var == 0 || r == 2 || r >= 5 || (r != 1 && var != 1)) return 0;
     const Recipe d = grad_recipe(r);
     int k = 0;
     for (int i = 0; i < d.nops; ++i)
@@ -1806,11 +1832,11 @@ __global__ void __launch_bounds__(1 << (Q - R), sizeof(real) == 4 ? 2 : 1) grad_
     }
 }
 
-// Index of the last exchange of a compiled program (-1: none).
-__host__ __device__ constexpr int recipe_last_xchg(uint64_t r, int nops) {
+// Index of the last exchange of a compiled (one- or two-word) program (-1: none).
+__host__ __device__ constexpr int recipe_last_xchg(uint64_t lo, uint64_t hi, int nops) {
     int last = -1;
     for (int i = 0; i < nops; ++i)
-        if (recipe_kind(r, i) == OP_XCHG) last = i;
+        if (recipe_kind2(lo, hi, i) == OP_XCHG) last = i;
     return last;
 }
 
@@ -1826,24 +1852,24 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // pair per slot: partials[2 b + slot] for b < G (the host reduces G entries per pass).  The
 // order is fixed for a given grid, so results are deterministic; they equal grad_kernel's up to
 // the order of the per-tile sums.
-template <int Q, int R, uint64_t kRecipe, int kNops, uint64_t kMasks>
+template <int Q, int R, uint64_t kRecipe, int kNops, uint64_t kMasks, uint64_t kRecipeHi = 0>
 __global__ void __launch_bounds__(1 << (Q - R), 2)
     grad_pf_kernel(const __grid_constant__ TileArgs<Q> a, uint64_t tiles) {
     using real = float;
     using T = Tile<real, Q, R, true>;
     using C2 = typename T::C2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr int kSetup = recipe_cut_setup(kRecipe, 0, kNops);
+    constexpr int kSetup = recipe_cut_setup(kRecipe, kRecipeHi, kNops);
     static_assert(kSetup == 0 || kSetup == 1 || kSetup == 2, "compiled sweep program");
     // cut terms: one copy per warp (kSetup 2), else two copies used by alternate tiles, so that
     // warp 0 can write a tile's terms while slower warps still read the previous tile's
     constexpr int kCopies = kSetup == 2 ? T::NT / 32 : 2;
     __shared__ int sE_all[kCopies][Q];
     __shared__ int sK_all[kCopies];
-    constexpr bool kLam = kNops > 1 && recipe_kind(kRecipe, 1) == OP_LAMBDA;
-    constexpr int kLastX = recipe_last_xchg(kRecipe, kNops);
+    constexpr bool kLam = kNops > 1 && recipe_kind2(kRecipe, kRecipeHi, 1) == OP_LAMBDA;
+    constexpr int kLastX = recipe_last_xchg(kRecipe, kRecipeHi, kNops);
     static_assert(kLastX > 0, "the prefetch follows the program's last exchange");
-    constexpr int kL0 = recipe_layout(kRecipe, 0);
+    constexpr int kL0 = recipe_layout2(kRecipe, kRecipeHi, 0);
 
     unsigned char* tile = smem_raw;
     unsigned char* tile2 = smem_raw + (1u << Q) * sizeof(C2);
@@ -1899,9 +1925,9 @@ __global__ void __launch_bounds__(1 << (Q - R), 2)
         C2 v[T::NE], w[T::NE];
         T::template for_x<kNops>([&](auto I) {
             constexpr int i = decltype(I)::value;
-            constexpr int kind = recipe_kind(kRecipe, i);
-            constexpr int Lc = recipe_layout(kRecipe, i);
-            constexpr int Lp = i == 0 ? 0 : recipe_layout(kRecipe, i - 1);
+            constexpr int kind = recipe_kind2(kRecipe, kRecipeHi, i);
+            constexpr int Lc = recipe_layout2(kRecipe, kRecipeHi, i);
+            constexpr int Lp = i == 0 ? 0 : recipe_layout2(kRecipe, kRecipeHi, i - 1);
             if constexpr (kind == OP_LOAD) {
                 T::template from_smem<Lc>(v, tile, tid, a.bounds_flag);
                 if constexpr (!kLam) T::template from_smem<Lc>(w, tile2, tid, a.bounds_flag);

@@ -28,12 +28,13 @@ CASES = {
 }
 
 # adjoint gradients at the sizes whose sweeps use each compiled sweep program (high groups of
-# 6, 7 and 8 bits)
+# 6, 7, 8 and 9 bits)
 GRAD_CASES = {
     "grad_regular3_n24_p3": lambda: (I.regular3(24, 0), *I.angles(3, 24)),
     "grad_regular3_n25_p3": lambda: (I.regular3(25, 0), *I.angles(3, 25)),
     "grad_regular3_n27_p2": lambda: (I.regular3(27, 0), *I.angles(2, 27)),
     "grad_regular3_n28_p2": lambda: (I.regular3(28, 0), *I.angles(2, 28)),
+    "grad_regular3_n29_p2": lambda: (I.regular3(29, 0), *I.angles(2, 29)),
 }
 
 

@@ -217,16 +217,18 @@ def test_gradient_full_size_p1_closed_form(B, n, prec):
         assert abs(dg[0] - ref_dg) <= tol and abs(db[0] - ref_db) <= tol
 
 
-GRAD_GOLDEN = ["grad_regular3_n24_p3", "grad_regular3_n25_p3", "grad_regular3_n27_p2", "grad_regular3_n28_p2"]
+GRAD_GOLDEN = ["grad_regular3_n24_p3", "grad_regular3_n25_p3", "grad_regular3_n27_p2", "grad_regular3_n28_p2",
+               "grad_regular3_n29_p2"]
 
 
 @pytest.mark.parametrize("prec", ["c64", "c128"])
 @pytest.mark.parametrize("name", GRAD_GOLDEN)
 def test_gradient_stored_oracle_adjoint(B, name, prec):
-    """The adjoint gradient at n = 24..28, where the sweep runs its compiled programs (the
+    """The adjoint gradient at n = 24..29, where the sweep runs its compiled programs (the
     persistent prefetching form in complex64: the first, group-0, fused and last passes, with
-    the masks of 6-, 7- and 8-bit high groups), against the oracle's FP64 adjoint stored by
-    tests/golden/make_golden.py (which calls only the oracle)."""
+    the masks of 6-, 7- and 8-bit high groups, and the three-layout programs of 9-bit groups),
+    against the oracle's FP64 adjoint stored by tests/golden/make_golden.py (which calls only
+    the oracle)."""
     path = os.path.join(os.path.dirname(__file__), "golden", f"{name}.json")
     rec = json.load(open(path))
     g = I.Graph(rec["n"], np.array(rec["edges"], dtype=np.int32))
