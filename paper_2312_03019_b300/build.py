@@ -20,7 +20,7 @@ LIB = os.path.join(HERE, "libqaoa_b300.so")
 LIB_DEBUG = os.path.join(HERE, "libqaoa_b300_debug.so")
 # translation units, compiled in parallel and linked into one shared object
 SOURCES = ["capi.cu", "tile_c64.cu", "recipes_c64.cu", "recipes_w_c64.cu", "tile_c128.cu", "grad_kernels.cu",
-           "grad_recipes.cu", "grad_recipes_m.cu", "grad_recipes_x.cu", "grad_pf.cu", "recipes2_c64.cu", "batch_c64.cu", "plan.cpp"]
+           "grad_recipes.cu", "grad_recipes_m.cu", "grad_recipes_x.cu", "grad_pf.cu", "grad_pf_w.cu", "recipes2_c64.cu", "batch_c64.cu", "plan.cpp"]
 HEADERS = ["kernels.cuh", "plan.h", "server.cuh", "instances.h", os.path.join("..", "..", "include", "qaoa.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -530,30 +530,34 @@ GradFn<real> grad_recipe_kernel(int r, bool weighted, int v = 0) {
 }
 
 // The persistent prefetching form of compiled sweep program r with mask variant v (complex64,
-// unit weights; grad_pf_kernel), or nullptr.
+// unit or edge weights; grad_pf_kernel), or nullptr.
 using GradPfFn = void (*)(TileArgs<GradTraits<float>::Q>, uint64_t);
-template <int r, int v>
+template <bool kW, int r, int v>
 constexpr GradPfFn grad_pf_fn() {
-    return grad_pf_kernel<GradTraits<float>::Q, GradTraits<float>::R, grad_recipe(r).code, grad_recipe(r).nops,
+    return grad_pf_kernel<GradTraits<float>::Q, GradTraits<float>::R, kW, grad_recipe(r).code, grad_recipe(r).nops,
                           grad_masks(r, v), grad_recipe(r).hi>;
 }
-GradPfFn grad_pf_for(int r, int v) {
+template <bool kW>
+GradPfFn grad_pf_for_w(int r, int v) {
     switch (r * 8 + v) {
-        case 0 * 8 + 1: return grad_pf_fn<0, 1>();
-        case 1 * 8 + 0: return grad_pf_fn<1, 0>();
-        case 1 * 8 + 1: return grad_pf_fn<1, 1>();
-        case 1 * 8 + 2: return grad_pf_fn<1, 2>();
-        case 1 * 8 + 3: return grad_pf_fn<1, 3>();
-        case 3 * 8 + 0: return grad_pf_fn<3, 0>();
-        case 3 * 8 + 1: return grad_pf_fn<3, 1>();
-        case 4 * 8 + 0: return grad_pf_fn<4, 0>();
-        case 4 * 8 + 1: return grad_pf_fn<4, 1>();
-        case 5 * 8 + 0: return grad_pf_fn<5, 0>();
-        case 6 * 8 + 0: return grad_pf_fn<6, 0>();
-        case 7 * 8 + 0: return grad_pf_fn<7, 0>();
-        case 8 * 8 + 0: return grad_pf_fn<8, 0>();
+        case 0 * 8 + 1: return grad_pf_fn<kW, 0, 1>();
+        case 1 * 8 + 0: return grad_pf_fn<kW, 1, 0>();
+        case 1 * 8 + 1: return grad_pf_fn<kW, 1, 1>();
+        case 1 * 8 + 2: return grad_pf_fn<kW, 1, 2>();
+        case 1 * 8 + 3: return grad_pf_fn<kW, 1, 3>();
+        case 3 * 8 + 0: return grad_pf_fn<kW, 3, 0>();
+        case 3 * 8 + 1: return grad_pf_fn<kW, 3, 1>();
+        case 4 * 8 + 0: return grad_pf_fn<kW, 4, 0>();
+        case 4 * 8 + 1: return grad_pf_fn<kW, 4, 1>();
+        case 5 * 8 + 0: return grad_pf_fn<kW, 5, 0>();
+        case 6 * 8 + 0: return grad_pf_fn<kW, 6, 0>();
+        case 7 * 8 + 0: return grad_pf_fn<kW, 7, 0>();
+        case 8 * 8 + 0: return grad_pf_fn<kW, 8, 0>();
         default: return nullptr;
     }
+}
+GradPfFn grad_pf_for(int r, int v, bool weighted) {
+    return weighted ? grad_pf_for_w<true>(r, v) : grad_pf_for_w<false>(r, v);
 }
 
 // The compiled sweep program (r, v) a pass's program matches, among those `exists(r, v)`
@@ -599,14 +603,14 @@ GradFn<real> pick_grad_kernel(const TileArgs<GradTraits<real>::Q>& a, bool weigh
     return weighted ? grad_kernel<real, Q, R, true> : grad_kernel<real, Q, R, false>;
 }
 
-// The persistent prefetching kernel for a pass, when its program has one (complex64, unit
-// weights, a compiled program with an exchange), else nullptr.
+// The persistent prefetching kernel for a pass, when its program has one (complex64, a compiled
+// program with an exchange), else nullptr.
 template <typename real>
 GradPfFn pick_grad_pf_kernel(const TileArgs<GradTraits<real>::Q>& a, bool weighted) {
     int r = 0, v = 0;
-    auto exists = [](int rr, int vv) { return grad_pf_for(rr, vv) != nullptr; };
-    if (weighted || !match_grad_recipe<real>(a, exists, &r, &v)) return nullptr;
-    return grad_pf_for(r, v);
+    auto exists = [&](int rr, int vv) { return grad_pf_for(rr, vv, weighted) != nullptr; };
+    if (!match_grad_recipe<real>(a, exists, &r, &v)) return nullptr;
+    return grad_pf_for(r, v, weighted);
 }
 
 // CTAs of a persistent kernel that fit the current device at once (cached per device and kernel).
@@ -670,9 +674,10 @@ qaoa_status ensure_attributes() {
                     if (GradFn<real> f = grad_recipe_kernel<real>(r, w, v))
                         CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                       (int)(2 * (1u << GQ) * sizeof(C2))));
-                if (GradPfFn f = grad_pf_for(r, v))
-                    CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  (int)(2 * (1u << GQ) * sizeof(C2))));
+                for (bool w : {false, true})
+                    if (GradPfFn f = grad_pf_for(r, v, w))
+                        CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                      (int)(2 * (1u << GQ) * sizeof(C2))));
             }
     CUDA_TRY(cudaFuncSetAttribute(small_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024));
     CUDA_TRY(cudaFuncSetAttribute(small_batch_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024));

@@ -1,6 +1,6 @@
 // instances.h -- the heavy kernel template instantiations (the pass kernels, their packed forms and
 // the adjoint-sweep kernels), each compiled in a translation unit of its own (tile_c64.cu,
-// tile_c128.cu, batch_c64.cu, grad_kernels.cu, grad_recipes.cu, grad_recipes_m.cu, grad_recipes_x.cu, grad_pf.cu, ...) so that the library builds
+// tile_c128.cu, batch_c64.cu, grad_kernels.cu, grad_recipes.cu, grad_recipes_m.cu, grad_recipes_x.cu, grad_pf.cu, grad_pf_w.cu, ...) so that the library builds
 // in parallel.  capi.cu includes this file after
 // kernels.cuh with QAOA_INSTANCE = "extern template" (declarations); each instance unit defines
 // QAOA_OWN_* for the set it owns and instantiates that set with QAOA_INSTANCE = "template".
@@ -100,26 +100,27 @@
     QAOA_GRAD_RECIPE_V(real, Q, R, 1, 3)                                                               \
     }
 
-// the persistent prefetching sweep programs (grad_pf_kernel), complex64 unit weights
-#define QAOA_GRAD_PF_ONE(Q, R, r, v)                                                                  \
-    QAOA_INSTANCE __global__ void grad_pf_kernel<Q, R, grad_recipe(r).code, grad_recipe(r).nops,           \
+// the persistent prefetching sweep programs (grad_pf_kernel), complex64, unit weights (w =
+// false, grad_pf.cu) and edge weights (w = true, grad_pf_w.cu)
+#define QAOA_GRAD_PF_ONE(Q, R, w, r, v)                                                               \
+    QAOA_INSTANCE __global__ void grad_pf_kernel<Q, R, w, grad_recipe(r).code, grad_recipe(r).nops,        \
                                                  grad_masks(r, v), grad_recipe(r).hi>(                         \
         const __grid_constant__ TileArgs<Q>, uint64_t);
-#define QAOA_GRAD_PF_INSTANCES(Q, R)                                                                  \
+#define QAOA_GRAD_PF_INSTANCES(Q, R, w)                                                               \
     namespace qaoa {                                                                                   \
-    QAOA_GRAD_PF_ONE(Q, R, 0, 1)                                                                       \
-    QAOA_GRAD_PF_ONE(Q, R, 1, 0)                                                                       \
-    QAOA_GRAD_PF_ONE(Q, R, 1, 1)                                                                       \
-    QAOA_GRAD_PF_ONE(Q, R, 1, 2)                                                                       \
-    QAOA_GRAD_PF_ONE(Q, R, 1, 3)                                                                       \
-    QAOA_GRAD_PF_ONE(Q, R, 3, 0)                                                                       \
-    QAOA_GRAD_PF_ONE(Q, R, 3, 1)                                                                       \
-    QAOA_GRAD_PF_ONE(Q, R, 4, 0)                                                                       \
-    QAOA_GRAD_PF_ONE(Q, R, 4, 1)                                                                       \
-    QAOA_GRAD_PF_ONE(Q, R, 5, 0)                                                                       \
-    QAOA_GRAD_PF_ONE(Q, R, 6, 0)                                                                       \
-    QAOA_GRAD_PF_ONE(Q, R, 7, 0)                                                                       \
-    QAOA_GRAD_PF_ONE(Q, R, 8, 0)                                                                       \
+    QAOA_GRAD_PF_ONE(Q, R, w, 0, 1)                                                                    \
+    QAOA_GRAD_PF_ONE(Q, R, w, 1, 0)                                                                    \
+    QAOA_GRAD_PF_ONE(Q, R, w, 1, 1)                                                                    \
+    QAOA_GRAD_PF_ONE(Q, R, w, 1, 2)                                                                    \
+    QAOA_GRAD_PF_ONE(Q, R, w, 1, 3)                                                                    \
+    QAOA_GRAD_PF_ONE(Q, R, w, 3, 0)                                                                    \
+    QAOA_GRAD_PF_ONE(Q, R, w, 3, 1)                                                                    \
+    QAOA_GRAD_PF_ONE(Q, R, w, 4, 0)                                                                    \
+    QAOA_GRAD_PF_ONE(Q, R, w, 4, 1)                                                                    \
+    QAOA_GRAD_PF_ONE(Q, R, w, 5, 0)                                                                    \
+    QAOA_GRAD_PF_ONE(Q, R, w, 6, 0)                                                                    \
+    QAOA_GRAD_PF_ONE(Q, R, w, 7, 0)                                                                    \
+    QAOA_GRAD_PF_ONE(Q, R, w, 8, 0)                                                                    \
     }
 
 // packed mid-size requests of the server: the complex64 two-group programs (recipes 8..12) and the
@@ -170,5 +171,8 @@ QAOA_GRAD_RECIPE_M_INSTANCES(float, 12, 4)
 QAOA_GRAD_RECIPE_X_INSTANCES(float, 12, 4)
 #endif
 #if !defined(QAOA_OWN_GRAD_PF)
-QAOA_GRAD_PF_INSTANCES(12, 4)
+QAOA_GRAD_PF_INSTANCES(12, 4, false)
+#endif
+#if !defined(QAOA_OWN_GRAD_PF_W)
+QAOA_GRAD_PF_INSTANCES(12, 4, true)
 #endif

@@ -1843,7 +1843,7 @@ __host__ __device__ constexpr int recipe_last_xchg(uint64_t lo, uint64_t hi, int
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// The compiled complex64 sweep programs (unit weights) as a persistent, prefetching kernel: CTA b
+// The compiled complex64 sweep programs (unit or edge weights) as a persistent, prefetching kernel: CTA b
 // runs tiles b, b + G, b + 2G, ... (G = gridDim.x, at most the CTAs that fit the GPU at once).
 // The next tile's psi and lambda are copied into the CTA's two exchange tiles by cp.async as
 // soon as the program's last exchange has read them, so the copy overlaps the rest of the
@@ -1852,20 +1852,25 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // pair per slot: partials[2 b + slot] for b < G (the host reduces G entries per pass).  The
 // order is fixed for a given grid, so results are deterministic; they equal grad_kernel's up to
 // the order of the per-tile sums.
-template <int Q, int R, uint64_t kRecipe, int kNops, uint64_t kMasks, uint64_t kRecipeHi = 0>
+template <int Q, int R, bool kW, uint64_t kRecipe, int kNops, uint64_t kMasks, uint64_t kRecipeHi = 0>
 __global__ void __launch_bounds__(1 << (Q - R), 2)
     grad_pf_kernel(const __grid_constant__ TileArgs<Q> a, uint64_t tiles) {
     using real = float;
     using T = Tile<real, Q, R, true>;
     using C2 = typename T::C2;
+    using WA = typename T::WA;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr int kSetup = recipe_cut_setup(kRecipe, kRecipeHi, kNops);
-    static_assert(kSetup == 0 || kSetup == 1 || kSetup == 2, "compiled sweep program");
+    // unit weights: where the CTA's cut terms are computed (recipe_cut_setup); edge weights: the
+    // weighted terms of every tile by all threads (weighted_cta_setup), -1
+    constexpr int kSetup = kW ? -1 : recipe_cut_setup(kRecipe, kRecipeHi, kNops);
+    static_assert(kSetup >= -1 && kSetup <= 2, "compiled sweep program");
     // cut terms: one copy per warp (kSetup 2), else two copies used by alternate tiles, so that
-    // warp 0 can write a tile's terms while slower warps still read the previous tile's
+    // a tile's terms can be written while slower warps still read the previous tile's
     constexpr int kCopies = kSetup == 2 ? T::NT / 32 : 2;
-    __shared__ int sE_all[kCopies][Q];
-    __shared__ int sK_all[kCopies];
+    __shared__ int sE_all[kW ? 1 : kCopies][Q];
+    __shared__ int sK_all[kW ? 1 : kCopies];
+    __shared__ WA sKw[kW ? 2 : 1][kWSlots];
+    __shared__ WA sEw[kW ? 2 : 1][kWSlots][Q];
     constexpr bool kLam = kNops > 1 && recipe_kind2(kRecipe, kRecipeHi, 1) == OP_LAMBDA;
     constexpr int kLastX = recipe_last_xchg(kRecipe, kRecipeHi, kNops);
     static_assert(kLastX > 0, "the prefetch follows the program's last exchange");
@@ -1897,7 +1902,7 @@ __global__ void __launch_bounds__(1 << (Q - R), 2)
     int it = 0;
     for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x, ++it) {
         const uint64_t zb = zb_of(t);
-        const uint32_t copy = kSetup == 2 ? tid / 32 : (uint32_t)(it & 1);
+        const uint32_t copy = kW ? 0u : (kSetup == 2 ? tid / 32 : (uint32_t)(it & 1));
         int* const sE = sE_all[copy];
         auto cut_terms = [&]() {
             const uint32_t lane = tid & 31u;
@@ -1915,7 +1920,12 @@ __global__ void __launch_bounds__(1 << (Q - R), 2)
         c.sg = (((__popcll(zb) + __popc(tid)) & 1) != 0) ? (real)-1 : (real)1;  // P of the parity form
         cp_async_wait_all();
         __syncthreads();  // every thread's copies of tile t have landed
-        if constexpr (kSetup == 2) {
+        if constexpr (kW) {
+            weighted_cta_setup<WA, Q>(a, zb, sKw[it & 1], sEw[it & 1], tid, T::NT);
+            c.wK = sKw[it & 1];
+            c.wE = sEw[it & 1];
+            c.K = 0;
+        } else if constexpr (kSetup == 2) {
             cut_terms();
             __syncwarp();
             c.K = sK_all[copy];
@@ -1932,7 +1942,7 @@ __global__ void __launch_bounds__(1 << (Q - R), 2)
                 T::template from_smem<Lc>(v, tile, tid, a.bounds_flag);
                 if constexpr (!kLam) T::template from_smem<Lc>(w, tile2, tid, a.bounds_flag);
             } else if constexpr (kind == OP_LAMBDA) {
-                T::template lambda_init<Lc, false>(v, w, c, tid);
+                T::template lambda_init<Lc, kW>(v, w, c, tid);
             } else if constexpr (kind == OP_XCHG) {
                 T::template to_smem<Lp>(v, tile, tid, a.bounds_flag);
                 T::template to_smem<Lp>(w, tile2, tid, a.bounds_flag);
@@ -1954,20 +1964,20 @@ __global__ void __launch_bounds__(1 << (Q - R), 2)
                 else acc[0] += dd;
             } else if constexpr (kind == OP_GRADG) {
                 if constexpr (kSetup == 1) c.K = sK_all[copy];
-                const real g = T::template grad_gamma_parity<Lc, false>(v, w, c, tid);
+                const real g = T::template grad_gamma_parity<Lc, kW>(v, w, c, tid);
                 const double dd = (double)(c.sg * g) * a.gpow[sweep_level(a.ops[i].arg) * (kMaxN + 1) + a.n];
                 if (sweep_slot(a.ops[i].arg)) acc[3] += dd;
                 else acc[1] += dd;
             } else if constexpr (kind == OP_PHASED) {
                 if constexpr (kSetup == 1) c.K = sK_all[copy];
-                T::template phase_dual_parity<Lc, false>(v, w, c, tid, a.ops[i].arg);
+                T::template phase_dual_parity<Lc, kW>(v, w, c, tid, a.ops[i].arg);
             } else if constexpr (kind == OP_STORE) {
                 T::template store_to<Lc>(v, c, tid, a.state);
                 T::template store_to<Lc>(w, c, tid, a.state2);
             }
             // warp 0 computes the cut terms after its loads; the next exchange's barrier
             // publishes them
-            if constexpr (kSetup == 1 && i == 0)
+            if constexpr (!kW && kSetup == 1 && i == 0)
                 if (a.need_cut && tid < 32) cut_terms();
         });
     }
