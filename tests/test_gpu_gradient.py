@@ -248,3 +248,19 @@ def test_gradient_stored_oracle_adjoint(B, name, prec):
         assert abs(c - rec["expectation"]) <= 1e-5 * g.m
         assert np.max(np.abs(dg - ref_dg)) <= tol
         assert np.max(np.abs(db - ref_db)) <= tol
+
+
+def test_gradient_many_passes_persistent_sweep(B):
+    """n = 22, p = 40: 81 sweep passes in the persistent form, whose per-CTA partials are reduced
+    in two batches (64 + 17 passes), against the same gradient in complex128 (one CTA per tile,
+    one reduction per pass; pinned to the oracle by the tests above)."""
+    g = I.regular3(22, 3)
+    gamma, beta = I.angles(40, 321)
+    gamma *= 0.2
+    c64, dg64, db64 = gpu_gradient(B, g, gamma, beta, "c64")
+    c128, dg128, db128 = gpu_gradient(B, g, gamma, beta, "c128")
+    big = np.max(np.abs(np.concatenate([dg128, db128])))
+    tol = c64_grad_tol(22, 40, g.m, big)
+    assert abs(c64 - c128) <= 1e-5 * g.m
+    assert np.max(np.abs(dg64 - dg128)) <= tol
+    assert np.max(np.abs(db64 - db128)) <= tol
