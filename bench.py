@@ -457,6 +457,11 @@ def run_ours(args):
         if args.n != 30:
             rec["n30"] = size_block(B, 30, 8, "c64", steps=10, warmup=3)
         rec["grad"] = grad_block(B, "c64", False, 10, 3, not args.no_accuracy)
+        # the same at a size where neither state fits in L2 (G(28, 0.5), p = 6; timing only)
+        g28 = grad_block(B, "c64", False, 4, 3, False, n=28, p=6)
+        rec["grad"]["n28"] = {k: g28[k] for k in ("value", "unit", "ms_per_gradient", "ms_per_forward",
+                                                  "gradient_over_forward")}
+        rec["grad"]["n28"]["workload"] = g28["config"]["workload"]
         rec["serve"] = serve_block(B, count=args.extra_serve_requests,
                                    rates=(args.serve_rate, args.serve_sustain_rate), prec="c64")
         rec["extra_blocks_s"] = time.perf_counter() - t0
