@@ -88,8 +88,9 @@ size_t qaoa_state_bytes(int32_t n, qaoa_prec prec);
  * here: the uniform amplitudes are produced by the first kernel that needs them, so the first
  * level of qaoa_apply_layers reads nothing.  Validates the graph (QAOA_ERR_INVALID on a self
  * loop, repeated edge, endpoint out of range, non-finite weight or |w| > 1e12), encodes the
- * rows graph_I of Table 1 and the pass plan, and allocates workspace (QAOA_ERR_OOM).  On
- * success *out receives the handle. */
+ * rows graph_I of Table 1 and the pass plan, and takes its workspace from the library's pool on
+ * that stream (QAOA_ERR_OOM).  The buffer and the stream must stay valid until qaoa_state_free
+ * returns.  On success *out receives the handle. */
 qaoa_status qaoa_state_init(const qaoa_graph *g, qaoa_prec prec, void *dev_buf, size_t buf_bytes,
                             void *cuda_stream, qaoa_state *out);
 
