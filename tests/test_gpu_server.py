@@ -283,3 +283,40 @@ def test_deadline_expires_while_queued(B):
         assert res[t]["t_done"] - res[t]["t_submit"] >= 1e-4
         assert res[t]["t_submit"] < res[big]["t_done"]
     assert stats["timed_out"] == 3
+
+
+def test_gpu_filling_requests_on_the_lane(B):
+    """Requests whose state fills the GPU (64 MiB or more: n = 24 here) run one after another on
+    the low-priority lane while small ones run beside them: the n = 24 results (a forward run
+    of G(24, 0.5), p = 10 and a gradient of a 3-regular n = 24 graph, p = 3) equal the same
+    requests run alone bit for bit and match the oracle's stored values (tests/golden, written
+    by the oracle only); the small requests equal theirs run alone."""
+    import json
+    import os
+    gold = os.path.join(os.path.dirname(__file__), "golden")
+    fwd = json.load(open(os.path.join(gold, "gnp24_p10.json")))
+    grd = json.load(open(os.path.join(gold, "grad_regular3_n24_p3.json")))
+    gf = I.Graph(fwd["n"], np.array(fwd["edges"], dtype=np.int32))
+    gg = I.Graph(grd["n"], np.array(grd["edges"], dtype=np.int32))
+    big = [(gf, np.array(fwd["gamma"]), np.array(fwd["beta"]), False),
+           (gg, np.array(grd["gamma"]), np.array(grd["beta"]), True)] * 2
+    small = mixed_requests(24, seed=11)
+    reqs = [x for pair in zip(big + [None] * (len(small) - len(big)), small) for x in pair if x is not None]
+    sv = B.qaoa_server_create(8 << 30, "c64", max_inflight=16, max_batch=8, streams=4)
+    tickets = [B.qaoa_submit(sv, g, ga, be, grad) for g, ga, be, grad in reqs]
+    res = wait_all(B, sv, tickets)
+    B.qaoa_server_destroy(sv)
+    for (g, ga, be, grad), t in zip(reqs, tickets):
+        r = res[t]
+        assert r["status"] == 0
+        c, dg, db = alone(B, g, ga, be, grad)
+        assert r["expectation"] == c, (g.name, r["expectation"], c)
+        if grad:
+            assert np.array_equal(r["d_gamma"], dg) and np.array_equal(r["d_beta"], db)
+        if g is gf:
+            assert abs(r["expectation"] - fwd["expectation"]) <= 1e-5 * fwd["m"]
+        elif g is gg:
+            ref = np.concatenate([grd["d_gamma"], grd["d_beta"]])
+            tol = c64_grad_tol(gg.n, len(grd["gamma"]), gg.m, np.max(np.abs(ref)))
+            assert abs(r["expectation"] - grd["expectation"]) <= 1e-5 * grd["m"]
+            assert np.max(np.abs(np.concatenate([r["d_gamma"], r["d_beta"]]) - ref)) <= tol
