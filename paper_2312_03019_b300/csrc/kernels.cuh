@@ -1845,10 +1845,11 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 // The compiled complex64 sweep programs (unit or edge weights) as a persistent, prefetching kernel: CTA b
 // runs tiles b, b + G, b + 2G, ... (G = gridDim.x, at most the CTAs that fit the GPU at once).
-// The next tile's psi and lambda are copied into the CTA's two exchange tiles by cp.async as
-// soon as the program's last exchange has read them, so the copy overlaps the rest of the
-// current tile (its last butterflies and its stores); the program's LOAD then reads shared
-// memory.  The FP64 sums of a thread run over all of its tiles and each CTA writes one partial
+// The next tile's lambda (psi in the first pass, which makes lambda itself) is copied into its
+// exchange tile by cp.async as soon as the program's last exchange has read it, so the copy
+// overlaps the rest of the current tile (its last butterflies and its stores); the program's
+// LOAD then reads lambda from shared memory and psi straight from HBM.  (Staging both states
+// moved the passes' top stall to the shared-memory queue: 2.5-3 % slower.)  The FP64 sums of a thread run over all of its tiles and each CTA writes one partial
 // pair per slot: partials[2 b + slot] for b < G (the host reduces G entries per pass).  The
 // order is fixed for a given grid, so results are deterministic; they equal grad_kernel's up to
 // the order of the per-tile sums.
@@ -1893,8 +1894,9 @@ __global__ void __launch_bounds__(1 << (Q - R), 2)
     auto prefetch = [&](uint64_t t) {
         typename T::Ctx cn = c;
         cn.zb = zb_of(t);
-        T::template prefetch_to<kL0>(tile, cn, tid, a.state, a.bounds_flag);
-        if constexpr (!kLam) T::template prefetch_to<kL0>(tile2, cn, tid, a.state2, a.bounds_flag);
+        // one state per tile is staged: lambda (psi in the first pass, which makes lambda)
+        if constexpr (kLam) T::template prefetch_to<kL0>(tile, cn, tid, a.state, a.bounds_flag);
+        else T::template prefetch_to<kL0>(tile2, cn, tid, a.state2, a.bounds_flag);
         cp_async_commit();
     };
     if ((uint64_t)blockIdx.x < tiles) prefetch(blockIdx.x);
@@ -1939,8 +1941,12 @@ __global__ void __launch_bounds__(1 << (Q - R), 2)
             constexpr int Lc = recipe_layout2(kRecipe, kRecipeHi, i);
             constexpr int Lp = i == 0 ? 0 : recipe_layout2(kRecipe, kRecipeHi, i - 1);
             if constexpr (kind == OP_LOAD) {
-                T::template from_smem<Lc>(v, tile, tid, a.bounds_flag);
-                if constexpr (!kLam) T::template from_smem<Lc>(w, tile2, tid, a.bounds_flag);
+                if constexpr (kLam) {
+                    T::template from_smem<Lc>(v, tile, tid, a.bounds_flag);
+                } else {  // psi straight from HBM, lambda from its staged tile
+                    T::template load_from<Lc>(v, c, tid, a.state);
+                    T::template from_smem<Lc>(w, tile2, tid, a.bounds_flag);
+                }
             } else if constexpr (kind == OP_LAMBDA) {
                 T::template lambda_init<Lc, kW>(v, w, c, tid);
             } else if constexpr (kind == OP_XCHG) {
