@@ -1832,6 +1832,13 @@ __global__ void __launch_bounds__(1 << (Q - R), sizeof(real) == 4 ? 2 : 1) grad_
     }
 }
 
+// Whether a compiled (one- or two-word) program has an op of the given kind.
+__host__ __device__ constexpr bool recipe_has(uint64_t lo, uint64_t hi, int nops, int kind) {
+    for (int i = 0; i < nops; ++i)
+        if (recipe_kind2(lo, hi, i) == kind) return true;
+    return false;
+}
+
 // Index of the last exchange of a compiled (one- or two-word) program (-1: none).
 __host__ __device__ constexpr int recipe_last_xchg(uint64_t lo, uint64_t hi, int nops) {
     int last = -1;
@@ -1849,7 +1856,8 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // exchange tile by cp.async as soon as the program's last exchange has read it, so the copy
 // overlaps the rest of the current tile (its last butterflies and its stores); the program's
 // LOAD then reads lambda from shared memory and psi straight from HBM.  (Staging both states
-// moved the passes' top stall to the shared-memory queue: 2.5-3 % slower.)  The FP64 sums of a thread run over all of its tiles and each CTA writes one partial
+// moved the passes' top stall to the shared-memory queue: 2.5-3 % slower, except in the fused
+// boundary passes, which stage both.)  The FP64 sums of a thread run over all of its tiles and each CTA writes one partial
 // pair per slot: partials[2 b + slot] for b < G (the host reduces G entries per pass).  The
 // order is fixed for a given grid, so results are deterministic; they equal grad_kernel's up to
 // the order of the per-tile sums.
@@ -1876,6 +1884,9 @@ __global__ void __launch_bounds__(1 << (Q - R), 2)
     constexpr int kLastX = recipe_last_xchg(kRecipe, kRecipeHi, kNops);
     static_assert(kLastX > 0, "the prefetch follows the program's last exchange");
     constexpr int kL0 = recipe_layout2(kRecipe, kRecipeHi, 0);
+    // the fused boundary programs (with the inverse phase) stage psi as well: measured faster
+    // for them (2.24 against 2.29 ms per pass at n = 28), slower for the others
+    constexpr bool kBoth = !kLam && recipe_has(kRecipe, kRecipeHi, kNops, OP_PHASED);
 
     unsigned char* tile = smem_raw;
     unsigned char* tile2 = smem_raw + (1u << Q) * sizeof(C2);
@@ -1894,9 +1905,9 @@ __global__ void __launch_bounds__(1 << (Q - R), 2)
     auto prefetch = [&](uint64_t t) {
         typename T::Ctx cn = c;
         cn.zb = zb_of(t);
-        // one state per tile is staged: lambda (psi in the first pass, which makes lambda)
-        if constexpr (kLam) T::template prefetch_to<kL0>(tile, cn, tid, a.state, a.bounds_flag);
-        else T::template prefetch_to<kL0>(tile2, cn, tid, a.state2, a.bounds_flag);
+        // lambda is staged (psi in the first pass, which makes lambda; both in fused passes)
+        if constexpr (kLam || kBoth) T::template prefetch_to<kL0>(tile, cn, tid, a.state, a.bounds_flag);
+        if constexpr (!kLam) T::template prefetch_to<kL0>(tile2, cn, tid, a.state2, a.bounds_flag);
         cp_async_commit();
     };
     if ((uint64_t)blockIdx.x < tiles) prefetch(blockIdx.x);
@@ -1941,12 +1952,9 @@ __global__ void __launch_bounds__(1 << (Q - R), 2)
             constexpr int Lc = recipe_layout2(kRecipe, kRecipeHi, i);
             constexpr int Lp = i == 0 ? 0 : recipe_layout2(kRecipe, kRecipeHi, i - 1);
             if constexpr (kind == OP_LOAD) {
-                if constexpr (kLam) {
-                    T::template from_smem<Lc>(v, tile, tid, a.bounds_flag);
-                } else {  // psi straight from HBM, lambda from its staged tile
-                    T::template load_from<Lc>(v, c, tid, a.state);
-                    T::template from_smem<Lc>(w, tile2, tid, a.bounds_flag);
-                }
+                if constexpr (kLam || kBoth) T::template from_smem<Lc>(v, tile, tid, a.bounds_flag);
+                else T::template load_from<Lc>(v, c, tid, a.state);  // psi straight from HBM
+                if constexpr (!kLam) T::template from_smem<Lc>(w, tile2, tid, a.bounds_flag);
             } else if constexpr (kind == OP_LAMBDA) {
                 T::template lambda_init<Lc, kW>(v, w, c, tid);
             } else if constexpr (kind == OP_XCHG) {
