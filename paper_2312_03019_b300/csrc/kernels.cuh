@@ -999,6 +999,37 @@ struct Tile {
         });
     }
 
+    // grad_gamma_parity followed by phase_dual_parity in the same layout (unit weights), with
+    // each amplitude's cut value counted once for both: the gamma term of slot x is taken from
+    // the amplitudes before their phase, the sums run in the same order, so the results are
+    // bit-identical to the two ops in turn.  The cut value is exact, so the table index needs no
+    // clamp (the debug build checks it).
+    template <int L>
+    static __device__ __forceinline__ real grad_gamma_phase_dual_parity(C2 (&v)[NE], C2 (&w)[NE], const Ctx& c,
+                                                                        uint32_t tid, int level) {
+        const TileArgs<Q>& a = *c.a;
+        const C2* __restrict__ T = reinterpret_cast<const C2*>(a.phase) + (size_t)level * a.E1;
+        real acc_e = 0, acc_o = 0;
+        int s[R];
+        const int base = cut_setup<L>(c, tid, s);
+        for_x<NE>([&](auto X) {
+            constexpr int x = decltype(X)::value;
+            int cidx = base + a.crtab[L][x];
+#pragma unroll
+            for (int j = 0; j < R; ++j)
+                if ((x >> j) & 1) cidx += s[j];
+            const real d = (real)cidx * (w[x].x * v[x].y - w[x].y * v[x].x);
+            if constexpr (odd_parity(x)) acc_o += d;
+            else acc_e += d;
+            (void)QAOA_IN_BOUNDS(a.bounds_flag, (unsigned)cidx < (unsigned)a.E1, 16u);
+            const C2 f = __ldg(T + cidx);
+            const C2 fc = make_c2(f.x, -f.y);
+            v[x] = apply_phase<x>(v[x], fc, c.sg);
+            w[x] = apply_phase<x>(w[x], fc, c.sg);
+        });
+        return acc_e - acc_o;
+    }
+
     // sum_z C(z) Im(conj(lambda_z) psi_z) over the thread's amplitudes
     template <int L, bool kW = false>
     static __device__ __forceinline__ real grad_gamma(const C2 (&v)[NE], const C2 (&w)[NE], const Ctx& c, uint32_t tid) {
@@ -1978,13 +2009,20 @@ __global__ void __launch_bounds__(1 << (Q - R), 2)
                 else acc[0] += dd;
             } else if constexpr (kind == OP_GRADG) {
                 if constexpr (kSetup == 1) c.K = sK_all[copy];
-                const real g = T::template grad_gamma_parity<Lc, kW>(v, w, c, tid);
+                // a GRADG directly followed by the PHASED of the same layout runs as one op
+                constexpr bool kMerged = !kW && i + 1 < kNops && recipe_kind2(kRecipe, kRecipeHi, i + 1) == OP_PHASED;
+                real g;
+                if constexpr (kMerged) g = T::template grad_gamma_phase_dual_parity<Lc>(v, w, c, tid, a.ops[i + 1].arg);
+                else g = T::template grad_gamma_parity<Lc, kW>(v, w, c, tid);
                 const double dd = (double)(c.sg * g) * a.gpow[sweep_level(a.ops[i].arg) * (kMaxN + 1) + a.n];
                 if (sweep_slot(a.ops[i].arg)) acc[3] += dd;
                 else acc[1] += dd;
             } else if constexpr (kind == OP_PHASED) {
-                if constexpr (kSetup == 1) c.K = sK_all[copy];
-                T::template phase_dual_parity<Lc, kW>(v, w, c, tid, a.ops[i].arg);
+                constexpr bool kMerged = !kW && i > 0 && recipe_kind2(kRecipe, kRecipeHi, i - 1) == OP_GRADG;
+                if constexpr (!kMerged) {
+                    if constexpr (kSetup == 1) c.K = sK_all[copy];
+                    T::template phase_dual_parity<Lc, kW>(v, w, c, tid, a.ops[i].arg);
+                }
             } else if constexpr (kind == OP_STORE) {
                 T::template store_to<Lc>(v, c, tid, a.state);
                 T::template store_to<Lc>(w, c, tid, a.state2);
