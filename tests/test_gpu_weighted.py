@@ -243,6 +243,9 @@ def test_weighted_zero_levels_expectation(B, prec):
     (12, 2, lambda: weighted(I.gnp(12, 0.5, 21), 21)),
     (14, 3, lambda: weighted(I.regular3(14, 22), 22)),
     (16, 2, lambda: weighted(I.gnp(16, 0.3, 23), 23, lo=2.0, hi=20.0)),
+    # the persistent sweep programs with edge weights (complex64, n >= 22)
+    (22, 2, lambda: weighted(I.regular3(22, 24), 24)),
+    (24, 2, lambda: weighted(I.gnp(24, 0.3, 25), 25, lo=0.1, hi=2.0)),
 ])
 def test_weighted_gradient_matches_oracle_adjoint(B, prec, n, p, mk):
     import oracle
