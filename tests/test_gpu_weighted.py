@@ -15,6 +15,7 @@ import numpy as np
 import pytest
 
 from paper_2312_03019_b300 import inputs as I
+from tests.tolerances import c64_grad_tol
 
 pytestmark = pytest.mark.gpu
 
@@ -264,9 +265,13 @@ def test_weighted_gradient_matches_oracle_adjoint(B, prec, n, p, mk):
         assert np.max(np.abs(dg - ref_dg)) <= 1e-10 * scale
         assert np.max(np.abs(db - ref_db)) <= 1e-10 * scale
     else:
+        # the FP32 rounding bound of the unit-weight gradient (tests/tolerances.py): the weights
+        # enter through the phase tables (angles rounded to 2^-32 turns) and the fixed-point
+        # values (rounded to 2^-S with S such that sum |w| 2^S is near 2^30), both far below it
+        tol = c64_grad_tol(n, p, g.m, np.max(np.abs(np.concatenate([ref_dg, ref_db]))))
         assert abs(c - ref_c) <= 1e-5 * W
-        assert np.max(np.abs(dg - ref_dg)) <= 1e-4 * W * max(1.0, W / g.m)
-        assert np.max(np.abs(db - ref_db)) <= 1e-4 * W
+        assert np.max(np.abs(dg - ref_dg)) <= tol
+        assert np.max(np.abs(db - ref_db)) <= tol
 
 
 def test_weighted_requests_through_the_server(B):
