@@ -305,6 +305,17 @@ def test_weighted_requests_through_the_server(B):
             c, _ = s.expectation()
         s.close()
         assert r["expectation"] == c
+        # and against the oracle (<C_w> by the gate-level circuit, the gradient by its adjoint)
+        import oracle
+        W = float(np.sum(np.abs(g.weights)))
+        if grad:
+            rc, rdg, rdb = oracle.adjoint_gradient(g, ga, be)
+            ref = np.concatenate([rdg, rdb])
+            tol = c64_grad_tol(g.n, len(ga), g.m, float(np.max(np.abs(ref))))
+            assert np.max(np.abs(np.concatenate([r["d_gamma"], r["d_beta"]]) - ref)) <= tol
+        else:
+            rc, _ = oracle.expectation(g, oracle.qaoa_state(g, ga, be))
+        assert abs(r["expectation"] - rc) <= 1e-5 * W
 
 
 def test_weighted_more_levels_than_one_coefficient_chunk(B):
